@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Jacobi3D benchmark: cell-updates/s and the fraction of the HBM roofline.
+
+Workload (one step): a 512^3 binary64 grid split into 8 x 8 x 8 blocks of
+64^3, Dirichlet 1.0 outside the x = 0 face and 0.0 elsewhere, interior
+uniform in [0, 1) from SplitMix64 seed 0; one step runs 1000 Jacobi
+iterations (halo exchange + update of every block each iteration) followed by
+the binary64 residual norm. Inputs stay resident in HBM between steps; the
+2.15 GB working set is larger than the 129 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Under torchrun with N > 1 every rank runs an
+independent replica on its own GPU (the path does not shard across GPUs);
+the timed region is bracketed by a barrier and the slowest rank's time is
+used.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Jacobi3D cell-updates/s"
+UNIT = "cell-updates/s"
+BYTES_PER_UPDATE = {"f64": 16, "f32": 8}  # read + write of one cell at ideal neighbour reuse
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--grid", type=int, nargs=3, default=[512, 512, 512])
+    p.add_argument("--block", type=int, nargs=3, default=[64, 64, 64])
+    p.add_argument("--iters", type=int, default=1000, help="Jacobi iterations per step")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--mode", default="persistent")
+    p.add_argument("--arith", default="exact", choices=["exact", "seq"])
+    p.add_argument("--forms", action="store_true", help="also time the unfused / fused / graph forms")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------- helpers
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        import torch
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, v: float) -> float:
+    if pg is None:
+        return v
+    import torch
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:  # noqa: BLE001
+                self.proc.kill()
+
+    def summary(self):
+        if self.f is None:
+            return None
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except Exception:  # noqa: BLE001
+                    pass
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_tag: str):
+    """dram bytes per launch of the timed kernel from the committed ncu
+    summary (profiles/<kernel_tag>.txt, line 'traffic_bytes_per_launch: N'),
+    or None when no capture of the current kernel exists."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("null", "None", "") else float(v)
+    return None
+
+
+def workload_name(a):
+    g, b = a.grid, a.block
+    nb = [-(-g[i] // b[i]) for i in range(3)]
+    return (f"Jacobi3D {g[0]}x{g[1]}x{g[2]} {a.dtype.upper()}, {nb[0]}x{nb[1]}x{nb[2]} blocks of "
+            f"{b[0]}x{b[1]}x{b[2]}, {a.iters} iterations + residual per step, {a.mode} form, "
+            f"{'correctly rounded mean' if (a.arith == 'exact' and a.dtype == 'f64') else 'left-to-right sum / 7'}")
+
+
+# ----------------------------------------------------------------- oracle arms
+def oracle_rate(a, cells_budget: float):
+    """Time the oracle on a bounded sample of the workload: the full grid for
+    as many iterations as fit the budget (at least one)."""
+    import oracle
+    import synth
+
+    g = a.grid
+    u0 = synth.grid_uniform01(0, *g)
+    rule = oracle.RULE_EXACT if a.arith == "exact" else oracle.RULE_SEQ
+    ncell = g[0] * g[1] * g[2]
+    iters = max(1, int(cells_budget // ncell))
+    t = time.perf_counter()
+    if a.dtype == "f32":
+        oracle.jacobi_f32(u0.astype(np.float32), synth.DIRICHLET_X0, iters)
+    else:
+        oracle.jacobi(u0, synth.DIRICHLET_X0, iters, rule)
+    dt = time.perf_counter() - t
+    return ncell * iters / dt, iters, dt, oracle.num_threads()
+
+
+def run_reference(a, rank, world, pg):
+    """The reference arm: the CPU oracle, as it stands, on the host cores."""
+    import oracle
+    import synth
+
+    if rank != 0:
+        return
+    g = a.grid
+    u0 = synth.grid_uniform01(0, *g)
+    rule = oracle.RULE_EXACT if a.arith == "exact" else oracle.RULE_SEQ
+    ncell = g[0] * g[1] * g[2]
+    per_step_iters = 1
+    times = []
+    for i in range(a.warmup + a.steps):
+        t = time.perf_counter()
+        if a.dtype == "f32":
+            oracle.jacobi_f32(u0.astype(np.float32), synth.DIRICHLET_X0, per_step_iters)
+        else:
+            oracle.jacobi(u0, synth.DIRICHLET_X0, per_step_iters, rule)
+        dt = time.perf_counter() - t
+        if i >= a.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = ncell * per_step_iters * a.steps / total
+    sample = f"full {g[0]}x{g[1]}x{g[2]} grid, {per_step_iters} iteration per step (of {a.iters} in the GPU step)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": a.dtype, "data": "synthetic",
+        "config": {"workload": workload_name(a)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(a, rank, world, local, pg):
+    import torch
+
+    import synth
+    from paper_2202_11819_gb300 import Jacobi3D, _lib, use_torch_allocator
+
+    torch.cuda.set_device(local)
+    use_torch_allocator(True)
+    stream = torch.cuda.Stream()
+    g, b = a.grid, a.block
+    ncell = g[0] * g[1] * g[2]
+    np_dt = np.float32 if a.dtype == "f32" else np.float64
+    u0 = synth.grid_uniform01(0, *g)
+    if a.dtype == "f32":
+        u0 = u0.astype(np.float32)
+    host_in = torch.from_numpy(u0.reshape(-1)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    dev_u0 = host_in.to(f"cuda:{local}")
+    rho = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
+
+    with torch.cuda.stream(stream):
+        J = Jacobi3D(g, b, dtype=a.dtype, bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode,
+                     arith=a.arith if a.dtype == "f64" else "seq")
+        J.write_device(dev_u0)
+
+        def step():
+            J.iterate(a.iters)
+            J.residual_device(rho)
+
+        for _ in range(a.warmup):
+            step()
+        stream.synchronize()
+        J.sync()
+
+        # ---- device-resident timed region
+        launches0 = J.info()["kernel_launches"]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        barrier(pg)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for i in range(a.steps):
+                ev[i][0].record(stream)
+                J.iterate(a.iters)
+                ev[i][1].record(stream)
+                J.residual_device(rho)
+            stream.synchronize()
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        barrier(pg)
+        J.sync()
+        launches = J.info()["kernel_launches"] - launches0
+        clocks = clk.summary()
+        iter_ms = [e[0].elapsed_time(e[1]) for e in ev]  # the iteration launch(es) of each step
+        wall = max_over_ranks(pg, wall)
+        value = world * ncell * a.iters * a.steps / wall
+
+        # ---- roofline of the dominant kernel (the iteration launch)
+        peak, peak_kind = measured_peaks()
+        mean_launch_s = statistics.mean(iter_ms) / 1e3
+        algo_bytes = BYTES_PER_UPDATE[a.dtype] * ncell * a.iters
+        achieved = algo_bytes / mean_launch_s / 1e9
+        kernel_tag = f"{a.mode}_{a.dtype}_{a.arith}_{g[0]}"
+        traffic = profile_traffic(kernel_tag)
+        if traffic is not None:
+            traffic = traffic * a.iters  # summaries store bytes per iteration
+
+        # ---- end to end through the C ABI with host buffers
+        e2e = None
+        if not a.no_e2e:
+            e2e_steps = max(1, min(a.steps, 3))
+            barrier(pg)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                if a.dtype == "f32":
+                    _lib.jac_write_f32(J.h, host_in.numpy())
+                else:
+                    _lib.jac_write(J.h, host_in.numpy())
+                J.iterate(a.iters)
+                r = J.residual()
+                if a.dtype == "f32":
+                    _lib.jac_read_f32(J.h, host_out.numpy())
+                else:
+                    _lib.jac_read(J.h, host_out.numpy())
+            torch.cuda.synchronize()
+            e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
+            nbytes = ncell * np.dtype(np_dt).itemsize
+            e2e = {"value": world * ncell * a.iters * e2e_steps / e2e_wall, "unit": UNIT,
+                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
+                   "residual": r}
+
+        # ---- other issue forms on the same grid (fewer iterations)
+        forms = None
+        if a.forms:
+            forms = {}
+            for mode, n in (("unfused", 10), ("graph", 10), ("fused", 100), ("graph_fused", 100),
+                            ("persistent", 100)):
+                J.set_mode(mode)
+                J.iterate(2)  # builds graphs / streams outside the timing
+                stream.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0 = time.perf_counter()
+                e0.record(stream)
+                J.iterate(n)
+                e1.record(stream)
+                stream.synchronize()
+                w = time.perf_counter() - t0
+                forms[mode] = {"iters": n, "ms_per_iter": 1e3 * w / n,
+                               "cell_updates_per_s": ncell * n / w,
+                               "device_ms_per_iter": e0.elapsed_time(e1) / n}
+            J.set_mode(a.mode)
+        J.sync()
+        J.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if not a.no_cpu:
+        budget = 1.0e8 if (a.arith == "exact" and a.dtype == "f64") else 2.0e9
+        rate, it, dt, cores = oracle_rate(a, budget)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"full {g[0]}x{g[1]}x{g[2]} grid, {it} iteration(s), {dt:.1f} s"}
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": a.steps,
+        "warmup": a.warmup,
+        "ms_per_step": 1e3 * wall / a.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": a.dtype,
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "grid": list(g), "block": list(b), "iterations_per_step": a.iters,
+                   "mode": a.mode, "arith": a.arith if a.dtype == "f64" else "seq",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (working set %.2f GB vs 129 MB L2)" % (
+                       2 * ncell * np.dtype(np_dt).itemsize / 1e9)},
+        "hbm_frac": achieved / peak,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s",
+                     "algorithmic_bytes_per_launch": algo_bytes,
+                     "launch_ms_mean": 1e3 * mean_launch_s},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if forms is not None:
+        line["forms"] = forms
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank, world, local, pg = dist_setup(a.gpus)
+    try:
+        if a.impl == "reference":
+            run_reference(a, rank, world, pg)
+        else:
+            run_ours(a, rank, world, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * jacobi3d.h -- C ABI of the GB300 Jacobi3D library (libjacobi3d.so).
+ *
+ * The library runs the paper's Jacobi3D proxy application ("Improving
+ * Scalability with GPU-Aware Asynchronous Tasks", Choi, Richards, Kale):
+ * a 3D grid overdecomposed into blocks that each carry a one-cell ghost
+ * layer and two copies of their data (Section III-C), updated every
+ * iteration after the halos of the previous iteration have been packed,
+ * exchanged with the six face neighbours and unpacked (Section II-A,
+ * Figs. 1 and 3). All blocks live in one GPU's HBM; the exchange is a
+ * device-to-device copy or a direct read of the neighbour's face.
+ *
+ * Conventions
+ *   - Global interior arrays are x fastest: cell (i, j, k) of an
+ *     nx x ny x nz grid is element i + nx*(j + ny*k).
+ *   - Faces and boundary values are ordered -x, +x, -y, +y, -z, +z.
+ *   - The update of an interior cell is the mean of itself and its six face
+ *     neighbours; outside the global grid the neighbours are the Dirichlet
+ *     values bc[6], constant across iterations.
+ *   - Every call returns JAC_OK (0) or a negative JAC_E* code; no call
+ *     aborts, throws or exits. jac_strerror() names a code; jac_last_error()
+ *     gives a human-readable message for the calling thread's last failure.
+ *   - Host pointers are borrowed for the duration of the call only. Device
+ *     memory of a context is owned by the library and freed by
+ *     jac_destroy().
+ *   - Calls on one context must not run concurrently from several host
+ *     threads. Work is ordered on the context's CUDA stream.
+ */
+#ifndef JACOBI3D_H
+#define JACOBI3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ */
+/* Codes and enums                                                     */
+/* ------------------------------------------------------------------ */
+
+#define JAC_OK 0
+#define JAC_EINVAL (-1)   /* bad argument: null pointer, size, dims, mode   */
+#define JAC_ENOMEM (-2)   /* a device or host allocation failed             */
+#define JAC_ECUDA (-3)    /* a CUDA runtime call failed                     */
+#define JAC_ETIMEOUT (-4) /* a device-side wait gave up (bounded spin)      */
+#define JAC_EBUDGET (-5)  /* the request exceeds the configured HBM budget  */
+#define JAC_ESTATE (-6)   /* call not valid in the context's current state  */
+
+typedef enum { JAC_F64 = 0, JAC_F32 = 1 } jac_dtype;
+
+/* How one iteration is issued (paper Sections III-A and III-D):
+ *  UNFUSED    per block: 6 pack kernels, 6 device-to-device halo copies into
+ *             the neighbours' receive buffers, 6 unpack kernels into the
+ *             ghost layer and 1 update kernel, on per-block streams (packing,
+ *             copies and unpacking on high-priority streams, the update on a
+ *             low-priority one, Section III-A), ordered with events.
+ *  FUSED      one kernel per iteration for all blocks: unpack, update and
+ *             pack fused (strategy C of Section III-D1) by reading each ghost
+ *             face straight from the neighbour block.
+ *  GRAPH      the UNFUSED iteration captured once as a CUDA graph per
+ *             pointer parity, the two graphs launched alternately
+ *             (Section III-D2).
+ *  PERSISTENT one launch runs all requested iterations for all blocks; each
+ *             block waits only for its six neighbours to finish the previous
+ *             iteration (per-block iteration counters, the device form of
+ *             the reference numbers of Section II-A), with bounded waits.
+ *  GRAPH_FUSED the FUSED kernel captured as two alternating graphs.       */
+typedef enum {
+    JAC_MODE_UNFUSED = 0,
+    JAC_MODE_FUSED = 1,
+    JAC_MODE_GRAPH = 2,
+    JAC_MODE_PERSISTENT = 3,
+    JAC_MODE_GRAPH_FUSED = 4
+} jac_mode;
+
+/* Rounding of the binary64 mean (binary32 contexts always use SEQ):
+ *  SEQ    left-to-right sum c, -x, +x, -y, +y, -z, +z, each addition
+ *         rounded to nearest even, then a correctly rounded division by 7,
+ *         in the GPU's binary64 units.
+ *  EXACT  the exact sum of the seven values divided by 7 and rounded once to
+ *         nearest even (the correctly rounded mean), computed in integer
+ *         arithmetic.                                                     */
+typedef enum { JAC_ARITH_SEQ = 0, JAC_ARITH_EXACT = 1 } jac_arith;
+
+typedef struct jac_ctx jac_ctx;
+
+typedef struct {
+    int64_t dims[3];         /* nx, ny, nz                                   */
+    int32_t block[3];        /* requested block dims bx, by, bz              */
+    int32_t nblocks[3];      /* blocks per axis                              */
+    int32_t dtype;           /* jac_dtype                                    */
+    int32_t mode;            /* jac_mode                                     */
+    int32_t arith;           /* jac_arith                                    */
+    int32_t persistent_ctas; /* CTAs of the persistent launch (0 until used) */
+    int64_t iterations;      /* iterations completed (enqueued) so far       */
+    int64_t device_bytes;    /* device memory held by the context            */
+    int64_t kernel_launches; /* kernels this context has launched so far     */
+} jac_info_t;
+
+/* ------------------------------------------------------------------ */
+/* Memory hook                                                         */
+/* ------------------------------------------------------------------ */
+
+/* Route the library's device allocations through a caller's allocator (the
+ * Python binding installs PyTorch's caching allocator). alloc returns a
+ * device pointer of at least `bytes` bytes, 256-byte aligned, usable on
+ * `stream`, or NULL; free releases it. Passing NULLs restores the default
+ * (cudaMallocAsync / cudaFreeAsync on the context's stream). Applies to
+ * contexts created afterwards. Not thread-safe against concurrent creates. */
+typedef void *(*jac_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*jac_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void *user);
+
+/* ------------------------------------------------------------------ */
+/* Context lifecycle                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Create a context for one global grid.
+ * The paper's statement of the problem: a global 3D grid decomposed into
+ * cuboid blocks (Section IV-A, overdecomposition factor), each block with
+ * one-cell ghost layers and two copies of its data (Section III-C).
+ *   out      receives the new context (set to NULL on failure).
+ *   nx,ny,nz global interior dims, each >= 1.
+ *   bx,by,bz requested block dims, 1 <= b* <= n*, b* <= 256. An axis of n
+ *            cells is split into ceil(n / b) blocks whose sizes differ by at
+ *            most one, the larger ones first.
+ *   dtype    JAC_F64 or JAC_F32: storage and arithmetic type.
+ *   bc       6 finite Dirichlet values (-x, +x, -y, +y, -z, +z); for F32
+ *            they are rounded to nearest binary32. |bc| <= 1e300.
+ *   stream   a cudaStream_t (may be NULL for the legacy default stream) on
+ *            which all of the context's work is ordered.
+ * The interior starts at 0. Fails with JAC_EINVAL on bad arguments,
+ * JAC_ENOMEM if device memory runs out, JAC_ECUDA on other CUDA errors. */
+int jac_create(jac_ctx **out, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
+               int32_t bz, int32_t dtype, const double bc[6], void *stream);
+
+/* Release the context and all of its device memory after its stream has
+ * drained. NULL is accepted. */
+int jac_destroy(jac_ctx *h);
+
+/* Select how iterations are issued (jac_mode). Default JAC_MODE_PERSISTENT.
+ * Any mode may follow any other; the grid state carries over. */
+int jac_set_mode(jac_ctx *h, int32_t mode);
+
+/* Select the binary64 rounding (jac_arith); default JAC_ARITH_EXACT.
+ * JAC_EINVAL for F32 contexts unless arith == JAC_ARITH_SEQ. */
+int jac_set_arith(jac_ctx *h, int32_t arith);
+
+/* ------------------------------------------------------------------ */
+/* Data in and out                                                     */
+/* ------------------------------------------------------------------ */
+
+/* Set the interior from a host array of n_cells = nx*ny*nz binary64 values
+ * (x fastest). Values must be finite with magnitude <= 1e300 (JAC_EINVAL
+ * otherwise, checked on the host); F32 contexts round them to nearest.
+ * The copy goes through pinned staging; the call returns after the data has
+ * left `host` (the host buffer may be reused at once). Resets the
+ * iteration count. */
+int jac_write(jac_ctx *h, const double *host, size_t n_cells);
+
+/* As jac_write, from a host binary32 array (F32 contexts only: exact). */
+int jac_write_f32(jac_ctx *h, const float *host, size_t n_cells);
+
+/* As jac_write, from device memory already on this GPU: `dev` holds n_cells
+ * values of type `dtype` (which must equal the context's dtype), x fastest.
+ * Stream-ordered, no host sync; the caller keeps `dev` alive until the
+ * context's stream passes this point. The values are NOT range-checked. */
+int jac_write_device(jac_ctx *h, const void *dev, size_t n_cells, int32_t dtype);
+
+/* Copy the interior to a host array of n_cells binary64 values (x fastest;
+ * F32 values are widened exactly). Synchronises the context's stream and
+ * returns JAC_ETIMEOUT if a device wait gave up since the last sync. */
+int jac_read(jac_ctx *h, double *host, size_t n_cells);
+
+/* As jac_read into a binary32 host array (F32 contexts only). */
+int jac_read_f32(jac_ctx *h, float *host, size_t n_cells);
+
+/* Gather the interior into device memory `dev` (n_cells values of the
+ * context's dtype, x fastest). Stream-ordered, no host sync. */
+int jac_read_device(jac_ctx *h, void *dev, size_t n_cells, int32_t dtype);
+
+/* ------------------------------------------------------------------ */
+/* Iteration and residual                                              */
+/* ------------------------------------------------------------------ */
+
+/* Enqueue n_iters >= 0 Jacobi iterations (paper Section II-A: halo
+ * exchange then update, two buffers swapped each iteration, Section III-C)
+ * in the selected mode. Asynchronous and stream-ordered: no host sync. */
+int jac_iterate(jac_ctx *h, int64_t n_iters);
+
+/* rho(u) = sqrt( sum over interior cells of L^2 ),
+ * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly and rounded once
+ * to binary64, squared and accumulated in binary64 on the GPU with a
+ * deterministic reduction order. The paper runs a fixed iteration count
+ * and prints no residual (Section IV-A); this is the convergence measure
+ * the library adds. Synchronises the stream; JAC_ETIMEOUT as for jac_read. */
+int jac_residual(jac_ctx *h, double *out);
+
+/* Enqueue the residual computation and write rho into device memory
+ * `dev_out` (one double). Stream-ordered, no host sync. */
+int jac_residual_device(jac_ctx *h, double *dev_out);
+
+/* Wait for the context's stream and report a device-side wait timeout
+ * (JAC_ETIMEOUT) or a CUDA error (JAC_ECUDA). */
+int jac_sync(jac_ctx *h);
+
+/* Describe the context. */
+int jac_info(jac_ctx *h, jac_info_t *info);
+
+/* ------------------------------------------------------------------ */
+/* Diagnostics                                                         */
+/* ------------------------------------------------------------------ */
+
+const char *jac_strerror(int code);
+const char *jac_last_error(void);
+
+/* Limit, in nanoseconds, of every device-side wait of the persistent mode
+ * (default 2e9). After it the kernel records JAC_ETIMEOUT, stops issuing
+ * work and returns; the context's next sync reports it. */
+int jac_set_wait_limit_ns(jac_ctx *h, int64_t ns);
+
+/* Test hook for the timeout path: while `block` >= 0, the persistent kernel
+ * never publishes that block's progress counter after iteration
+ * `after_iter`, so its neighbours' waits run out. -1 disables. */
+int jac_debug_withhold_progress(jac_ctx *h, int32_t block, int64_t after_iter);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI3D_H */

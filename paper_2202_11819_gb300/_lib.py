@@ -1,0 +1,248 @@
+"""ctypes binding of libjacobi3d.so: the C ABI of include/jacobi3d.h with the
+same names. Argument marshalling only: every step of the Jacobi iteration
+runs in the library's CUDA kernels; there is no Python or CPU fallback, and a
+missing or unloadable library raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+JAC_OK = 0
+JAC_EINVAL = -1
+JAC_ENOMEM = -2
+JAC_ECUDA = -3
+JAC_ETIMEOUT = -4
+JAC_EBUDGET = -5
+JAC_ESTATE = -6
+
+JAC_F64 = 0
+JAC_F32 = 1
+
+JAC_MODE_UNFUSED = 0
+JAC_MODE_FUSED = 1
+JAC_MODE_GRAPH = 2
+JAC_MODE_PERSISTENT = 3
+JAC_MODE_GRAPH_FUSED = 4
+
+JAC_ARITH_SEQ = 0
+JAC_ARITH_EXACT = 1
+
+MODES = {
+    "unfused": JAC_MODE_UNFUSED,
+    "fused": JAC_MODE_FUSED,
+    "graph": JAC_MODE_GRAPH,
+    "persistent": JAC_MODE_PERSISTENT,
+    "graph_fused": JAC_MODE_GRAPH_FUSED,
+}
+
+
+class JacError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+class jac_info_t(ctypes.Structure):
+    _fields_ = [
+        ("dims", ctypes.c_int64 * 3),
+        ("block", ctypes.c_int32 * 3),
+        ("nblocks", ctypes.c_int32 * 3),
+        ("dtype", ctypes.c_int32),
+        ("mode", ctypes.c_int32),
+        ("arith", ctypes.c_int32),
+        ("persistent_ctas", ctypes.c_int32),
+        ("iterations", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+        ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+JAC_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+JAC_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+_SIGS = {
+    "jac_set_allocator": ([JAC_ALLOC_FN, JAC_FREE_FN, ctypes.c_void_p], ctypes.c_int),
+    "jac_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                    ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                    ctypes.c_void_p], ctypes.c_int),
+    "jac_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "jac_set_mode": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "jac_set_arith": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "jac_write": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_write_f32": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_write_device": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32], ctypes.c_int),
+    "jac_read": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_read_f32": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_read_device": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32], ctypes.c_int),
+    "jac_iterate": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
+    "jac_residual": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "jac_residual_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "jac_sync": ([ctypes.c_void_p], ctypes.c_int),
+    "jac_info": ([ctypes.c_void_p, ctypes.POINTER(jac_info_t)], ctypes.c_int),
+    "jac_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "jac_last_error": ([], ctypes.c_char_p),
+    "jac_set_wait_limit_ns": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
+    "jac_debug_withhold_progress": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libjacobi3d.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libjacobi3d.so not found at {path}; run paper_2202_11819_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str) -> int:
+    if rc != JAC_OK:
+        lib = load()
+        raise JacError(rc, where, lib.jac_last_error().decode() or lib.jac_strerror(rc).decode())
+    return rc
+
+
+def _host(a: np.ndarray, dtype) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a
+
+
+# ------------------------------------------------------------- same names as the C ABI
+
+def jac_strerror(code: int) -> str:
+    return load().jac_strerror(int(code)).decode()
+
+
+def jac_last_error() -> str:
+    return load().jac_last_error().decode()
+
+
+def jac_set_allocator(alloc, free_fn, user=None) -> None:
+    """``alloc``/``free_fn`` are JAC_ALLOC_FN / JAC_FREE_FN instances (kept
+    alive by the caller) or None to restore the default."""
+    lib = load()
+    a = alloc if alloc is not None else JAC_ALLOC_FN()
+    f = free_fn if free_fn is not None else JAC_FREE_FN()
+    _check(lib.jac_set_allocator(a, f, user), "jac_set_allocator")
+
+
+def jac_create(nx, ny, nz, bx, by, bz, dtype=JAC_F64, bc=(0.0,) * 6, stream=None) -> ctypes.c_void_p:
+    """Returns the context handle; ``stream`` is a cudaStream_t as an int (or None)."""
+    lib = load()
+    h = ctypes.c_void_p()
+    b = (ctypes.c_double * 6)(*[float(x) for x in bc])
+    _check(lib.jac_create(ctypes.byref(h), int(nx), int(ny), int(nz), int(bx), int(by), int(bz), int(dtype),
+                          b, ctypes.c_void_p(stream or 0)), "jac_create")
+    return h
+
+
+def jac_destroy(h) -> None:
+    _check(load().jac_destroy(h), "jac_destroy")
+
+
+def jac_set_mode(h, mode) -> None:
+    m = MODES[mode] if isinstance(mode, str) else int(mode)
+    _check(load().jac_set_mode(h, m), "jac_set_mode")
+
+
+def jac_set_arith(h, arith) -> None:
+    a = {"seq": JAC_ARITH_SEQ, "exact": JAC_ARITH_EXACT}[arith] if isinstance(arith, str) else int(arith)
+    _check(load().jac_set_arith(h, a), "jac_set_arith")
+
+
+def jac_write(h, host: np.ndarray) -> None:
+    a = _host(host, np.float64)
+    _check(load().jac_write(h, a.ctypes.data, a.size), "jac_write")
+
+
+def jac_write_f32(h, host: np.ndarray) -> None:
+    a = _host(host, np.float32)
+    _check(load().jac_write_f32(h, a.ctypes.data, a.size), "jac_write_f32")
+
+
+def jac_write_device(h, dev_ptr: int, n_cells: int, dtype: int) -> None:
+    _check(load().jac_write_device(h, ctypes.c_void_p(dev_ptr), int(n_cells), int(dtype)), "jac_write_device")
+
+
+def jac_read(h, out: np.ndarray) -> np.ndarray:
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(load().jac_read(h, out.ctypes.data, out.size), "jac_read")
+    return out
+
+
+def jac_read_f32(h, out: np.ndarray) -> np.ndarray:
+    if out.dtype != np.float32 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float32 array")
+    _check(load().jac_read_f32(h, out.ctypes.data, out.size), "jac_read_f32")
+    return out
+
+
+def jac_read_device(h, dev_ptr: int, n_cells: int, dtype: int) -> None:
+    _check(load().jac_read_device(h, ctypes.c_void_p(dev_ptr), int(n_cells), int(dtype)), "jac_read_device")
+
+
+def jac_iterate(h, n_iters: int) -> None:
+    _check(load().jac_iterate(h, int(n_iters)), "jac_iterate")
+
+
+def jac_residual(h) -> float:
+    r = ctypes.c_double()
+    _check(load().jac_residual(h, ctypes.byref(r)), "jac_residual")
+    return r.value
+
+
+def jac_residual_device(h, dev_ptr: int) -> None:
+    _check(load().jac_residual_device(h, ctypes.c_void_p(dev_ptr)), "jac_residual_device")
+
+
+def jac_sync(h) -> None:
+    _check(load().jac_sync(h), "jac_sync")
+
+
+def jac_info(h) -> dict:
+    info = jac_info_t()
+    _check(load().jac_info(h, ctypes.byref(info)), "jac_info")
+    return {
+        "dims": tuple(info.dims),
+        "block": tuple(info.block),
+        "nblocks": tuple(info.nblocks),
+        "dtype": info.dtype,
+        "mode": info.mode,
+        "arith": info.arith,
+        "persistent_ctas": info.persistent_ctas,
+        "iterations": info.iterations,
+        "device_bytes": info.device_bytes,
+        "kernel_launches": info.kernel_launches,
+    }
+
+
+def jac_set_wait_limit_ns(h, ns: int) -> None:
+    _check(load().jac_set_wait_limit_ns(h, int(ns)), "jac_set_wait_limit_ns")
+
+
+def jac_debug_withhold_progress(h, block: int, after_iter: int) -> None:
+    _check(load().jac_debug_withhold_progress(h, int(block), int(after_iter)), "jac_debug_withhold_progress")

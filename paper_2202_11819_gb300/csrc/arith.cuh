@@ -1,0 +1,382 @@
+// Device arithmetic of the 7-point Jacobi update and of the residual term.
+//
+// The paper (Section II-A, Figs. 1 and 3) updates every cell of a block from
+// its six face neighbours each iteration but does not print the formula; the
+// update here is the mean of the cell and its six face neighbours.
+//
+//  mean7_seq      binary64: c + xm + xp + ym + yp + zm + zp left to right,
+//                 every addition rounded to nearest even, then a correctly
+//                 rounded division by 7 (the GPU's binary64 units).
+//  mean7_seq_f32  the same in binary32.
+//  mean7_exact    the exact sum of the seven values divided by 7, rounded
+//                 once to nearest even. Computed in integer arithmetic: on
+//                 this GPU the binary64 pipe issues about two operations per
+//                 SM per clock, while the integer pipes issue 64-128, so the
+//                 exact mean in integers is both more accurate and faster than
+//                 six binary64 additions and a binary64 division.
+//  laplacian_exact xm + xp + ym + yp + zm + zp - 6c, exact, rounded once.
+//
+// Fast paths cover values of one sign whose exponents lie within 72 bits of
+// the largest and whose result is a normal number; everything else takes an
+// exact wide-accumulator path (rare: mixed signs, subnormals, huge spreads).
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+
+#if defined(__CUDACC__)
+#define JAC_HD __host__ __device__
+#else
+#define JAC_HD
+#endif
+
+namespace jac {
+
+// bit casts and leading-zero counts that also compile for the host, so the
+// integer arithmetic below can be checked on a CPU
+JAC_HD inline uint64_t dbits(double v)
+{
+#if defined(__CUDA_ARCH__)
+    return (uint64_t)__double_as_longlong(v);
+#else
+    uint64_t b;
+    memcpy(&b, &v, 8);
+    return b;
+#endif
+}
+
+JAC_HD inline double bitsd(uint64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __longlong_as_double((long long)b);
+#else
+    double v;
+    memcpy(&v, &b, 8);
+    return v;
+#endif
+}
+
+JAC_HD inline int clz64(uint64_t x)  // x != 0
+{
+#if defined(__CUDA_ARCH__)
+    return __clzll((long long)x);
+#else
+    return __builtin_clzll(x);
+#endif
+}
+
+JAC_HD inline int clz32(uint32_t x)  // x != 0
+{
+#if defined(__CUDA_ARCH__)
+    return __clz((int)x);
+#else
+    return __builtin_clz(x);
+#endif
+}
+
+JAC_HD inline int imax(int a, int b) { return a > b ? a : b; }
+
+__device__ __forceinline__ double mean7_seq(double c, double xm, double xp, double ym, double yp,
+                                            double zm, double zp)
+{
+    double s = __dadd_rn(c, xm);
+    s = __dadd_rn(s, xp);
+    s = __dadd_rn(s, ym);
+    s = __dadd_rn(s, yp);
+    s = __dadd_rn(s, zm);
+    s = __dadd_rn(s, zp);
+    return __ddiv_rn(s, 7.0);
+}
+
+__device__ __forceinline__ float mean7_seq_f32(float c, float xm, float xp, float ym, float yp,
+                                               float zm, float zp)
+{
+    float s = __fadd_rn(c, xm);
+    s = __fadd_rn(s, xp);
+    s = __fadd_rn(s, ym);
+    s = __fadd_rn(s, yp);
+    s = __fadd_rn(s, zm);
+    s = __fadd_rn(s, zp);
+    return __fdiv_rn(s, 7.0f);
+}
+
+// ------------------------------------------------------------------------
+// Wide exact accumulator (slow path). Bit q of the accumulator weighs
+// 2^(q - 1074), so every finite binary64 is an integer number of units.
+// ------------------------------------------------------------------------
+constexpr int kWideWords = 72;  // 2304 bits
+
+JAC_HD __noinline__ double exact_weighted_sum_round(const double* v, const int* w, int n,
+                                                        uint32_t divisor)
+{
+    uint32_t P[kWideWords], N[kWideWords];
+    for (int t = 0; t < kWideWords; ++t) {
+        P[t] = 0u;
+        N[t] = 0u;
+    }
+    for (int t = 0; t < n; ++t) {
+        uint64_t bits = dbits(v[t]);
+        int neg = (int)(bits >> 63);
+        int e = (int)((bits >> 52) & 0x7FF);
+        uint64_t m = bits & ((1ull << 52) - 1);
+        int pos = 0;
+        if (e != 0) {
+            m |= (1ull << 52);
+            pos = e - 1;
+        }
+        if (m == 0) continue;
+        int wt = w[t];
+        if (wt < 0) {
+            neg = !neg;
+            wt = -wt;
+        }
+        m *= (uint64_t)wt;
+        uint32_t* A = neg ? N : P;
+        int q = pos >> 5, sh = pos & 31;
+        uint64_t lo = m << sh;
+        uint64_t hi = sh ? (m >> (64 - sh)) : 0ull;
+        uint32_t part[3] = {(uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi};
+        uint64_t carry = 0;
+        for (int u = 0; u < 3; ++u) {
+            uint64_t s = (uint64_t)A[q + u] + part[u] + carry;
+            A[q + u] = (uint32_t)s;
+            carry = s >> 32;
+        }
+        for (int u = q + 3; carry && u < kWideWords; ++u) {
+            uint64_t s = (uint64_t)A[u] + carry;
+            A[u] = (uint32_t)s;
+            carry = s >> 32;
+        }
+    }
+    // magnitude and sign of P - N
+    int cmp = 0;
+    for (int t = kWideWords - 1; t >= 0 && cmp == 0; --t) {
+        if (P[t] != N[t]) cmp = P[t] > N[t] ? 1 : -1;
+    }
+    if (cmp == 0) return 0.0;
+    const uint32_t* big = cmp > 0 ? P : N;
+    const uint32_t* small = cmp > 0 ? N : P;
+    uint32_t S[kWideWords];
+    int64_t borrow = 0;
+    for (int t = 0; t < kWideWords; ++t) {
+        int64_t d = (int64_t)big[t] - (int64_t)small[t] - borrow;
+        borrow = d < 0;
+        S[t] = (uint32_t)(d + (borrow ? (1ll << 32) : 0));
+    }
+    // long division by the divisor
+    uint64_t r = 0;
+    for (int t = kWideWords - 1; t >= 0; --t) {
+        uint64_t cur = (r << 32) | S[t];
+        uint64_t qt = cur / divisor;
+        S[t] = (uint32_t)qt;
+        r = cur - qt * divisor;
+    }
+    int top = -1;
+    for (int t = kWideWords - 1; t >= 0 && top < 0; --t)
+        if (S[t]) top = t * 32 + 31 - clz32(S[t]);
+    uint64_t mant = 0;
+    int shift = 0;
+    bool up;
+    if (top < 0) {
+        up = 2 * r > divisor;
+    } else {
+        shift = top > 52 ? top - 52 : 0;
+        for (int q = top; q >= shift; --q) mant = (mant << 1) | ((S[q >> 5] >> (q & 31)) & 1u);
+        if (shift > 0) {
+            bool rbit = (S[(shift - 1) >> 5] >> ((shift - 1) & 31)) & 1u;
+            bool sticky = r != 0;
+            int below = shift - 1;
+            int wf = below >> 5;
+            for (int t = 0; t < wf && !sticky; ++t) sticky = S[t] != 0;
+            if (!sticky && (below & 31)) sticky = (S[wf] & ((1u << (below & 31)) - 1u)) != 0;
+            up = rbit && (sticky || (mant & 1));
+        } else {
+            up = (2 * r > divisor) || (2 * r == divisor && (mant & 1));
+        }
+    }
+    mant += up ? 1 : 0;
+    if (mant == 0ull) return 0.0;
+    // mant * 2^(shift - 1074): with mant < 2^52 (only when shift == 0) this is
+    // the subnormal encoding; otherwise the significand's leading bit adds one
+    // to the exponent field, so the same expression covers both.
+    uint64_t out = ((uint64_t)shift << 52) + mant;
+    if (cmp < 0) out |= (1ull << 63);
+    return bitsd(out);
+}
+
+// ------------------------------------------------------------------------
+// 128-bit helpers
+// ------------------------------------------------------------------------
+JAC_HD inline void add128(uint64_t& lo, uint64_t& hi, uint64_t alo, uint64_t ahi)
+{
+    uint64_t nlo = lo + alo;
+    hi = hi + ahi + (nlo < lo ? 1ull : 0ull);
+    lo = nlo;
+}
+
+// m (< 2^57) shifted left by s (0 <= s <= 71+) as a 128-bit value
+JAC_HD inline void shl128(uint64_t m, int s, uint64_t& lo, uint64_t& hi)
+{
+    if (s >= 64) {
+        lo = 0ull;
+        hi = m << (s - 64);
+    } else if (s == 0) {
+        lo = m;
+        hi = 0ull;
+    } else {
+        lo = m << s;
+        hi = m >> (64 - s);
+    }
+}
+
+// ------------------------------------------------------------------------
+// Correctly rounded mean of seven binary64 values.
+// Fast path: all values of one sign, each either zero or a normal number
+// within 72 binades of the largest, the largest at least 2^-959. The values
+// are placed in a 128-bit fixed-point frame whose unit is
+// 2^(emax - 1147) (the largest significand lands on bits 72..124), summed
+// exactly, and the top 64 bits are divided by 7; the remaining bits only
+// feed the sticky bit.
+// ------------------------------------------------------------------------
+JAC_HD inline double mean7_exact(double c, double xm, double xp, double ym, double yp,
+                                              double zm, double zp)
+{
+    const double v[7] = {c, xm, xp, ym, yp, zm, zp};
+    uint64_t b[7];
+    uint64_t sor = 0ull, sand = ~0ull;
+    int emax = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        b[t] = dbits(v[t]);
+        sor |= b[t];
+        sand &= b[t];
+        int e = (int)((b[t] >> 52) & 0x7FF);
+        emax = imax(emax, e);
+    }
+    const bool neg = (sand >> 63) != 0;
+    bool ok = neg || (sor >> 63) == 0;  // one sign only
+    if (emax == 0 && ok && ((sor << 1) == 0)) return 0.0;  // all zeros
+    ok = ok && emax >= 64;
+    uint64_t lo = 0ull, hi = 0ull;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        int e = (int)((b[t] >> 52) & 0x7FF);
+        uint64_t frac = b[t] & ((1ull << 52) - 1);
+        int d = emax - e;
+        if (e == 0) {
+            ok = ok && frac == 0;  // zero adds nothing; a subnormal goes the slow way
+        } else {
+            ok = ok && d <= 72;
+            uint64_t plo, phi;
+            shl128(frac | (1ull << 52), imax(72 - d, 0), plo, phi);
+            add128(lo, hi, plo, phi);
+        }
+    }
+    if (!ok) {
+        const int w[7] = {1, 1, 1, 1, 1, 1, 1};
+        return exact_weighted_sum_round(v, w, 7, 7u);
+    }
+    // S = hi:lo in [2^124, 7 * 2^125); S/7 = Q1 * 2^64 + (R1 * 2^64 + lo)/7
+    const uint64_t Q1 = hi / 7ull;
+    const uint64_t R1 = hi - Q1 * 7ull;
+    const int L = 64 - clz64(Q1);  // 58 .. 61
+    const int shift = L - 53;                  // 5 .. 8
+    uint64_t mant = Q1 >> shift;
+    const uint64_t rbit = (Q1 >> (shift - 1)) & 1ull;
+    const bool sticky = (Q1 & ((1ull << (shift - 1)) - 1ull)) != 0ull || R1 != 0ull || lo != 0ull;
+    mant += rbit & ((sticky ? 1ull : 0ull) | (mant & 1ull));
+    // value = mant * 2^(emax - 1083 + shift); biased exponent emax - 8 + shift
+    uint64_t out = ((uint64_t)(emax - 8 + shift - 1) << 52) + mant;
+    if (neg) out |= (1ull << 63);
+    return bitsd(out);
+}
+
+// ------------------------------------------------------------------------
+// Exact Laplacian term xm + xp + ym + yp + zm + zp - 6c, rounded once.
+// Fast path: all seven values >= 0, normal or zero, within 71 binades of
+// the largest (largest >= 2^-959), result normal. Frame unit 2^(emax - 1146):
+// the largest significand lands on bits 71..123, so both the neighbour sum
+// and 6c stay below 2^127 and the difference fits a signed 128-bit word.
+// ------------------------------------------------------------------------
+JAC_HD inline double laplacian_exact(double c, double xm, double xp, double ym,
+                                                  double yp, double zm, double zp)
+{
+    const double v[7] = {xm, xp, ym, yp, zm, zp, c};
+    uint64_t b[7];
+    uint64_t sor = 0ull;
+    int emax = 0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        b[t] = dbits(v[t]);
+        sor |= b[t];
+        emax = imax(emax, (int)((b[t] >> 52) & 0x7FF));
+    }
+    bool ok = (sor >> 63) == 0;
+    if (ok && (sor << 1) == 0) return 0.0;
+    ok = ok && emax >= 64;
+    uint64_t plo = 0ull, phi = 0ull, clo = 0ull, chi = 0ull;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) {
+        int e = (int)((b[t] >> 52) & 0x7FF);
+        uint64_t frac = b[t] & ((1ull << 52) - 1);
+        if (e == 0) {
+            ok = ok && frac == 0;
+        } else {
+            int d = emax - e;
+            ok = ok && d <= 71;
+            uint64_t m = frac | (1ull << 52);
+            if (t == 6) m *= 6ull;
+            uint64_t alo, ahi;
+            shl128(m, imax(71 - d, 0), alo, ahi);
+            if (t == 6) {
+                clo = alo;
+                chi = ahi;
+            } else {
+                add128(plo, phi, alo, ahi);
+            }
+        }
+    }
+    if (ok) {
+        // L = P - C (two's complement), then magnitude
+        uint64_t llo = plo - clo;
+        uint64_t lhi = phi - chi - (plo < clo ? 1ull : 0ull);
+        const bool lneg = (int64_t)lhi < 0;
+        if (lneg) {
+            llo = ~llo + 1ull;
+            lhi = ~lhi + (llo == 0ull ? 1ull : 0ull);
+        }
+        if ((llo | lhi) == 0ull) return 0.0;
+        const int t = lhi ? 127 - clz64(lhi) : 63 - clz64(llo);
+        const int bexp = t + emax - 123;  // biased exponent of the result
+        if (bexp >= 1) {
+            uint64_t mant;
+            uint64_t rbit = 0ull;
+            bool sticky = false;
+            if (t <= 52) {
+                mant = llo << (52 - t);  // exact
+            } else {
+                const int sh = t - 52;  // 1 .. 74
+                if (sh >= 64) {
+                    mant = lhi >> (sh - 64);
+                } else {
+                    mant = (llo >> sh) | (lhi << (64 - sh));
+                }
+                const int rb = sh - 1;  // round-bit position
+                rbit = rb >= 64 ? (lhi >> (rb - 64)) & 1ull : (llo >> rb) & 1ull;
+                if (rb >= 64) {
+                    sticky = llo != 0ull || (rb > 64 && (lhi & ((1ull << (rb - 64)) - 1ull)) != 0ull);
+                } else {
+                    sticky = rb > 0 && (llo & ((1ull << rb) - 1ull)) != 0ull;
+                }
+            }
+            mant += rbit & ((sticky ? 1ull : 0ull) | (mant & 1ull));
+            uint64_t out = ((uint64_t)(bexp - 1) << 52) + mant;
+            if (lneg) out |= (1ull << 63);
+            return bitsd(out);
+        }
+    }
+    const int w[7] = {1, 1, 1, 1, 1, 1, -6};
+    return exact_weighted_sum_round(v, w, 7, 1u);
+}
+
+}  // namespace jac

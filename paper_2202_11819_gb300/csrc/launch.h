@@ -1,0 +1,56 @@
+// Host-side launchers of the kernels in kernels.cu, used by the runtime in
+// runtime.cu. Internal; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "jac_common.cuh"
+
+namespace jac {
+
+struct LaunchArgs {
+    void* pool;              // block storage (both buffers)
+    const BlockDesc* desc;   // device block table
+    const TileUnit* units;   // device tile table
+    int nblocks;
+    int nunits;
+};
+
+struct PersistentArgs {
+    int p0;                  // parity read by the first iteration
+    int64_t n_iters;
+    uint32_t* done;          // per block: tiles finished (cumulative in this launch)
+    unsigned long long* work;
+    DeviceStatus* status;
+    int64_t wait_ns;
+    int hold_block;
+    int64_t hold_after;
+};
+
+int tile_width();
+int tile_height();
+int persistent_block_threads();
+const void* persistent_kernel(int dtype_f32, int arith);
+
+cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
+                                 int p, cudaStream_t s);
+cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s);
+cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int dtype_f32, int arith, int ctas,
+                              cudaStream_t s);
+cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
+                            cudaStream_t s);
+cudaError_t launch_pack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, void* send, int n,
+                             cudaStream_t s);
+cudaError_t launch_unpack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, const void* recv, int n,
+                               cudaStream_t s);
+cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void* send, const int64_t* faceoff,
+                         int maxface, cudaStream_t s);
+cudaError_t launch_unpack6(const LaunchArgs& a, int dtype_f32, int b, int p, const void* recv, const int64_t* faceoff,
+                           int maxface, cudaStream_t s);
+cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int p, cudaStream_t s);
+cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int p, cudaStream_t s);
+cudaError_t launch_init_ghosts(const LaunchArgs& a, int dtype_f32, cudaStream_t s);
+
+}  // namespace jac

@@ -1,0 +1,865 @@
+// Host runtime of libjacobi3d: the C ABI declared in include/jacobi3d.h.
+//
+// A context owns one global grid split into blocks (paper Section IV-A: the
+// grid is decomposed into cuboid blocks, more blocks than processors when
+// overdecomposed), the block table that the kernels read (per block: extents,
+// origin, the six neighbour ids or the global boundary, the offsets of its two
+// buffers), the two-buffer block storage (Section III-C), the halo send and
+// receive buffers of the unfused flow, and the per-block streams and events
+// that order that flow (Section III-A: packing, transfers and unpacking on
+// high-priority streams, the update on a low-priority stream, one set per
+// block).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "jacobi3d.h"
+#include "jac_common.cuh"
+#include "launch.h"
+
+using namespace jac;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+jac_alloc_fn g_alloc = nullptr;
+jac_free_fn g_free = nullptr;
+void* g_alloc_user = nullptr;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(JAC_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(JAC_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// An axis of n cells in ceil(n / b) blocks whose sizes differ by at most one,
+// the larger ones first.
+void split_axis(int64_t n, int32_t b, std::vector<int32_t>& size, std::vector<int32_t>& org)
+{
+    const int64_t nb = (n + b - 1) / b;
+    const int64_t base = n / nb, rem = n % nb;
+    size.resize(nb);
+    org.resize(nb);
+    int64_t o = 0;
+    for (int64_t i = 0; i < nb; ++i) {
+        size[i] = (int32_t)(base + (i < rem ? 1 : 0));
+        org[i] = (int32_t)o;
+        o += size[i];
+    }
+}
+
+}  // namespace
+
+struct jac_ctx {
+    int device = 0;
+    int64_t dims[3] = {0, 0, 0};
+    int32_t req_block[3] = {0, 0, 0};
+    int32_t nb[3] = {0, 0, 0};
+    int dtype = JAC_F64;
+    int esize = 8;
+    int mode = JAC_MODE_PERSISTENT;
+    int arith = JAC_ARITH_EXACT;
+    double bc[6] = {0, 0, 0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    jac_alloc_fn alloc = nullptr;
+    jac_free_fn free_fn = nullptr;
+    void* alloc_user = nullptr;
+    struct Alloc {
+        void* p;
+        size_t bytes;
+    };
+    std::vector<Alloc> allocs;
+    int64_t device_bytes = 0;
+
+    std::vector<BlockDesc> hdesc;
+    std::vector<TileUnit> hunits;
+    std::vector<int32_t> ntx, nty;  // tiles per block in x and y
+    BlockDesc* ddesc = nullptr;
+    TileUnit* dunits = nullptr;
+    void* pool = nullptr;
+    int parity = 0;
+    int64_t iters = 0;
+    int64_t launches = 0;
+
+    // unfused flow
+    bool halo_ready = false;
+    void* halo = nullptr;                 // send region then recv region
+    std::vector<int64_t> send_off, recv_off;  // per block*6 + face, elements
+    std::vector<int32_t> fsize;           // per block*6 + face
+    std::vector<cudaStream_t> comm, comp;
+    std::vector<cudaEvent_t> ev_sent, ev_unpacked, ev_updated;
+    cudaEvent_t ev_fork = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
+
+    // persistent
+    uint32_t* done = nullptr;
+    unsigned long long* work = nullptr;
+    DeviceStatus* status = nullptr;
+    int pctas = 0;
+    int64_t wait_ns = 2000000000LL;
+    int hold_block = -1;
+    int64_t hold_after = 0;
+
+    // residual and I/O staging
+    double* partials = nullptr;
+    double* dres = nullptr;
+    void* dense = nullptr;
+    size_t dense_bytes = 0;
+
+    LaunchArgs args() const
+    {
+        LaunchArgs a;
+        a.pool = pool;
+        a.desc = ddesc;
+        a.units = dunits;
+        a.nblocks = (int)hdesc.size();
+        a.nunits = (int)hunits.size();
+        return a;
+    }
+    int64_t ncells() const { return dims[0] * dims[1] * dims[2]; }
+};
+
+namespace {
+
+int dev_alloc(jac_ctx* h, size_t bytes, void** out)
+{
+    *out = nullptr;
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (h->alloc) {
+        p = h->alloc(bytes, (void*)h->stream, h->alloc_user);
+        if (!p) return fail(JAC_ENOMEM, "allocator hook returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    }
+    h->allocs.push_back({p, bytes});
+    h->device_bytes += (int64_t)bytes;
+    *out = p;
+    return JAC_OK;
+}
+
+void dev_free_all(jac_ctx* h)
+{
+    for (auto& a : h->allocs) {
+        if (h->free_fn) h->free_fn(a.p, a.bytes, (void*)h->stream, h->alloc_user);
+        else cudaFreeAsync(a.p, h->stream);
+    }
+    h->allocs.clear();
+    h->device_bytes = 0;
+}
+
+int check_ctx(jac_ctx* h)
+{
+    if (!h) return fail(JAC_EINVAL, "null context");
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return JAC_OK;
+}
+
+bool value_ok(double v, int dtype)
+{
+    if (!std::isfinite(v)) return false;
+    const double lim = dtype == JAC_F32 ? 3.0e38 : 1.0e300;
+    return std::fabs(v) <= lim;
+}
+
+int build_layout(jac_ctx* h)
+{
+    std::vector<int32_t> sx, ox, sy, oy, sz, oz;
+    split_axis(h->dims[0], h->req_block[0], sx, ox);
+    split_axis(h->dims[1], h->req_block[1], sy, oy);
+    split_axis(h->dims[2], h->req_block[2], sz, oz);
+    h->nb[0] = (int32_t)sx.size();
+    h->nb[1] = (int32_t)sy.size();
+    h->nb[2] = (int32_t)sz.size();
+    const int64_t nblocks = (int64_t)h->nb[0] * h->nb[1] * h->nb[2];
+    if (nblocks > (1 << 24)) return fail(JAC_EINVAL, "too many blocks (%lld)", (long long)nblocks);
+    const int OX = 128 / h->esize;
+    const int TW = tile_width(), TH = tile_height();
+    h->hdesc.resize(nblocks);
+    h->ntx.resize(nblocks);
+    h->nty.resize(nblocks);
+    int64_t off = 0;
+    for (int32_t bk = 0; bk < h->nb[2]; ++bk)
+        for (int32_t bj = 0; bj < h->nb[1]; ++bj)
+            for (int32_t bi = 0; bi < h->nb[0]; ++bi) {
+                const int64_t b = bi + (int64_t)h->nb[0] * (bj + (int64_t)h->nb[1] * bk);
+                BlockDesc& d = h->hdesc[b];
+                memset(&d, 0, sizeof d);
+                d.ext[0] = sx[bi];
+                d.ext[1] = sy[bj];
+                d.ext[2] = sz[bk];
+                d.org[0] = ox[bi];
+                d.org[1] = oy[bj];
+                d.org[2] = oz[bk];
+                const int32_t ids[3] = {bi, bj, bk};
+                for (int f = 0; f < 6; ++f) {
+                    const int a = f >> 1, dir = (f & 1) ? 1 : -1;
+                    int32_t q[3] = {bi, bj, bk};
+                    q[a] = ids[a] + dir;
+                    if (q[a] < 0 || q[a] >= h->nb[a]) d.nbr[f] = -1;
+                    else d.nbr[f] = (int32_t)(q[0] + (int64_t)h->nb[0] * (q[1] + (int64_t)h->nb[1] * q[2]));
+                    d.bc[f] = h->bc[f];
+                }
+                d.inst = 0;
+                d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
+                d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
+                const int64_t storage = d.plane * (d.ext[2] + 2);
+                d.off[0] = off;
+                d.off[1] = off + storage;
+                off += 2 * storage;
+                d.dense = 0;
+                d.gdim[0] = (int32_t)h->dims[0];
+                d.gdim[1] = (int32_t)h->dims[1];
+                d.gdim[2] = (int32_t)h->dims[2];
+                h->ntx[b] = (d.ext[0] + TW - 1) / TW;
+                h->nty[b] = (d.ext[1] + TH - 1) / TH;
+                d.ntiles = h->ntx[b] * h->nty[b];
+            }
+    h->hunits.clear();
+    for (int64_t b = 0; b < nblocks; ++b)
+        for (int32_t ty = 0; ty < h->nty[b]; ++ty)
+            for (int32_t tx = 0; tx < h->ntx[b]; ++tx) {
+                TileUnit u;
+                u.block = (int32_t)b;
+                u.x0 = (int16_t)(tx * TW);
+                u.y0 = (int16_t)(ty * TH);
+                h->hunits.push_back(u);
+            }
+    int rc;
+    if ((rc = dev_alloc(h, (size_t)off * h->esize, &h->pool))) return rc;
+    if ((rc = dev_alloc(h, nblocks * sizeof(BlockDesc), (void**)&h->ddesc))) return rc;
+    if ((rc = dev_alloc(h, h->hunits.size() * sizeof(TileUnit), (void**)&h->dunits))) return rc;
+    if ((rc = dev_alloc(h, nblocks * sizeof(uint32_t), (void**)&h->done))) return rc;
+    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
+    if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
+    if ((rc = dev_alloc(h, h->hunits.size() * sizeof(double), (void**)&h->partials))) return rc;
+    if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
+    CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), nblocks * sizeof(BlockDesc), cudaMemcpyHostToDevice, h->stream),
+       "copy block table");
+    CU(cudaMemcpyAsync(h->dunits, h->hunits.data(), h->hunits.size() * sizeof(TileUnit), cudaMemcpyHostToDevice,
+                       h->stream),
+       "copy tile table");
+    CU(cudaMemsetAsync(h->pool, 0, (size_t)off * h->esize, h->stream), "clear pool");
+    CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
+    CU(launch_init_ghosts(h->args(), h->dtype == JAC_F32, h->stream), "init ghosts");
+    h->launches += 1;
+    // the host tables must stay valid until the copies above have run
+    CU(cudaStreamSynchronize(h->stream), "create sync");
+    return JAC_OK;
+}
+
+int ensure_halo(jac_ctx* h)
+{
+    if (h->halo_ready) return JAC_OK;
+    const int64_t nblocks = (int64_t)h->hdesc.size();
+    h->send_off.assign(nblocks * 6, 0);
+    h->recv_off.assign(nblocks * 6, 0);
+    h->fsize.assign(nblocks * 6, 0);
+    int64_t total = 0;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        for (int f = 0; f < 6; ++f) {
+            const int a = f >> 1;
+            const int32_t n = a == 0 ? d.ext[1] * d.ext[2] : (a == 1 ? d.ext[0] * d.ext[2] : d.ext[0] * d.ext[1]);
+            h->fsize[b * 6 + f] = n;
+            h->send_off[b * 6 + f] = total;
+            total += round_up(n, 32);
+        }
+    }
+    for (int64_t i = 0; i < nblocks * 6; ++i) h->recv_off[i] = h->send_off[i] + total;
+    int rc;
+    if ((rc = dev_alloc(h, (size_t)(2 * total) * h->esize, &h->halo))) return rc;
+    int lo = 0, hi = 0;
+    CU(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priority range");
+    h->comm.resize(nblocks);
+    h->comp.resize(nblocks);
+    h->ev_sent.resize(nblocks);
+    h->ev_unpacked.resize(nblocks);
+    h->ev_updated.resize(nblocks);
+    for (int64_t b = 0; b < nblocks; ++b) {
+        CU(cudaStreamCreateWithPriority(&h->comm[b], cudaStreamNonBlocking, hi), "create comm stream");
+        CU(cudaStreamCreateWithPriority(&h->comp[b], cudaStreamNonBlocking, lo), "create compute stream");
+        CU(cudaEventCreateWithFlags(&h->ev_sent[b], cudaEventDisableTiming), "create event");
+        CU(cudaEventCreateWithFlags(&h->ev_unpacked[b], cudaEventDisableTiming), "create event");
+        CU(cudaEventCreateWithFlags(&h->ev_updated[b], cudaEventDisableTiming), "create event");
+    }
+    CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "create event");
+    h->halo_ready = true;
+    return JAC_OK;
+}
+
+// One iteration of the unfused flow reading buffer p (paper Fig. 1 without
+// the interior/exterior split, Fig. 3): per block pack the faces that have a
+// neighbour, copy them into the neighbours' receive buffers, then once all
+// six halos of a block have arrived unpack them and update the block.
+// `capture`: the iteration is being recorded into a graph, where the
+// cross-iteration waits are implied by the order of graph launches.
+int issue_unfused(jac_ctx* h, int p, bool capture)
+{
+    const LaunchArgs a = h->args();
+    const int f32 = h->dtype == JAC_F32;
+    const int64_t nblocks = (int64_t)h->hdesc.size();
+    char* send = (char*)h->halo;
+    const size_t es = (size_t)h->esize;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        cudaStream_t s = h->comm[b];
+        if (!capture) CU(cudaStreamWaitEvent(s, h->ev_updated[b], 0), "wait updated");
+        for (int f = 0; f < 6; ++f) {
+            if (d.nbr[f] < 0) continue;
+            CU(launch_pack_face(a, f32, (int)b, f, p, send + h->send_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
+               "pack");
+            h->launches += 1;
+        }
+        for (int f = 0; f < 6; ++f) {
+            const int n = d.nbr[f];
+            if (n < 0) continue;
+            if (!capture) CU(cudaStreamWaitEvent(s, h->ev_unpacked[n], 0), "wait unpacked");
+            CU(cudaMemcpyAsync(send + h->recv_off[(int64_t)n * 6 + opposite_face(f)] * es,
+                               send + h->send_off[b * 6 + f] * es, (size_t)h->fsize[b * 6 + f] * es,
+                               cudaMemcpyDeviceToDevice, s),
+               "halo copy");
+        }
+        CU(cudaEventRecord(h->ev_sent[b], s), "record sent");
+    }
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        cudaStream_t s = h->comm[b];
+        for (int f = 0; f < 6; ++f)
+            if (d.nbr[f] >= 0) CU(cudaStreamWaitEvent(s, h->ev_sent[d.nbr[f]], 0), "wait sent");
+        for (int f = 0; f < 6; ++f) {
+            if (d.nbr[f] < 0) continue;
+            CU(launch_unpack_face(a, f32, (int)b, f, p, send + h->recv_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
+               "unpack");
+            h->launches += 1;
+        }
+        CU(cudaEventRecord(h->ev_unpacked[b], s), "record unpacked");
+        CU(cudaStreamWaitEvent(h->comp[b], h->ev_unpacked[b], 0), "wait unpacked (update)");
+        CU(launch_stencil_block(a, f32, h->arith, (int)b, h->ntx[b], h->nty[b], p, h->comp[b]), "update");
+        h->launches += 1;
+        CU(cudaEventRecord(h->ev_updated[b], h->comp[b]), "record updated");
+    }
+    return JAC_OK;
+}
+
+int fork_blocks(jac_ctx* h)
+{
+    CU(cudaEventRecord(h->ev_fork, h->stream), "record fork");
+    for (size_t b = 0; b < h->hdesc.size(); ++b) {
+        CU(cudaStreamWaitEvent(h->comm[b], h->ev_fork, 0), "fork comm");
+        CU(cudaStreamWaitEvent(h->comp[b], h->ev_fork, 0), "fork comp");
+    }
+    return JAC_OK;
+}
+
+int join_blocks(jac_ctx* h)
+{
+    for (size_t b = 0; b < h->hdesc.size(); ++b)
+        CU(cudaStreamWaitEvent(h->stream, h->ev_updated[b], 0), "join");
+    return JAC_OK;
+}
+
+int ensure_graph(jac_ctx* h, int p)
+{
+    if (h->graph[p]) return JAC_OK;
+    int rc = ensure_halo(h);
+    if (rc) return rc;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    const int64_t before = h->launches;
+    rc = fork_blocks(h);
+    if (!rc) rc = issue_unfused(h, p, true);
+    if (!rc) rc = join_blocks(h);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->launches = before;  // recorded, not launched
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&h->graph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+    return JAC_OK;
+}
+
+// kernels per graph launch of the unfused flow
+int64_t unfused_kernels(const jac_ctx* h)
+{
+    int64_t n = 0;
+    for (const BlockDesc& d : h->hdesc) {
+        n += 1;
+        for (int f = 0; f < 6; ++f) n += d.nbr[f] >= 0 ? 2 : 0;
+    }
+    return n;
+}
+
+constexpr int kFusedGraphIters = 2;
+
+int ensure_fused_graph(jac_ctx* h, int p)
+{
+    if (h->fgraph[p]) return JAC_OK;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < kFusedGraphIters && le == cudaSuccess; ++i)
+        le = launch_fused_step(h->args(), h->dtype == JAC_F32, h->arith, (p + i) & 1, h->stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (le != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(le, "capture fused step");
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&h->fgraph[p], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "instantiate graph");
+    return JAC_OK;
+}
+
+void destroy_graphs(jac_ctx* h)
+{
+    for (int p = 0; p < 2; ++p) {
+        if (h->graph[p]) cudaGraphExecDestroy(h->graph[p]);
+        if (h->fgraph[p]) cudaGraphExecDestroy(h->fgraph[p]);
+        h->graph[p] = h->fgraph[p] = nullptr;
+    }
+}
+
+int ensure_dense(jac_ctx* h, size_t bytes)
+{
+    if (h->dense && h->dense_bytes >= bytes) return JAC_OK;
+    // the old staging buffer is released with the context
+    int rc = dev_alloc(h, bytes, &h->dense);
+    if (rc) return rc;
+    h->dense_bytes = bytes;
+    return JAC_OK;
+}
+
+int read_status(jac_ctx* h)
+{
+    DeviceStatus st;
+    CU(cudaMemcpyAsync(&st, h->status, sizeof st, cudaMemcpyDeviceToHost, h->stream), "read status");
+    CU(cudaStreamSynchronize(h->stream), "sync");
+    if (st.err != kErrNone) {
+        CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
+        CU(cudaStreamSynchronize(h->stream), "sync");
+        return fail(JAC_ETIMEOUT, "device wait gave up (block %d, iteration %d of the launch)", st.where_block,
+                    st.where_iter);
+    }
+    return JAC_OK;
+}
+
+int write_dense(jac_ctx* h, const void* src, size_t n, int src_f32, bool src_on_device)
+{
+    const size_t bytes = n * (src_f32 ? 4 : 8);
+    const void* dsrc = src;
+    if (!src_on_device) {
+        int rc = ensure_dense(h, bytes);
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(h->dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
+        dsrc = h->dense;
+    }
+    CU(launch_scatter(h->args(), h->dtype == JAC_F32, src_f32, dsrc, h->parity, h->stream), "scatter");
+    h->launches += 1;
+    h->iters = 0;
+    if (!src_on_device) CU(cudaStreamSynchronize(h->stream), "write sync");
+    return JAC_OK;
+}
+
+int read_dense(jac_ctx* h, void* dst, size_t n, int dst_f32, bool dst_on_device)
+{
+    const size_t bytes = n * (dst_f32 ? 4 : 8);
+    void* ddst = dst;
+    if (!dst_on_device) {
+        int rc = ensure_dense(h, bytes);
+        if (rc) return rc;
+        ddst = h->dense;
+    }
+    CU(launch_gather(h->args(), h->dtype == JAC_F32, dst_f32, ddst, h->parity, h->stream), "gather");
+    h->launches += 1;
+    if (!dst_on_device) {
+        CU(cudaMemcpyAsync(dst, h->dense, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
+        return read_status(h);
+    }
+    return JAC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" {
+
+const char* jac_strerror(int code)
+{
+    switch (code) {
+        case JAC_OK: return "ok";
+        case JAC_EINVAL: return "invalid argument";
+        case JAC_ENOMEM: return "out of memory";
+        case JAC_ECUDA: return "CUDA error";
+        case JAC_ETIMEOUT: return "device wait timed out";
+        case JAC_EBUDGET: return "HBM budget exceeded";
+        case JAC_ESTATE: return "invalid state";
+        default: return "unknown error";
+    }
+}
+
+const char* jac_last_error(void) { return g_last_error.c_str(); }
+
+int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void* user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(JAC_EINVAL, "alloc and free must both be set or both NULL");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = user;
+    return JAC_OK;
+}
+
+int jac_create(jac_ctx** out, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by, int32_t bz, int32_t dtype,
+               const double bc[6], void* stream)
+{
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(JAC_EINVAL, "grid dims must be >= 1");
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return fail(JAC_EINVAL, "grid dims too large");
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256)
+        return fail(JAC_EINVAL, "block dims must be in [1, 256]");
+    if (bx > nx || by > ny || bz > nz) return fail(JAC_EINVAL, "block dims must not exceed grid dims");
+    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "dtype must be JAC_F64 or JAC_F32");
+    if (!bc) return fail(JAC_EINVAL, "null boundary values");
+    for (int f = 0; f < 6; ++f)
+        if (!value_ok(bc[f], dtype)) return fail(JAC_EINVAL, "boundary value %d not finite or out of range", f);
+    jac_ctx* h = new jac_ctx();
+    h->dims[0] = nx;
+    h->dims[1] = ny;
+    h->dims[2] = nz;
+    h->req_block[0] = bx;
+    h->req_block[1] = by;
+    h->req_block[2] = bz;
+    h->dtype = dtype;
+    h->esize = dtype == JAC_F32 ? 4 : 8;
+    h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
+    for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
+    h->alloc = g_alloc;
+    h->free_fn = g_free;
+    h->alloc_user = g_alloc_user;
+    cudaError_t e;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+        e = cudaStreamGetDevice(h->stream, &h->device);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamGetDevice");
+        }
+        cudaSetDevice(h->device);
+    } else {
+        cudaGetDevice(&h->device);
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        h->own_stream = true;
+    }
+    int rc = build_layout(h);
+    if (rc) {
+        std::string msg = g_last_error;
+        jac_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
+    return JAC_OK;
+}
+
+int jac_destroy(jac_ctx* h)
+{
+    if (!h) return JAC_OK;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    for (auto s : h->comm) cudaStreamSynchronize(s);
+    for (auto s : h->comp) cudaStreamSynchronize(s);
+    destroy_graphs(h);
+    for (auto s : h->comm) cudaStreamDestroy(s);
+    for (auto s : h->comp) cudaStreamDestroy(s);
+    for (auto ev : h->ev_sent) cudaEventDestroy(ev);
+    for (auto ev : h->ev_unpacked) cudaEventDestroy(ev);
+    for (auto ev : h->ev_updated) cudaEventDestroy(ev);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    dev_free_all(h);
+    cudaStreamSynchronize(h->stream);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return JAC_OK;
+}
+
+int jac_set_mode(jac_ctx* h, int32_t mode)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (mode < JAC_MODE_UNFUSED || mode > JAC_MODE_GRAPH_FUSED) return fail(JAC_EINVAL, "unknown mode %d", mode);
+    h->mode = mode;
+    return JAC_OK;
+}
+
+int jac_set_arith(jac_ctx* h, int32_t arith)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (arith != JAC_ARITH_SEQ && arith != JAC_ARITH_EXACT) return fail(JAC_EINVAL, "unknown arith %d", arith);
+    if (h->dtype == JAC_F32 && arith != JAC_ARITH_SEQ) return fail(JAC_EINVAL, "F32 contexts use JAC_ARITH_SEQ");
+    if (arith != h->arith) destroy_graphs(h);
+    h->arith = arith;
+    return JAC_OK;
+}
+
+int jac_write(jac_ctx* h, const double* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    for (size_t i = 0; i < n_cells; ++i)
+        if (!value_ok(host[i], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", i);
+    return write_dense(h, host, n_cells, 0, false);
+}
+
+int jac_write_f32(jac_ctx* h, const float* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_write_f32 needs an F32 context");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    for (size_t i = 0; i < n_cells; ++i)
+        if (!std::isfinite(host[i])) return fail(JAC_EINVAL, "value at %zu not finite", i);
+    return write_dense(h, host, n_cells, 1, false);
+}
+
+int jac_write_device(jac_ctx* h, const void* dev, size_t n_cells, int32_t dtype)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!dev) return fail(JAC_EINVAL, "null device pointer");
+    if (dtype != h->dtype) return fail(JAC_EINVAL, "dtype must equal the context's dtype");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    return write_dense(h, dev, n_cells, dtype == JAC_F32, true);
+}
+
+int jac_read(jac_ctx* h, double* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    return read_dense(h, host, n_cells, 0, false);
+}
+
+int jac_read_f32(jac_ctx* h, float* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_read_f32 needs an F32 context");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    return read_dense(h, host, n_cells, 1, false);
+}
+
+int jac_read_device(jac_ctx* h, void* dev, size_t n_cells, int32_t dtype)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!dev) return fail(JAC_EINVAL, "null device pointer");
+    if (dtype != h->dtype && !(h->dtype == JAC_F32 && dtype == JAC_F64))
+        return fail(JAC_EINVAL, "dtype must be the context's dtype (or F64 for an F32 context)");
+    if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
+    return read_dense(h, dev, n_cells, dtype == JAC_F32, true);
+}
+
+int jac_iterate(jac_ctx* h, int64_t n)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (n < 0) return fail(JAC_EINVAL, "n_iters must be >= 0");
+    if (n == 0) return JAC_OK;
+    const int f32 = h->dtype == JAC_F32;
+    switch (h->mode) {
+        case JAC_MODE_FUSED:
+            for (int64_t i = 0; i < n; ++i) {
+                CU(launch_fused_step(h->args(), f32, h->arith, h->parity, h->stream), "fused step");
+                h->launches += 1;
+                h->parity ^= 1;
+            }
+            break;
+        case JAC_MODE_GRAPH_FUSED: {
+            int64_t i = 0;
+            for (; i + kFusedGraphIters <= n; i += kFusedGraphIters) {
+                if ((rc = ensure_fused_graph(h, h->parity))) return rc;
+                CU(cudaGraphLaunch(h->fgraph[h->parity], h->stream), "graph launch");
+                h->launches += kFusedGraphIters;
+                if (kFusedGraphIters & 1) h->parity ^= 1;
+            }
+            for (; i < n; ++i) {
+                CU(launch_fused_step(h->args(), f32, h->arith, h->parity, h->stream), "fused step");
+                h->launches += 1;
+                h->parity ^= 1;
+            }
+            break;
+        }
+        case JAC_MODE_UNFUSED:
+            if ((rc = ensure_halo(h))) return rc;
+            if ((rc = fork_blocks(h))) return rc;
+            for (int64_t i = 0; i < n; ++i) {
+                if ((rc = issue_unfused(h, h->parity, false))) return rc;
+                h->parity ^= 1;
+            }
+            if ((rc = join_blocks(h))) return rc;
+            break;
+        case JAC_MODE_GRAPH:
+            for (int64_t i = 0; i < n; ++i) {
+                if ((rc = ensure_graph(h, h->parity))) return rc;
+                CU(cudaGraphLaunch(h->graph[h->parity], h->stream), "graph launch");
+                h->launches += unfused_kernels(h);
+                h->parity ^= 1;
+            }
+            break;
+        case JAC_MODE_PERSISTENT: {
+            if (h->pctas == 0) {
+                int per_sm = 0, sms = 0;
+                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
+                                                                 persistent_block_threads(), 0),
+                   "occupancy");
+                CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+                h->pctas = std::max(1, std::min(per_sm * sms, (int)h->hunits.size()));
+            }
+            // counters are 32-bit: at most 2^32 / max tiles per block iterations per launch
+            int32_t maxt = 1;
+            for (const BlockDesc& d : h->hdesc) maxt = std::max(maxt, d.ntiles);
+            const int64_t chunk = std::max<int64_t>(1, (int64_t)(0xFFFFFFF0u / (uint32_t)maxt) - 1);
+            for (int64_t done_it = 0; done_it < n;) {
+                const int64_t m = std::min(chunk, n - done_it);
+                CU(cudaMemsetAsync(h->done, 0, h->hdesc.size() * sizeof(uint32_t), h->stream), "clear counters");
+                CU(cudaMemsetAsync(h->work, 0, sizeof(unsigned long long), h->stream), "clear work");
+                CU(cudaMemsetAsync(&h->status->abort, 0, sizeof(int32_t), h->stream), "clear abort");
+                PersistentArgs q;
+                q.p0 = h->parity;
+                q.n_iters = m;
+                q.done = h->done;
+                q.work = h->work;
+                q.status = h->status;
+                q.wait_ns = h->wait_ns;
+                q.hold_block = h->hold_block;
+                q.hold_after = h->hold_after;
+                CU(launch_persistent(h->args(), q, f32, h->arith, h->pctas, h->stream), "persistent");
+                h->launches += 1;
+                if (m & 1) h->parity ^= 1;
+                done_it += m;
+            }
+            break;
+        }
+        default:
+            return fail(JAC_ESTATE, "bad mode");
+    }
+    h->iters += n;
+    return JAC_OK;
+}
+
+int jac_residual_device(jac_ctx* h, double* dev_out)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
+    CU(launch_residual(h->args(), h->dtype == JAC_F32, h->parity, h->partials, dev_out, h->stream), "residual");
+    h->launches += 2;
+    return JAC_OK;
+}
+
+int jac_residual(jac_ctx* h, double* out)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    if ((rc = jac_residual_device(h, h->dres))) return rc;
+    CU(cudaMemcpyAsync(out, h->dres, sizeof(double), cudaMemcpyDeviceToHost, h->stream), "copy residual");
+    return read_status(h);
+}
+
+int jac_sync(jac_ctx* h)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    return read_status(h);
+}
+
+int jac_info(jac_ctx* h, jac_info_t* info)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!info) return fail(JAC_EINVAL, "null info pointer");
+    memset(info, 0, sizeof *info);
+    for (int a = 0; a < 3; ++a) {
+        info->dims[a] = h->dims[a];
+        info->block[a] = h->req_block[a];
+        info->nblocks[a] = h->nb[a];
+    }
+    info->dtype = h->dtype;
+    info->mode = h->mode;
+    info->arith = h->arith;
+    info->persistent_ctas = h->pctas;
+    info->iterations = h->iters;
+    info->device_bytes = h->device_bytes;
+    info->kernel_launches = h->launches;
+    return JAC_OK;
+}
+
+int jac_set_wait_limit_ns(jac_ctx* h, int64_t ns)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (ns < 1000) return fail(JAC_EINVAL, "wait limit must be >= 1000 ns");
+    h->wait_ns = ns;
+    return JAC_OK;
+}
+
+int jac_debug_withhold_progress(jac_ctx* h, int32_t block, int64_t after_iter)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (block >= (int32_t)h->hdesc.size()) return fail(JAC_EINVAL, "block out of range");
+    h->hold_block = block < 0 ? -1 : block;
+    h->hold_after = after_iter;
+    return JAC_OK;
+}
+
+}  // extern "C"

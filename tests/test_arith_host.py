@@ -1,0 +1,107 @@
+"""The CUDA path's integer arithmetic (correctly rounded mean of seven
+binary64 values, exact Laplacian term), compiled for the host, against the
+oracle's wide-accumulator arithmetic and exact rationals. Covers both the
+fast 128-bit-frame path and the wide fallback."""
+
+import ctypes
+import os
+import subprocess
+import tempfile
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2202_11819_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def host_lib():
+    d = tempfile.mkdtemp()
+    out = os.path.join(d, "libarith_host.so")
+    nvcc = "nvcc" if subprocess.run(["which", "nvcc"], capture_output=True).returncode == 0 else "/usr/local/cuda/bin/nvcc"
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-shared", "-Xcompiler", "-fPIC", "-I", CSRC,
+                    os.path.join(HERE, "host_arith", "arith_host.cu"), "-o", out], check=True, capture_output=True)
+    lib = ctypes.CDLL(out)
+    lib.host_mean7_exact.argtypes = [ctypes.c_void_p]
+    lib.host_mean7_exact.restype = ctypes.c_double
+    lib.host_laplacian_exact.argtypes = [ctypes.c_double, ctypes.c_void_p]
+    lib.host_laplacian_exact.restype = ctypes.c_double
+    return lib
+
+
+def mean_cases(rng):
+    cases = [
+        [1.0] * 7,
+        [1.0, 0, 0, 0, 0, 0, 0],
+        [0.0] * 7,
+        [-0.0] * 7,
+        [-0.0, 0.0, 0, 0, 0, 0, 0],
+        [1.0, 2.0 ** -60, 0, 0, 0, 0, 0],
+        [1.0, 2.0 ** -72, 0, 0, 0, 0, 0],
+        [1.0, 2.0 ** -73, 0, 0, 0, 0, 0],
+        [1.0, -1.0, 2.0 ** -1074, 0, 0, 0, 0],
+        [2.0 ** -1074] * 7,
+        [2.0 ** -1022] * 7,
+        [2.0 ** -960] * 7,
+        [2.0 ** -959, 1e-300, 0, 0, 0, 0, 0],
+        [1e300] * 7,
+        [-0.5, -0.25, -0.125, 0.0, -1.0, -2.0, -4.0],
+        [7.0, 0, 0, 0, 0, 0, 0],
+        [1.0 + 2.0 ** -52] * 7,
+        [3.5 * 2.0 ** -50, 0, 0, 0, 0, 0, 0],
+    ]
+    for _ in range(3000):
+        cases.append(list(rng.random(7)))
+    for _ in range(3000):
+        e = rng.integers(-80, 10, size=7)
+        cases.append(list(rng.random(7) * 2.0 ** e))
+    for _ in range(1000):
+        e = rng.integers(-5, 5, size=7)
+        s = rng.choice([-1.0, 1.0], size=7)
+        cases.append(list(s * rng.random(7) * 2.0 ** e))
+    for _ in range(1000):  # one sign, all negative
+        cases.append(list(-rng.random(7)))
+    # exact ties and near-ties at the rounding point: multiples of small units
+    for _ in range(2000):
+        cases.append(list(rng.integers(0, 16, size=7) * 2.0 ** -3))
+    return cases
+
+
+def test_mean7_exact_host_matches_oracle_and_rationals(host_lib):
+    rng = np.random.default_rng(2024)
+    for v in mean_cases(rng):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        got = host_lib.host_mean7_exact(a.ctypes.data)
+        want = oracle.exact_mean7(a)
+        assert np.float64(got).tobytes() == np.float64(want).tobytes(), v
+    for v in mean_cases(rng)[:500]:
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        exact = float(sum(Fraction(float(x)) for x in a) / 7)
+        assert host_lib.host_mean7_exact(a.ctypes.data) == exact
+
+
+def test_laplacian_exact_host_matches_oracle(host_lib):
+    rng = np.random.default_rng(99)
+    cases = [(0.3, [0.3] * 6), (1.0, [0.0] * 6), (0.0, [1.0] * 6), (2.0 ** -1070, [0.0] * 6),
+             (1.0, [1.0, 1.0, 1.0, 1.0, 1.0, 1.0 + 2.0 ** -52]), (-1.0, [2.0] * 6)]
+    for _ in range(4000):
+        c = float(rng.random())
+        nb = list(rng.random(6))
+        cases.append((c, nb))
+    for _ in range(2000):
+        c = float(rng.random() * 2.0 ** int(rng.integers(-75, 3)))
+        nb = list(rng.random(6) * 2.0 ** rng.integers(-75, 3, size=6))
+        cases.append((c, nb))
+    for _ in range(1000):  # near cancellation: neighbours average to c
+        c = float(rng.random())
+        nb = [c + float(x) * 2.0 ** -50 for x in rng.integers(-3, 4, size=6)]
+        cases.append((c, nb))
+    for c, nb in cases:
+        a = np.ascontiguousarray(nb, dtype=np.float64)
+        got = host_lib.host_laplacian_exact(c, a.ctypes.data)
+        want = oracle.exact_laplacian(c, a)
+        assert np.float64(got).tobytes() == np.float64(want).tobytes(), (c, nb)
