@@ -115,8 +115,12 @@ struct jac_ctx {
     std::vector<int64_t> send_off, recv_off;  // per block*6 + face, elements
     std::vector<int32_t> fsize;           // per block*6 + face
     std::vector<cudaStream_t> comm, comp;
-    std::vector<cudaEvent_t> ev_sent, ev_unpacked, ev_updated;
-    cudaEvent_t ev_fork = nullptr;
+    // Two event sets: one for eager issue and one used only while capturing a
+    // graph (a wait may not name an event whose last record was captured).
+    struct Events {
+        std::vector<cudaEvent_t> sent, unpacked, updated;
+        cudaEvent_t fork = nullptr;
+    } ev[2];
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
 
@@ -304,17 +308,21 @@ int ensure_halo(jac_ctx* h)
     CU(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priority range");
     h->comm.resize(nblocks);
     h->comp.resize(nblocks);
-    h->ev_sent.resize(nblocks);
-    h->ev_unpacked.resize(nblocks);
-    h->ev_updated.resize(nblocks);
     for (int64_t b = 0; b < nblocks; ++b) {
         CU(cudaStreamCreateWithPriority(&h->comm[b], cudaStreamNonBlocking, hi), "create comm stream");
         CU(cudaStreamCreateWithPriority(&h->comp[b], cudaStreamNonBlocking, lo), "create compute stream");
-        CU(cudaEventCreateWithFlags(&h->ev_sent[b], cudaEventDisableTiming), "create event");
-        CU(cudaEventCreateWithFlags(&h->ev_unpacked[b], cudaEventDisableTiming), "create event");
-        CU(cudaEventCreateWithFlags(&h->ev_updated[b], cudaEventDisableTiming), "create event");
     }
-    CU(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "create event");
+    for (auto& E : h->ev) {
+        E.sent.resize(nblocks);
+        E.unpacked.resize(nblocks);
+        E.updated.resize(nblocks);
+        for (int64_t b = 0; b < nblocks; ++b) {
+            CU(cudaEventCreateWithFlags(&E.sent[b], cudaEventDisableTiming), "create event");
+            CU(cudaEventCreateWithFlags(&E.unpacked[b], cudaEventDisableTiming), "create event");
+            CU(cudaEventCreateWithFlags(&E.updated[b], cudaEventDisableTiming), "create event");
+        }
+        CU(cudaEventCreateWithFlags(&E.fork, cudaEventDisableTiming), "create event");
+    }
     h->halo_ready = true;
     return JAC_OK;
 }
@@ -332,10 +340,11 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
     const int64_t nblocks = (int64_t)h->hdesc.size();
     char* send = (char*)h->halo;
     const size_t es = (size_t)h->esize;
+    auto& E = h->ev[capture ? 1 : 0];
     for (int64_t b = 0; b < nblocks; ++b) {
         const BlockDesc& d = h->hdesc[b];
         cudaStream_t s = h->comm[b];
-        if (!capture) CU(cudaStreamWaitEvent(s, h->ev_updated[b], 0), "wait updated");
+        if (!capture) CU(cudaStreamWaitEvent(s, E.updated[b], 0), "wait updated");
         for (int f = 0; f < 6; ++f) {
             if (d.nbr[f] < 0) continue;
             CU(launch_pack_face(a, f32, (int)b, f, p, send + h->send_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
@@ -345,48 +354,51 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
         for (int f = 0; f < 6; ++f) {
             const int n = d.nbr[f];
             if (n < 0) continue;
-            if (!capture) CU(cudaStreamWaitEvent(s, h->ev_unpacked[n], 0), "wait unpacked");
+            if (!capture) CU(cudaStreamWaitEvent(s, E.unpacked[n], 0), "wait unpacked");
             CU(cudaMemcpyAsync(send + h->recv_off[(int64_t)n * 6 + opposite_face(f)] * es,
                                send + h->send_off[b * 6 + f] * es, (size_t)h->fsize[b * 6 + f] * es,
                                cudaMemcpyDeviceToDevice, s),
                "halo copy");
         }
-        CU(cudaEventRecord(h->ev_sent[b], s), "record sent");
+        CU(cudaEventRecord(E.sent[b], s), "record sent");
     }
     for (int64_t b = 0; b < nblocks; ++b) {
         const BlockDesc& d = h->hdesc[b];
         cudaStream_t s = h->comm[b];
         for (int f = 0; f < 6; ++f)
-            if (d.nbr[f] >= 0) CU(cudaStreamWaitEvent(s, h->ev_sent[d.nbr[f]], 0), "wait sent");
+            if (d.nbr[f] >= 0) CU(cudaStreamWaitEvent(s, E.sent[d.nbr[f]], 0), "wait sent");
         for (int f = 0; f < 6; ++f) {
             if (d.nbr[f] < 0) continue;
             CU(launch_unpack_face(a, f32, (int)b, f, p, send + h->recv_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
                "unpack");
             h->launches += 1;
         }
-        CU(cudaEventRecord(h->ev_unpacked[b], s), "record unpacked");
-        CU(cudaStreamWaitEvent(h->comp[b], h->ev_unpacked[b], 0), "wait unpacked (update)");
+        CU(cudaEventRecord(E.unpacked[b], s), "record unpacked");
+        CU(cudaStreamWaitEvent(h->comp[b], E.unpacked[b], 0), "wait unpacked (update)");
         CU(launch_stencil_block(a, f32, h->arith, (int)b, h->ntx[b], h->nty[b], p, h->comp[b]), "update");
         h->launches += 1;
-        CU(cudaEventRecord(h->ev_updated[b], h->comp[b]), "record updated");
+        CU(cudaEventRecord(E.updated[b], h->comp[b]), "record updated");
     }
     return JAC_OK;
 }
 
-int fork_blocks(jac_ctx* h)
+int fork_blocks(jac_ctx* h, bool capture)
 {
-    CU(cudaEventRecord(h->ev_fork, h->stream), "record fork");
+    auto& E = h->ev[capture ? 1 : 0];
+    CU(cudaEventRecord(E.fork, h->stream), "record fork");
     for (size_t b = 0; b < h->hdesc.size(); ++b) {
-        CU(cudaStreamWaitEvent(h->comm[b], h->ev_fork, 0), "fork comm");
-        CU(cudaStreamWaitEvent(h->comp[b], h->ev_fork, 0), "fork comp");
+        CU(cudaStreamWaitEvent(h->comm[b], E.fork, 0), "fork comm");
+        CU(cudaStreamWaitEvent(h->comp[b], E.fork, 0), "fork comp");
     }
     return JAC_OK;
 }
 
-int join_blocks(jac_ctx* h)
+// The main stream waits for every block's last update, which follows all of
+// that block's packs, copies and unpacks of the iteration.
+int join_blocks(jac_ctx* h, bool capture)
 {
-    for (size_t b = 0; b < h->hdesc.size(); ++b)
-        CU(cudaStreamWaitEvent(h->stream, h->ev_updated[b], 0), "join");
+    auto& E = h->ev[capture ? 1 : 0];
+    for (size_t b = 0; b < h->hdesc.size(); ++b) CU(cudaStreamWaitEvent(h->stream, E.updated[b], 0), "join");
     return JAC_OK;
 }
 
@@ -397,9 +409,9 @@ int ensure_graph(jac_ctx* h, int p)
     if (rc) return rc;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     const int64_t before = h->launches;
-    rc = fork_blocks(h);
+    rc = fork_blocks(h, true);
     if (!rc) rc = issue_unfused(h, p, true);
-    if (!rc) rc = join_blocks(h);
+    if (!rc) rc = join_blocks(h, true);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->launches = before;  // recorded, not launched
@@ -613,10 +625,12 @@ int jac_destroy(jac_ctx* h)
     destroy_graphs(h);
     for (auto s : h->comm) cudaStreamDestroy(s);
     for (auto s : h->comp) cudaStreamDestroy(s);
-    for (auto ev : h->ev_sent) cudaEventDestroy(ev);
-    for (auto ev : h->ev_unpacked) cudaEventDestroy(ev);
-    for (auto ev : h->ev_updated) cudaEventDestroy(ev);
-    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (auto& E : h->ev) {
+        for (auto e : E.sent) cudaEventDestroy(e);
+        for (auto e : E.unpacked) cudaEventDestroy(e);
+        for (auto e : E.updated) cudaEventDestroy(e);
+        if (E.fork) cudaEventDestroy(E.fork);
+    }
     dev_free_all(h);
     cudaStreamSynchronize(h->stream);
     if (h->own_stream) cudaStreamDestroy(h->stream);
@@ -739,12 +753,12 @@ int jac_iterate(jac_ctx* h, int64_t n)
         }
         case JAC_MODE_UNFUSED:
             if ((rc = ensure_halo(h))) return rc;
-            if ((rc = fork_blocks(h))) return rc;
+            if ((rc = fork_blocks(h, false))) return rc;
             for (int64_t i = 0; i < n; ++i) {
                 if ((rc = issue_unfused(h, h->parity, false))) return rc;
                 h->parity ^= 1;
             }
-            if ((rc = join_blocks(h))) return rc;
+            if ((rc = join_blocks(h, false))) return rc;
             break;
         case JAC_MODE_GRAPH:
             for (int64_t i = 0; i < n; ++i) {
