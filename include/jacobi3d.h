@@ -209,6 +209,33 @@ int jac_sync(jac_ctx *h);
 /* Describe the context. */
 int jac_info(jac_ctx *h, jac_info_t *info);
 
+/* Residual rho of a dense grid held by the caller, computed without
+ * allocating memory. The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc (or any allocator) where they need
+ * the residual, e.g. inside a step of a framework that forbids allocation,
+ * while a memory pool is locked, or from a callback that must not block on
+ * the allocator.
+ *   u        device pointer: nx*ny*nz values of `dtype` (JAC_F64 or
+ *            JAC_F32), x fastest, owned by the caller.
+ *   bc       6 finite Dirichlet values (-x, +x, -y, +y, -z, +z); binary32
+ *            grids use them rounded to binary32.
+ *   out      device pointer to one double, receives rho (same definition
+ *            as jac_residual).
+ *   stream   cudaStream_t (NULL: legacy default stream); stream-ordered,
+ *            no host sync.
+ * Scratch: the per-CTA partial sums live in a fixed 65536-double (512 KiB)
+ * static device array of the library, held by every GPU that loads the
+ * library until the process exits. A grid needing more than 65536 partials
+ * (ceil(nx/32) * ceil(ny/8) > 65536) is rejected with JAC_EINVAL. The call
+ * makes no cudaMalloc/cudaFree or other allocation. Its first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the array,
+ * which keeps the last call's contents: calls whose kernels overlap on the
+ * GPU race and must be serialised by the caller.
+ * Returns JAC_EINVAL on bad arguments or sizes, JAC_ECUDA on CUDA errors. */
+int jac_residual_dense_noalloc(const void *u, int32_t dtype, int64_t nx, int64_t ny, int64_t nz,
+                               const double bc[6], double *out, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Diagnostics                                                         */
 /* ------------------------------------------------------------------ */

@@ -93,6 +93,9 @@ _SIGS = {
     "jac_last_error": ([], ctypes.c_char_p),
     "jac_set_wait_limit_ns": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
     "jac_debug_withhold_progress": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+    "jac_residual_dense_noalloc": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+                                   ctypes.c_int),
 }
 
 
@@ -246,3 +249,14 @@ def jac_set_wait_limit_ns(h, ns: int) -> None:
 
 def jac_debug_withhold_progress(h, block: int, after_iter: int) -> None:
     _check(load().jac_debug_withhold_progress(h, int(block), int(after_iter)), "jac_debug_withhold_progress")
+
+
+def jac_residual_dense_noalloc(dev_u: int, dtype: int, nx: int, ny: int, nz: int, bc, dev_out: int,
+                               stream=None) -> None:
+    """Residual of a caller-held dense device grid into the device double at
+    ``dev_out``; allocates nothing (scratch is a fixed static device array)."""
+    b = (ctypes.c_double * 6)(*[float(x) for x in bc])
+    rc = load().jac_residual_dense_noalloc(ctypes.c_void_p(dev_u), int(dtype), int(nx), int(ny), int(nz), b,
+                                           ctypes.c_void_p(dev_out), ctypes.c_void_p(stream or 0))
+    if rc != JAC_OK:
+        raise JacError(rc, "jac_residual_dense_noalloc", jac_strerror(rc))

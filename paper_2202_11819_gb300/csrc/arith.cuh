@@ -106,7 +106,7 @@ __device__ __forceinline__ float mean7_seq_f32(float c, float xm, float xp, floa
 // ------------------------------------------------------------------------
 constexpr int kWideWords = 72;  // 2304 bits
 
-JAC_HD __noinline__ double exact_weighted_sum_round(const double* v, const int* w, int n,
+JAC_HD inline __noinline__ double exact_weighted_sum_round(const double* v, const int* w, int n,
                                                         uint32_t divisor)
 {
     uint32_t P[kWideWords], N[kWideWords];
