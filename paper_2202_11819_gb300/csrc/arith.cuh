@@ -379,4 +379,193 @@ JAC_HD inline double laplacian_exact(double c, double xm, double xp, double ym,
     return exact_weighted_sum_round(v, w, 7, 1u);
 }
 
+// ========================================================================
+// Grid-frame arithmetic.
+//
+// One fixed-point frame per grid: with E the largest exponent field of any
+// value of the grid and its boundary (the maximum principle keeps every
+// later iterate at or below that maximum), the frame's unit is
+// 2^(Eref - 1106), Eref = E + 1. A normal binary64 value v >= 0 with
+// exponent field e is (1.f) 2^(e-1023) = m * 2^(e-1075), m < 2^53, i.e.
+// m << s units with s = e - Eref + 31 in [0, 31] when e >= Eref - 31. That
+// fits 96 bits as three 32-bit words (w < 2^84). Each cell converts only its
+// own value; the seven-term sum is then exact in 96-bit integer arithmetic
+// (< 2^87). A value outside the frame (negative, subnormal, or more than 31
+// binades below the maximum) becomes a marker 2^93, which a sum detects as
+// its top word reaching 2^29; such a cell takes the exact per-cell path.
+// ========================================================================
+namespace frame {
+
+constexpr uint32_t kMarker = 1u << 29;  // w2 of an unrepresentable value (2^93)
+
+struct W96 {
+    uint32_t w0, w1, w2, w3;  // w3 is padding (16-byte slots in shared memory)
+};
+
+JAC_HD inline uint32_t fsl(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) << s) >> 32, 0 <= s <= 31
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_l(lo, hi, s);
+#else
+    return (uint32_t)(((((uint64_t)hi << 32) | lo) << s) >> 32);
+#endif
+}
+
+JAC_HD inline uint32_t fsr(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) >> s) & 0xffffffff, 0 <= s <= 31
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_r(lo, hi, s);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> s);
+#endif
+}
+
+JAC_HD inline uint64_t umulhi64(uint64_t a, uint64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+JAC_HD inline W96 of(double v, int eref)
+{
+    const uint64_t b = dbits(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const int e = (int)((hi >> 20) & 0x7FF);
+    const int s = e - eref + 31;
+    const bool ok = (hi >> 31) == 0 && e != 0 && (unsigned)s <= 31u;
+    const bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0u;
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    const int sc = s & 31;
+    W96 w;
+    w.w0 = ok ? (lo << sc) : 0u;
+    w.w1 = ok ? fsl(lo, mh, sc) : 0u;
+    w.w2 = ok ? fsl(mh, 0u, sc) : (zero ? 0u : kMarker);
+    w.w3 = 0u;
+    return w;
+}
+
+JAC_HD inline W96 add(W96 a, const W96& b)
+{
+#if defined(__CUDA_ARCH__)
+    asm("add.cc.u32 %0, %0, %3;\n\t"
+        "addc.cc.u32 %1, %1, %4;\n\t"
+        "addc.u32 %2, %2, %5;"
+        : "+r"(a.w0), "+r"(a.w1), "+r"(a.w2)
+        : "r"(b.w0), "r"(b.w1), "r"(b.w2));
+    return a;
+#else
+    const uint64_t l = (uint64_t)a.w0 + b.w0;
+    const uint64_t m = (uint64_t)a.w1 + b.w1 + (l >> 32);
+    a.w0 = (uint32_t)l;
+    a.w1 = (uint32_t)m;
+    a.w2 = a.w2 + b.w2 + (uint32_t)(m >> 32);
+    return a;
+#endif
+}
+
+// Correctly rounded conversion of an integer below 2^63 to binary64.
+JAC_HD inline double u64_to_double_rn(uint64_t q)
+{
+#if defined(__CUDA_ARCH__)
+    return __ull2double_rn(q);
+#else
+    return (double)(int64_t)q;
+#endif
+}
+
+// RN((c + xm + xp + ym + yp + zm + zp) / 7) from frame values. Returns false
+// when the exact per-cell path must be taken (a marker, or a subnormal
+// result).
+JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& ym, const W96& yp, const W96& zm,
+                         const W96& zp, int eref, double& out)
+{
+    W96 S = add(add(add(c, xm), add(xp, ym)), add(add(yp, zm), zp));
+    if (S.w2 >= kMarker) return false;
+    uint64_t N;
+    bool st0;
+    int L;
+    if (S.w2 != 0u) {
+        const int r = 32 - clz32(S.w2);  // 1 .. 22
+        N = ((uint64_t)fsr(S.w1, S.w2, r) << 32) | fsr(S.w0, S.w1, r);
+        st0 = (S.w0 << (32 - r)) != 0u;
+        L = 64 + r;
+    } else {
+        const uint64_t s64 = ((uint64_t)S.w1 << 32) | S.w0;
+        if (s64 == 0ull) {
+            out = 0.0;
+            return true;
+        }
+        const int lz = clz64(s64);
+        N = s64 << lz;
+        st0 = false;
+        L = 64 - lz;
+    }
+    // N in [2^63, 2^64): Q = N / 7 (multiply-high by the magic 2^66/7 with
+    // the usual add-back), Q in [2^60.2, 2^61.2)
+    const uint64_t t = umulhi64(N, 0x2492492492492493ull);
+    const uint64_t Q = (((N - t) >> 1) + t) >> 2;
+    const uint64_t R = N - Q * 7ull;
+    // Q has 61 or 62 bits and is rounded to 53: its last bit lies below the
+    // rounding position, so OR-ing the sticky information (nonzero remainder
+    // or bits dropped from S) into it lets one correctly rounded conversion
+    // round the exact quotient Q + fraction.
+    const uint64_t qj = Q | ((R != 0ull || st0) ? 1ull : 0ull);
+    const double dq = u64_to_double_rn(qj);
+    // S/7 = (Q + fraction) * 2^(L-64) units of 2^(eref-1106): add that scale
+    // to the exponent field of dq (a normal number near 2^61)
+    const int biased = (int)(dbits(dq) >> 52) + L - 64 + eref - 1106;
+    if (biased < 1) return false;
+    out = bitsd(dbits(dq) + ((uint64_t)(int64_t)(L - 64 + eref - 1106) << 52));
+    return true;
+}
+
+// RN(xm + xp + ym + yp + zm + zp - 6c) from frame values. Returns false for
+// the exact per-cell path (a marker, or a subnormal result).
+JAC_HD inline bool laplacian(const W96& c, const W96& xm, const W96& xp, const W96& ym, const W96& yp,
+                             const W96& zm, const W96& zp, int eref, double& out)
+{
+    const W96 S = add(add(add(c, xm), add(xp, ym)), add(add(yp, zm), zp));
+    if (S.w2 >= kMarker) return false;
+    // T = 7c = 8c - c; L = S - T, two's complement over 96 bits
+    const uint64_t c64 = ((uint64_t)c.w1 << 32) | c.w0;
+    const uint64_t c8lo = c64 << 3;
+    const uint32_t c8hi = (c.w2 << 3) | (c.w1 >> 29);
+    const uint64_t tlo = c8lo - c64;
+    const uint32_t thi = c8hi - c.w2 - (c8lo < c64 ? 1u : 0u);
+    const uint64_t slo = ((uint64_t)S.w1 << 32) | S.w0;
+    uint64_t llo = slo - tlo;
+    uint32_t lhi = S.w2 - thi - (slo < tlo ? 1u : 0u);
+    const bool neg = (lhi >> 31) != 0u;
+    if (neg) {
+        llo = ~llo + 1ull;
+        lhi = ~lhi + (llo == 0ull ? 1u : 0u);
+    }
+    if ((llo | lhi) == 0ull) {
+        out = 0.0;
+        return true;
+    }
+    const int t = lhi ? 64 + 31 - clz32(lhi) : 63 - clz64(llo);  // top bit index
+    const int biased = t + eref - 83;
+    if (biased < 1) return false;
+    uint64_t mant;
+    if (t <= 52) {
+        mant = llo << (52 - t);
+    } else {
+        const int sh = t - 52;  // 1 .. 34
+        mant = (llo >> sh) | ((uint64_t)lhi << (64 - sh));
+        const uint64_t rbit = (llo >> (sh - 1)) & 1ull;
+        const bool sticky = (llo & ((1ull << (sh - 1)) - 1ull)) != 0ull;
+        mant += rbit & ((sticky ? 1ull : 0ull) | (mant & 1ull));
+    }
+    uint64_t out_bits = ((uint64_t)(biased - 1) << 52) + mant;
+    if (neg) out_bits |= (1ull << 63);
+    out = bitsd(out_bits);
+    return true;
+}
+
+}  // namespace frame
+
 }  // namespace jac

@@ -40,6 +40,8 @@ struct BlockDesc {
     int32_t gdim[3];  // the instance's global dims
     int32_t ntiles;   // work units (tiles) of this block
     double bc[6];     // Dirichlet value per face (used where nbr[f] < 0)
+    float bcf[6];     // the same rounded to binary32 (binary32 grids)
+    int32_t pad;
 };
 
 // One unit of fused / persistent work: a column tile of one block.

@@ -32,11 +32,12 @@
 
 namespace jac {
 
-// Tile of the z-marching update: 32 x 8 threads, each thread owning VX
-// columns spaced 32 apart, so one tile covers 64 x 8 columns of a block.
+// Tile of the z-marching update: 32 x 16 threads, one column each, so one
+// tile covers 32 x 16 columns of a block (a 128-byte-aligned 256-byte row
+// segment per warp for binary64).
 constexpr int kTX = 32;
-constexpr int kTY = 8;
-constexpr int kVX = 2;
+constexpr int kTY = 16;
+constexpr int kVX = 1;
 constexpr int kTW = kTX * kVX;
 constexpr int kSW = kTW + 2;  // shared row with one halo cell on each side
 constexpr int kSmemCells = (kTY + 2) * kSW;
@@ -89,110 +90,364 @@ __device__ __forceinline__ T load_cell(const T* __restrict__ pool, const BlockDe
     return ld<T, CG>(pool + cell_index<T>(d, p, x, y, k));
 }
 
-template <typename T, int ARITH>
+template <typename T, int UNUSED>
 __device__ __forceinline__ T mean7(T c, T xm, T xp, T ym, T yp, T zm, T zp)
 {
-    if constexpr (sizeof(T) == 4) {
-        return mean7_seq_f32(c, xm, xp, ym, yp, zm, zp);
-    } else if constexpr (ARITH == 1) {
-        return mean7_exact(c, xm, xp, ym, yp, zm, zp);
-    } else {
-        return mean7_seq(c, xm, xp, ym, yp, zm, zp);
-    }
+    if constexpr (sizeof(T) == 4) return mean7_seq_f32(c, xm, xp, ym, yp, zm, zp);
+    else return mean7_seq(c, xm, xp, ym, yp, zm, zp);
 }
 
-// The z-marching update of one tile (x0..x0+63, y0..y0+7, all k) of block b:
-// reads buffer p, writes the interior of buffer p^1. The current plane of the
-// tile plus a one-cell halo ring sits in shared memory; the planes below and
-// above are carried in registers.
-template <typename T, int ARITH, bool PULL, bool CG>
-__device__ void update_tile(T* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p,
-                            int x0, int y0, T* sm)
+constexpr int OP_SEQ = 0;    // binary64/binary32 left-to-right sum / 7 in floating point
+constexpr int OP_EXACT = 1;  // binary64 correctly rounded mean, grid-frame integer arithmetic
+constexpr int OP_RES = 2;    // residual: sum of L^2 with the exact Laplacian term
+
+template <typename T, int OP>
+struct Elem {
+    using type = frame::W96;
+};
+template <typename T>
+struct Elem<T, OP_SEQ> {
+    using type = T;
+};
+
+template <typename T>
+__device__ __forceinline__ const T* bc_ptr(const BlockDesc& d, int f);
+template <>
+__device__ __forceinline__ const double* bc_ptr<double>(const BlockDesc& d, int f)
+{
+    return &d.bc[f];
+}
+template <>
+__device__ __forceinline__ const float* bc_ptr<float>(const BlockDesc& d, int f)
+{
+    return &d.bcf[f];
+}
+
+template <typename T, bool CG>
+__device__ __forceinline__ T ldv(const T* p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <typename T, int OP>
+__device__ __forceinline__ typename Elem<T, OP>::type conv(T v, int eref)
+{
+    if constexpr (OP == OP_SEQ) return v;
+    else return frame::of((double)v, eref);
+}
+
+// Where the value of (x, y) lives along z, for -1 <= x <= bx, -1 <= y <= by
+// with at most one coordinate outside the block: plane k is p[k * stride].
+// PULL: outside cells come from the neighbouring block (stride: its plane) or
+// are the Dirichlet constant (stride 0). Otherwise the block's ghost layer.
+template <typename T>
+struct Src {
+    const T* p;
+    int64_t stride;
+};
+
+template <typename T, bool PULL>
+__device__ __forceinline__ Src<T> xy_source(const T* pool, const BlockDesc* desc, const BlockDesc& d, int p, int x,
+                                            int y)
+{
+    if constexpr (PULL) {
+        int f = -1;
+        if (x < 0) f = 0;
+        else if (x >= d.ext[0]) f = 1;
+        else if (y < 0) f = 2;
+        else if (y >= d.ext[1]) f = 3;
+        if (f >= 0) {
+            const int nb = d.nbr[f];
+            if (nb < 0) return {bc_ptr<T>(d, f), 0};
+            const BlockDesc& n = desc[nb];
+            const int xx = f == 0 ? n.ext[0] - 1 : (f == 1 ? 0 : x);
+            const int yy = f == 2 ? n.ext[1] - 1 : (f == 3 ? 0 : y);
+            return {pool + cell_index<T>(n, p, xx, yy, 0), n.plane};
+        }
+    }
+    return {pool + cell_index<T>(d, p, x, y, 0), d.plane};
+}
+
+// The value of column (x, y) at plane -1 (zface 4) or plane bz (zface 5).
+template <typename T, bool PULL>
+__device__ __forceinline__ const T* z_source(const T* pool, const BlockDesc* desc, const BlockDesc& d, int p, int x,
+                                             int y, int zface)
+{
+    if constexpr (PULL) {
+        const int nb = d.nbr[zface];
+        if (nb < 0) return bc_ptr<T>(d, zface);
+        const BlockDesc& n = desc[nb];
+        return pool + cell_index<T>(n, p, x, y, zface == 4 ? n.ext[2] - 1 : 0);
+    }
+    return pool + cell_index<T>(d, p, x, y, zface == 4 ? -1 : d.ext[2]);
+}
+
+// Exact per-cell path for the rare cells the grid frame cannot hold: the
+// seven raw values are re-read and handed to the per-cell exact routines.
+template <typename T, bool PULL, bool CG, bool LAPLACIAN>
+__device__ __noinline__ double exact_cell(const T* pool, const BlockDesc* desc, int b, int p, int x, int y, int k)
 {
     const BlockDesc& d = desc[b];
+    const double c = (double)ld<T, CG>(pool + cell_index<T>(d, p, x, y, k));
+    const double xm = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x - 1, y, k);
+    const double xp = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x + 1, y, k);
+    const double ym = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x, y - 1, k);
+    const double yp = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x, y + 1, k);
+    const double zm = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x, y, k - 1);
+    const double zp = (double)load_cell<T, PULL, CG>(pool, desc, d, p, x, y, k + 1);
+    if constexpr (LAPLACIAN) return laplacian_exact(c, xm, xp, ym, yp, zm, zp);
+    else return mean7_exact(c, xm, xp, ym, yp, zm, zp);
+}
+
+// Cells the grid frame cannot hold are not computed inside the z loop (a call
+// there would make the compiler save registers on every plane); they are
+// recorded here and recomputed with the exact per-cell routines once the
+// tile's loop has finished. That is safe: until this tile reports completion
+// neither its input buffer region nor its neighbours' faces can change.
+constexpr int kSlowMax = 256;
+
+struct SlowList {
+    int n;
+    uint32_t cell[kSlowMax];  // (k << 9) | tid
+};
+
+// The z-marching engine over one tile (x0 .. x0+31, y0 .. y0+15, all k) of
+// block b, reading buffer p.
+//   OP_SEQ / OP_EXACT: writes the interior of buffer p^1;
+//   OP_RES:           returns this thread's sum of L^2 (thread 0 also adds the
+//                     cells recomputed exactly, in (k, tid) order).
+// Every shared slot of the tile plane (the 32 x 16 interior plus its halo
+// ring) is a stream along z (pointer + plane stride, or a constant): own
+// columns, halo cells that fall inside the tile where it overhangs the block
+// edge, and one extra ring slot for each of the first 96 threads. Values are
+// loaded D planes ahead into registers, converted once (to the grid frame for
+// the exact ops), stored in a double-buffered shared plane (one barrier per
+// plane), and the z neighbours are carried in registers.
+template <typename T, int OP, bool PULL, bool CG, int D>
+__device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0,
+                              typename Elem<T, OP>::type* sm, SlowList* slow)
+{
+    using E = typename Elem<T, OP>::type;
+    const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int y = y0 + ty;
-    const bool yin = y < by;
-    T zm[kVX], c[kVX], zp[kVX];
+    const int eref = (OP == OP_SEQ) ? 0 : frame_e[d.inst] + 1;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+    const int x = x0 + tx, y = y0 + ty;
+    const int64_t plane = d.plane;
+    if (OP != OP_SEQ && tid == 0) slow->n = 0;
+
+    // own column: 0 unused, 1 interior cell, 2 halo cell inside the tile
+    int kind = 0;
+    const T* sp = pool;
+    int64_t ss = 0;
+    const T* zhi = pool;
+    int64_t oidx = 0;
+    E wzm{}, wc{};
+    T ring[D + 1];  // interior: planes k+1 .. k+1+D; halo: planes k .. k+D
 #pragma unroll
-    for (int v = 0; v < kVX; ++v) {
-        const int x = x0 + tx + kTX * v;
-        if (yin && x < bx) {
-            zm[v] = load_cell<T, PULL, CG>(pool, desc, d, p, x, y, -1);
-            c[v] = ld<T, CG>(pool + cell_index<T>(d, p, x, y, 0));
+    for (int i = 0; i <= D; ++i) ring[i] = T(0);
+    if (x < bx && y < by) {
+        kind = 1;
+        sp = pool + cell_index<T>(d, p, x, y, 0);
+        ss = plane;
+        zhi = z_source<T, PULL>(pool, desc, d, p, x, y, 5);
+        oidx = cell_index<T>(d, p ^ 1, x, y, 0);
+        wzm = conv<T, OP>(ldv<T, CG>(z_source<T, PULL>(pool, desc, d, p, x, y, 4)), eref);
+        wc = conv<T, OP>(ldv<T, CG>(sp), eref);
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const int q = 1 + i;
+            ring[i] = q < bz ? ldv<T, CG>(sp + q * ss) : (q == bz ? ldv<T, CG>(zhi) : T(0));
+        }
+    } else if ((x == bx && y < by) || (y == by && x < bx)) {
+        kind = 2;
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
+        sp = s.p;
+        ss = s.stride;
+#pragma unroll
+        for (int i = 0; i < D; ++i) ring[i] = i < bz ? ldv<T, CG>(sp + i * ss) : T(0);
+    }
+    // one ring slot per thread for tid < 96: row y0-1, row y0+16, column
+    // x0-1, column x0+32 (only the slots some interior cell reads)
+    int er = -1, ec = 0;
+    const T* ep = pool;
+    int64_t es = 0;
+    T ering[D + 1];  // planes k .. k+D
+#pragma unroll
+    for (int i = 0; i <= D; ++i) ering[i] = T(0);
+    if (tid < 2 * kTW + 2 * kTY) {
+        int hx, hy;
+        if (tid < kTW) {
+            er = 0;
+            ec = tid + 1;
+            hx = x0 + tid;
+            hy = y0 - 1;
+            if (hx >= bx) er = -1;
+        } else if (tid < 2 * kTW) {
+            const int c = tid - kTW;
+            er = kTY + 1;
+            ec = c + 1;
+            hx = x0 + c;
+            hy = y0 + kTY;
+            if (hx >= bx || hy > by) er = -1;
+        } else if (tid < 2 * kTW + kTY) {
+            const int r = tid - 2 * kTW;
+            er = r + 1;
+            ec = 0;
+            hx = x0 - 1;
+            hy = y0 + r;
+            if (hy >= by) er = -1;
         } else {
-            zm[v] = T(0);
-            c[v] = T(0);
+            const int r = tid - 2 * kTW - kTY;
+            er = r + 1;
+            ec = kTW + 1;
+            hx = x0 + kTW;
+            hy = y0 + r;
+            if (hy >= by || hx > bx) er = -1;
+        }
+        if (er >= 0) {
+            const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, hx, hy);
+            ep = s.p;
+            es = s.stride;
+#pragma unroll
+            for (int i = 0; i < D; ++i) ering[i] = i < bz ? ldv<T, CG>(ep + i * es) : T(0);
         }
     }
+    if (OP != OP_SEQ) __syncthreads();  // slow->n = 0 visible before any append
+
+    double acc = 0.0;
+#pragma unroll 2
     for (int k = 0; k < bz; ++k) {
-#pragma unroll
-        for (int v = 0; v < kVX; ++v) {
-            const int x = x0 + tx + kTX * v;
-            if (yin && x < bx) {
-                zp[v] = (k + 1 < bz) ? ld<T, CG>(pool + cell_index<T>(d, p, x, y, k + 1))
-                                     : load_cell<T, PULL, CG>(pool, desc, d, p, x, y, bz);
+        E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
+        // issue the loads D planes ahead
+        if (kind == 1) {
+            const int q = k + 1 + D;
+            ring[D] = q < bz ? ldv<T, CG>(sp + q * ss) : (q == bz ? ldv<T, CG>(zhi) : T(0));
+        } else if (kind == 2) {
+            ring[D] = k + D < bz ? ldv<T, CG>(sp + (k + D) * ss) : T(0);
+        }
+        if (er >= 0) ering[D] = k + D < bz ? ldv<T, CG>(ep + (k + D) * es) : T(0);
+        // this plane's shared slots
+        E* slot = buf + (ty + 1) * kSW + tx + 1;
+        if (kind == 1) *slot = wc;
+        else if (kind == 2) *slot = conv<T, OP>(ring[0], eref);
+        if (er >= 0) buf[er * kSW + ec] = conv<T, OP>(ering[0], eref);
+        __syncthreads();
+        if (kind == 1) {
+            const E wzp = conv<T, OP>(ring[0], eref);
+            const int sc = (ty + 1) * kSW + tx + 1;
+            if constexpr (OP == OP_SEQ) {
+                pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
             } else {
-                zp[v] = T(0);
+                double o;
+                bool ok;
+                if constexpr (OP == OP_EXACT) {
+                    ok = frame::mean7(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
+                    if (ok) pool[oidx + k * plane] = (T)o;
+                } else {
+                    ok = frame::laplacian(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
+                    if (ok) acc = fma(o, o, acc);
+                }
+                if (!ok) {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
+                }
             }
-            // own slot: the cell itself, or the +x / +y halo when the tile
-            // overhangs the block edge by exactly that cell
-            T s = T(0);
-            if (yin && x < bx) s = c[v];
-            else if (yin && x == bx) s = load_cell<T, PULL, CG>(pool, desc, d, p, x, y, k);
-            else if (y == by && x < bx) s = load_cell<T, PULL, CG>(pool, desc, d, p, x, y, k);
-            sm[(ty + 1) * kSW + tx + kTX * v + 1] = s;
+            wzm = wc;
+            wc = wzp;
         }
-        if (ty == 0) {  // row y0 - 1
 #pragma unroll
-            for (int v = 0; v < kVX; ++v) {
-                const int x = x0 + tx + kTX * v;
-                sm[tx + kTX * v + 1] = x < bx ? load_cell<T, PULL, CG>(pool, desc, d, p, x, y0 - 1, k) : T(0);
-            }
+        for (int i = 0; i < D; ++i) {
+            ring[i] = ring[i + 1];
+            ering[i] = ering[i + 1];
         }
-        if (ty == kTY - 1 && y0 + kTY <= by) {  // row y0 + 8 (inside or +y halo)
-#pragma unroll
-            for (int v = 0; v < kVX; ++v) {
-                const int x = x0 + tx + kTX * v;
-                sm[(kTY + 1) * kSW + tx + kTX * v + 1] =
-                    x < bx ? load_cell<T, PULL, CG>(pool, desc, d, p, x, y0 + kTY, k) : T(0);
-            }
-        }
-        if (tx == 0) sm[(ty + 1) * kSW] = yin ? load_cell<T, PULL, CG>(pool, desc, d, p, x0 - 1, y, k) : T(0);
-        if (tx == kTX - 1 && x0 + kTW <= bx)
-            sm[(ty + 1) * kSW + kTW + 1] = yin ? load_cell<T, PULL, CG>(pool, desc, d, p, x0 + kTW, y, k) : T(0);
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < kVX; ++v) {
-            const int x = x0 + tx + kTX * v;
-            if (yin && x < bx) {
-                const int sc = (ty + 1) * kSW + tx + kTX * v + 1;
-                const T out = mean7<T, ARITH>(c[v], sm[sc - 1], sm[sc + 1], sm[sc - kSW], sm[sc + kSW], zm[v], zp[v]);
-                pool[cell_index<T>(d, p ^ 1, x, y, k)] = out;
-            }
-            zm[v] = c[v];
-            c[v] = zp[v];
-        }
-        __syncthreads();
     }
+    if constexpr (OP != OP_SEQ) {
+        __syncthreads();
+        const int n = slow->n;
+        if (n > 0) {
+            if (n <= kSlowMax) {
+                if constexpr (OP == OP_EXACT) {
+                    for (int i = tid; i < n; i += kTX * kTY) {
+                        const uint32_t c = slow->cell[i];
+                        const int kk = (int)(c >> 9), t = (int)(c & 511u);
+                        const int cx = x0 + t % kTX, cy = y0 + t / kTX;
+                        pool[cell_index<T>(d, p ^ 1, cx, cy, kk)] =
+                            (T)exact_cell<T, PULL, CG, false>(pool, desc, b, p, cx, cy, kk);
+                    }
+                } else if (tid == 0) {
+                    // deterministic: ascending (k, tid)
+                    for (int i = 1; i < n; ++i) {
+                        const uint32_t v = slow->cell[i];
+                        int j = i - 1;
+                        while (j >= 0 && slow->cell[j] > v) {
+                            slow->cell[j + 1] = slow->cell[j];
+                            --j;
+                        }
+                        slow->cell[j + 1] = v;
+                    }
+                    for (int i = 0; i < n; ++i) {
+                        const uint32_t c = slow->cell[i];
+                        const int kk = (int)(c >> 9), t = (int)(c & 511u);
+                        const double L = exact_cell<T, PULL, CG, true>(pool, desc, b, p, x0 + t % kTX, y0 + t / kTX, kk);
+                        acc = fma(L, L, acc);
+                    }
+                }
+            } else {
+                // more cells outside the frame than the list holds: redo the
+                // whole tile with the exact per-cell routines
+                if constexpr (OP == OP_EXACT) {
+                    if (kind == 1)
+                        for (int kk = 0; kk < bz; ++kk)
+                            pool[oidx + kk * plane] = (T)exact_cell<T, PULL, CG, false>(pool, desc, b, p, x, y, kk);
+                } else {
+                    acc = 0.0;
+                    if (kind == 1)
+                        for (int kk = 0; kk < bz; ++kk) {
+                            const double L = exact_cell<T, PULL, CG, true>(pool, desc, b, p, x, y, kk);
+                            acc = fma(L, L, acc);
+                        }
+                }
+            }
+        }
+    }
+    return acc;
+}
+
+template <typename T, int OP>
+__host__ __device__ constexpr int smem_bytes()
+{
+    return 2 * (kTY + 2) * kSW * (int)sizeof(typename Elem<T, OP>::type);
 }
 
 // ---------------------------------------------------------------- kernels
 
-template <typename T, int ARITH>
-__global__ void __launch_bounds__(kTX * kTY) k_stencil_block(T* pool, const BlockDesc* desc, int b, int p)
+// prefetch depth: binary32 tiles are bandwidth-bound and need more bytes in
+// flight; binary64 tiles are bound by the arithmetic
+template <typename T>
+constexpr int kDepth = sizeof(T) == 4 ? 6 : 3;
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kTX * kTY, 2) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+                                                                int b, int p)
 {
-    __shared__ T sm[kSmemCells];
-    update_tile<T, ARITH, false, false>(pool, desc, b, p, blockIdx.x * kTW, blockIdx.y * kTY, sm);
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ SlowList slow;
+    tile_engine<T, OP, false, false, kDepth<T>>(pool, desc, frame_e, b, p, blockIdx.x * kTW, blockIdx.y * kTY,
+                                                (typename Elem<T, OP>::type*)sm, &slow);
 }
 
-template <typename T, int ARITH>
-__global__ void __launch_bounds__(kTX * kTY) k_fused_step(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
+template <typename T, int OP>
+__global__ void __launch_bounds__(kTX * kTY, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+                                                             const TileUnit* units, int p)
 {
-    __shared__ T sm[kSmemCells];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
-    update_tile<T, ARITH, true, false>(pool, desc, u.block, p, u.x0, u.y0, sm);
+    tile_engine<T, OP, true, false, kDepth<T>>(pool, desc, frame_e, u.block, p, u.x0, u.y0,
+                                               (typename Elem<T, OP>::type*)sm, &slow);
 }
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -222,13 +477,14 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // all their tiles of iteration t-1 (done[n] >= t * ntiles[n]): that covers
 // both the halo it reads (buffer p) and every reader of the region it
 // overwrites (buffer p^1 held iteration t-1). Every wait is bounded.
-template <typename T, int ARITH>
-__global__ void __launch_bounds__(kTX * kTY) k_persistent(T* pool, const BlockDesc* desc, const TileUnit* units,
-                                                          int nunits, int p0, int64_t n_iters, uint32_t* done,
-                                                          unsigned long long* work, DeviceStatus* st,
-                                                          int64_t wait_ns, int hold_block, int64_t hold_after)
+template <typename T, int OP>
+__global__ void __launch_bounds__(kTX * kTY, 2)
+    k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
+                 int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
+                 int hold_block, int64_t hold_after)
 {
-    __shared__ T sm[kSmemCells];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ SlowList slow;
     __shared__ long long s_w;
     __shared__ int s_stop;
     const long long total = (long long)n_iters * nunits;
@@ -276,7 +532,8 @@ __global__ void __launch_bounds__(kTX * kTY) k_persistent(T* pool, const BlockDe
         if (w >= total || s_stop) break;
         const int t = (int)(w / nunits);
         const TileUnit u = units[w % nunits];
-        update_tile<T, ARITH, true, true>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, sm);
+        tile_engine<T, OP, true, true, kDepth<T>>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
+                                                  (typename Elem<T, OP>::type*)sm, &slow);
         __syncthreads();
         if (lead && !(u.block == hold_block && t >= hold_after)) {
             __threadfence();
@@ -285,84 +542,20 @@ __global__ void __launch_bounds__(kTX * kTY) k_persistent(T* pool, const BlockDe
     }
 }
 
-// Residual: sum over the tile of L^2, L = xm+xp+ym+yp+zm+zp-6c exact, one
-// partial per CTA in a fixed order (per thread over k, then a fixed tree).
+// Residual: per CTA the sum over its tile of L^2 (L the exact Laplacian term
+// rounded once), in a fixed order (per thread over k, then a fixed tree).
 template <typename T>
-__global__ void __launch_bounds__(kTX * kTY) k_residual(const T* pool, const BlockDesc* desc, const TileUnit* units,
-                                                        int p, double* partials)
+__global__ void __launch_bounds__(kTX * kTY, 2) k_residual(const T* pool, const BlockDesc* desc,
+                                                           const int32_t* frame_e, const TileUnit* units, int p,
+                                                           double* partials)
 {
-    __shared__ T sm[kSmemCells];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP_RES>()];
+    __shared__ SlowList slow;
     __shared__ double red[kTX * kTY];
     const TileUnit u = units[blockIdx.x];
-    const BlockDesc& d = desc[u.block];
-    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = u.x0, y0 = u.y0;
-    const int y = y0 + ty;
-    const bool yin = y < by;
-    double acc = 0.0;
-    T zm[kVX], c[kVX], zp[kVX];
-#pragma unroll
-    for (int v = 0; v < kVX; ++v) {
-        const int x = x0 + tx + kTX * v;
-        if (yin && x < bx) {
-            zm[v] = load_cell<T, true, false>(pool, desc, d, p, x, y, -1);
-            c[v] = pool[cell_index<T>(d, p, x, y, 0)];
-        } else {
-            zm[v] = T(0);
-            c[v] = T(0);
-        }
-    }
-    for (int k = 0; k < bz; ++k) {
-#pragma unroll
-        for (int v = 0; v < kVX; ++v) {
-            const int x = x0 + tx + kTX * v;
-            if (yin && x < bx)
-                zp[v] = (k + 1 < bz) ? pool[cell_index<T>(d, p, x, y, k + 1)]
-                                     : load_cell<T, true, false>(pool, desc, d, p, x, y, bz);
-            else
-                zp[v] = T(0);
-            T s = T(0);
-            if (yin && x < bx) s = c[v];
-            else if (yin && x == bx) s = load_cell<T, true, false>(pool, desc, d, p, x, y, k);
-            else if (y == by && x < bx) s = load_cell<T, true, false>(pool, desc, d, p, x, y, k);
-            sm[(ty + 1) * kSW + tx + kTX * v + 1] = s;
-        }
-        if (ty == 0) {
-#pragma unroll
-            for (int v = 0; v < kVX; ++v) {
-                const int x = x0 + tx + kTX * v;
-                sm[tx + kTX * v + 1] = x < bx ? load_cell<T, true, false>(pool, desc, d, p, x, y0 - 1, k) : T(0);
-            }
-        }
-        if (ty == kTY - 1 && y0 + kTY <= by) {
-#pragma unroll
-            for (int v = 0; v < kVX; ++v) {
-                const int x = x0 + tx + kTX * v;
-                sm[(kTY + 1) * kSW + tx + kTX * v + 1] =
-                    x < bx ? load_cell<T, true, false>(pool, desc, d, p, x, y0 + kTY, k) : T(0);
-            }
-        }
-        if (tx == 0) sm[(ty + 1) * kSW] = yin ? load_cell<T, true, false>(pool, desc, d, p, x0 - 1, y, k) : T(0);
-        if (tx == kTX - 1 && x0 + kTW <= bx)
-            sm[(ty + 1) * kSW + kTW + 1] = yin ? load_cell<T, true, false>(pool, desc, d, p, x0 + kTW, y, k) : T(0);
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < kVX; ++v) {
-            const int x = x0 + tx + kTX * v;
-            if (yin && x < bx) {
-                const int sc = (ty + 1) * kSW + tx + kTX * v + 1;
-                const double L = laplacian_exact((double)c[v], (double)sm[sc - 1], (double)sm[sc + 1],
-                                                 (double)sm[sc - kSW], (double)sm[sc + kSW], (double)zm[v],
-                                                 (double)zp[v]);
-                acc = fma(L, L, acc);
-            }
-            zm[v] = c[v];
-            c[v] = zp[v];
-        }
-        __syncthreads();
-    }
-    const int tid = ty * kTX + tx;
+    const double acc = tile_engine<T, OP_RES, true, false, 2>(const_cast<T*>(pool), desc, frame_e, u.block, p, u.x0,
+                                                              u.y0, (frame::W96*)sm, &slow);
+    const int tid = threadIdx.y * kTX + threadIdx.x;
     red[tid] = acc;
     __syncthreads();
     for (int s = kTX * kTY / 2; s > 0; s >>= 1) {
@@ -469,17 +662,24 @@ __global__ void k_unpack6(T* pool, const BlockDesc* desc, int b, int p, const T*
 // Dense x-fastest instance arrays <-> block interiors (buffer p). Grid x is
 // the block, grid y strides over the block's rows; threads walk x.
 template <typename TS, typename TD>
-__global__ void k_scatter(const TS* dense, TD* pool, const BlockDesc* desc, int p)
+__global__ void k_scatter(const TS* dense, TD* pool, const BlockDesc* desc, int p, int32_t* frame_e)
 {
     const BlockDesc& d = desc[blockIdx.x];
     const int rows = d.ext[1] * d.ext[2];
+    int emax = 0;
     for (int r = blockIdx.y; r < rows; r += gridDim.y) {
         const int y = r % d.ext[1], k = r / d.ext[1];
         const int64_t g = d.dense + (int64_t)d.org[0] +
                           (int64_t)d.gdim[0] * ((int64_t)(d.org[1] + y) + (int64_t)d.gdim[1] * (d.org[2] + k));
-        for (int x = threadIdx.x; x < d.ext[0]; x += blockDim.x)
-            pool[cell_index<TD>(d, p, x, y, k)] = (TD)dense[g + x];
+        for (int x = threadIdx.x; x < d.ext[0]; x += blockDim.x) {
+            const TD v = (TD)dense[g + x];
+            pool[cell_index<TD>(d, p, x, y, k)] = v;
+            emax = max(emax, (int)((dbits((double)v) >> 52) & 0x7FF));
+        }
     }
+    // largest exponent field of the instance: the grid frame's reference
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(frame_e + d.inst, emax);
 }
 
 template <typename TS, typename TD>
@@ -526,10 +726,13 @@ static cudaError_t stencil_block_t(const LaunchArgs& a, int arith, int b, int nx
                                    cudaStream_t s)
 {
     dim3 grid(nx_tiles, ny_tiles, 1);
-    if (sizeof(T) == 8 && arith == 1)
-        k_stencil_block<T, 1><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, b, p);
-    else
-        k_stencil_block<T, 0><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, b, p);
+    if constexpr (sizeof(T) == 8) {
+        if (arith == 1) {
+            k_stencil_block<T, OP_EXACT><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
+            return cudaGetLastError();
+        }
+    }
+    k_stencil_block<T, OP_SEQ><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
     return cudaGetLastError();
 }
 
@@ -543,10 +746,13 @@ cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, 
 template <typename T>
 static cudaError_t fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
 {
-    if (sizeof(T) == 8 && arith == 1)
-        k_fused_step<T, 1><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.units, p);
-    else
-        k_fused_step<T, 0><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.units, p);
+    if constexpr (sizeof(T) == 8) {
+        if (arith == 1) {
+            k_fused_step<T, OP_EXACT><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+            return cudaGetLastError();
+        }
+    }
+    k_fused_step<T, OP_SEQ><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
     return cudaGetLastError();
 }
 
@@ -555,16 +761,10 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
     return dtype_f32 ? fused_step_t<float>(a, arith, p, s) : fused_step_t<double>(a, arith, p, s);
 }
 
-template <typename T, int ARITH>
-static const void* persistent_fn()
-{
-    return (const void*)k_persistent<T, ARITH>;
-}
-
 const void* persistent_kernel(int dtype_f32, int arith)
 {
-    if (dtype_f32) return persistent_fn<float, 0>();
-    return arith == 1 ? persistent_fn<double, 1>() : persistent_fn<double, 0>();
+    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ>;
+    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT> : (const void*)k_persistent<double, OP_SEQ>;
 }
 
 int persistent_block_threads() { return kTX * kTY; }
@@ -572,14 +772,17 @@ int persistent_block_threads() { return kTX * kTY; }
 template <typename T>
 static cudaError_t persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith, int ctas, cudaStream_t s)
 {
-    if (sizeof(T) == 8 && arith == 1)
-        k_persistent<T, 1><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.units, a.nunits, q.p0, q.n_iters,
-                                                         q.done, q.work, q.status, q.wait_ns, q.hold_block,
-                                                         q.hold_after);
-    else
-        k_persistent<T, 0><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.units, a.nunits, q.p0, q.n_iters,
-                                                         q.done, q.work, q.status, q.wait_ns, q.hold_block,
-                                                         q.hold_after);
+    if constexpr (sizeof(T) == 8) {
+        if (arith == 1) {
+            k_persistent<T, OP_EXACT><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
+                                                                    q.p0, q.n_iters, q.done, q.work, q.status,
+                                                                    q.wait_ns, q.hold_block, q.hold_after);
+            return cudaGetLastError();
+        }
+    }
+    k_persistent<T, OP_SEQ><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+                                                          q.n_iters, q.done, q.work, q.status, q.wait_ns,
+                                                          q.hold_block, q.hold_after);
     return cudaGetLastError();
 }
 
@@ -593,9 +796,11 @@ cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* p
                             cudaStream_t s)
 {
     if (dtype_f32)
-        k_residual<float><<<a.nunits, tile_block(), 0, s>>>((const float*)a.pool, a.desc, a.units, p, partials);
+        k_residual<float><<<a.nunits, tile_block(), 0, s>>>((const float*)a.pool, a.desc, a.frame, a.units, p,
+                                                             partials);
     else
-        k_residual<double><<<a.nunits, tile_block(), 0, s>>>((const double*)a.pool, a.desc, a.units, p, partials);
+        k_residual<double><<<a.nunits, tile_block(), 0, s>>>((const double*)a.pool, a.desc, a.frame, a.units, p,
+                                                              partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 256, 0, s>>>(partials, a.nunits, out);
@@ -642,10 +847,12 @@ cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, cons
 {
     dim3 grid(a.nblocks, 16, 1);
     if (dtype_f32) {
-        if (src_f32) k_scatter<float, float><<<grid, 256, 0, s>>>((const float*)dense, (float*)a.pool, a.desc, p);
-        else k_scatter<double, float><<<grid, 256, 0, s>>>((const double*)dense, (float*)a.pool, a.desc, p);
+        if (src_f32)
+            k_scatter<float, float><<<grid, 256, 0, s>>>((const float*)dense, (float*)a.pool, a.desc, p, a.frame);
+        else
+            k_scatter<double, float><<<grid, 256, 0, s>>>((const double*)dense, (float*)a.pool, a.desc, p, a.frame);
     } else {
-        k_scatter<double, double><<<grid, 256, 0, s>>>((const double*)dense, (double*)a.pool, a.desc, p);
+        k_scatter<double, double><<<grid, 256, 0, s>>>((const double*)dense, (double*)a.pool, a.desc, p, a.frame);
     }
     return cudaGetLastError();
 }

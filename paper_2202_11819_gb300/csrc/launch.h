@@ -14,6 +14,7 @@ struct LaunchArgs {
     void* pool;              // block storage (both buffers)
     const BlockDesc* desc;   // device block table
     const TileUnit* units;   // device tile table
+    int32_t* frame;          // per instance: largest exponent field (grid frame)
     int nblocks;
     int nunits;
 };

@@ -105,6 +105,8 @@ struct jac_ctx {
     BlockDesc* ddesc = nullptr;
     TileUnit* dunits = nullptr;
     void* pool = nullptr;
+    int32_t* frame = nullptr;  // per instance: largest exponent field of the grid and its boundary
+    int32_t bc_frame = 0;      // that field over the boundary values alone
     int parity = 0;
     int64_t iters = 0;
     int64_t launches = 0;
@@ -145,6 +147,7 @@ struct jac_ctx {
         a.pool = pool;
         a.desc = ddesc;
         a.units = dunits;
+        a.frame = frame;
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
         return a;
@@ -234,6 +237,7 @@ int build_layout(jac_ctx* h)
                     if (q[a] < 0 || q[a] >= h->nb[a]) d.nbr[f] = -1;
                     else d.nbr[f] = (int32_t)(q[0] + (int64_t)h->nb[0] * (q[1] + (int64_t)h->nb[1] * q[2]));
                     d.bc[f] = h->bc[f];
+                    d.bcf[f] = (float)h->bc[f];
                 }
                 d.inst = 0;
                 d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
@@ -269,6 +273,15 @@ int build_layout(jac_ctx* h)
     if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
     if ((rc = dev_alloc(h, h->hunits.size() * sizeof(double), (void**)&h->partials))) return rc;
     if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
+    if ((rc = dev_alloc(h, sizeof(int32_t), (void**)&h->frame))) return rc;
+    h->bc_frame = 0;
+    for (int f = 0; f < 6; ++f) {
+        const double v = h->dtype == JAC_F32 ? (double)(float)h->bc[f] : h->bc[f];
+        uint64_t bits;
+        memcpy(&bits, &v, 8);
+        h->bc_frame = std::max(h->bc_frame, (int32_t)((bits >> 52) & 0x7FF));
+    }
+    CU(cudaMemcpyAsync(h->frame, &h->bc_frame, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream), "init frame");
     CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), nblocks * sizeof(BlockDesc), cudaMemcpyHostToDevice, h->stream),
        "copy block table");
     CU(cudaMemcpyAsync(h->dunits, h->hunits.data(), h->hunits.size() * sizeof(TileUnit), cudaMemcpyHostToDevice,
@@ -502,6 +515,8 @@ int write_dense(jac_ctx* h, const void* src, size_t n, int src_f32, bool src_on_
         CU(cudaMemcpyAsync(h->dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
         dsrc = h->dense;
     }
+    // the scatter raises the frame to the largest exponent of the new interior
+    CU(cudaMemcpyAsync(h->frame, &h->bc_frame, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream), "reset frame");
     CU(launch_scatter(h->args(), h->dtype == JAC_F32, src_f32, dsrc, h->parity, h->stream), "scatter");
     h->launches += 1;
     h->iters = 0;

@@ -12,3 +12,20 @@ extern "C" double host_laplacian_exact(double c, const double* nb)
 {
     return jac::laplacian_exact(c, nb[0], nb[1], nb[2], nb[3], nb[4], nb[5]);
 }
+
+extern "C" int host_frame_mean7(const double* v, int eref, double* out)
+{
+    using namespace jac::frame;
+    W96 w[7];
+    for (int i = 0; i < 7; ++i) w[i] = of(v[i], eref);
+    return mean7(w[0], w[1], w[2], w[3], w[4], w[5], w[6], eref, *out) ? 1 : 0;
+}
+
+extern "C" int host_frame_laplacian(double c, const double* nb, int eref, double* out)
+{
+    using namespace jac::frame;
+    return laplacian(of(c, eref), of(nb[0], eref), of(nb[1], eref), of(nb[2], eref), of(nb[3], eref),
+                     of(nb[4], eref), of(nb[5], eref), eref, *out)
+               ? 1
+               : 0;
+}

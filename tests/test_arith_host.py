@@ -30,6 +30,11 @@ def host_lib():
     lib.host_mean7_exact.restype = ctypes.c_double
     lib.host_laplacian_exact.argtypes = [ctypes.c_double, ctypes.c_void_p]
     lib.host_laplacian_exact.restype = ctypes.c_double
+    lib.host_frame_mean7.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.host_frame_mean7.restype = ctypes.c_int
+    lib.host_frame_laplacian.argtypes = [ctypes.c_double, ctypes.c_void_p, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double)]
+    lib.host_frame_laplacian.restype = ctypes.c_int
     return lib
 
 
@@ -105,3 +110,58 @@ def test_laplacian_exact_host_matches_oracle(host_lib):
         got = host_lib.host_laplacian_exact(c, a.ctypes.data)
         want = oracle.exact_laplacian(c, a)
         assert np.float64(got).tobytes() == np.float64(want).tobytes(), (c, nb)
+
+
+def exp_field(x):
+    return int((np.float64(x).view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF))
+
+
+def test_grid_frame_mean7_matches_oracle(host_lib):
+    """The grid-frame fast path either declines (the kernel then takes the
+    exact per-cell path) or returns exactly the correctly rounded mean."""
+    rng = np.random.default_rng(7)
+    fast = total = 0
+    out = ctypes.c_double()
+    for v in mean_cases(rng):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        E = max(exp_field(x) for x in a)
+        for extra in (1, 2, 5):
+            eref = max(E, 0) + extra
+            total += 1
+            if host_lib.host_frame_mean7(a.ctypes.data, eref, ctypes.byref(out)):
+                fast += 1
+                want = oracle.exact_mean7(a)
+                assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (v, eref)
+    # uniform [0, 1) data must essentially always take the fast path
+    ok = 0
+    for _ in range(3000):
+        a = np.ascontiguousarray(rng.random(7))
+        ok += host_lib.host_frame_mean7(a.ctypes.data, 1024, ctypes.byref(out))
+        assert out.value == oracle.exact_mean7(a)
+    assert ok == 3000
+    assert fast > total // 3
+
+
+def test_grid_frame_laplacian_matches_oracle(host_lib):
+    rng = np.random.default_rng(8)
+    out = ctypes.c_double()
+    cases = [(0.3, [0.3] * 6), (1.0, [0.0] * 6), (0.0, [1.0] * 6),
+             (1.0, [1.0, 1.0, 1.0, 1.0, 1.0, 1.0 + 2.0 ** -52])]
+    for _ in range(4000):
+        cases.append((float(rng.random()), list(rng.random(6))))
+    for _ in range(2000):
+        c = float(rng.random())
+        cases.append((c, [c + float(x) * 2.0 ** -50 for x in rng.integers(-3, 4, size=6)]))
+    for _ in range(2000):
+        e = rng.integers(-25, 1, size=7)
+        vals = rng.random(7) * 2.0 ** e
+        cases.append((float(vals[0]), list(vals[1:])))
+    fast = 0
+    for c, nb in cases:
+        a = np.ascontiguousarray(nb, dtype=np.float64)
+        eref = max(exp_field(x) for x in [c] + list(nb)) + 1
+        if host_lib.host_frame_laplacian(c, a.ctypes.data, eref, ctypes.byref(out)):
+            fast += 1
+            want = oracle.exact_laplacian(c, a)
+            assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (c, nb)
+    assert fast > 0.9 * len(cases)
