@@ -153,14 +153,14 @@ def measured_peaks():
 
 def profile_traffic(kernel_tag: str):
     """dram bytes per launch of the timed kernel from the committed ncu
-    summary (profiles/<kernel_tag>.txt, line 'traffic_bytes_per_launch: N'),
+    summary (profiles/<kernel_tag>.txt, line 'traffic_bytes_per_iteration: N'),
     or None when no capture of the current kernel exists."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         for line in f:
-            if line.startswith("traffic_bytes_per_launch:"):
+            if line.startswith("traffic_bytes_per_iteration:"):
                 v = line.split(":", 1)[1].strip()
                 return None if v in ("null", "None", "") else float(v)
     return None

@@ -476,7 +476,9 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // block b), the CTA waits until b and its six neighbours have each finished
 // all their tiles of iteration t-1 (done[n] >= t * ntiles[n]): that covers
 // both the halo it reads (buffer p) and every reader of the region it
-// overwrites (buffer p^1 held iteration t-1). Every wait is bounded.
+// overwrites (buffer p^1 held iteration t-1). The seven counters are polled
+// by seven threads at once, and the next unit is taken while the current
+// one computes. Every wait is bounded.
 template <typename T, int OP>
 __global__ void __launch_bounds__(kTX * kTY, 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
@@ -485,57 +487,53 @@ __global__ void __launch_bounds__(kTX * kTY, 2)
 {
     __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
     __shared__ SlowList slow;
-    __shared__ long long s_w;
+    __shared__ long long s_next;
     __shared__ int s_stop;
     const long long total = (long long)n_iters * nunits;
-    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const int tid = threadIdx.y * kTX + threadIdx.x;
+    if (tid == 0) s_next = (long long)atomicAdd(work, 1ull);
+    __syncthreads();
     for (;;) {
-        if (lead) {
-            long long w = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
-            s_w = w;
-            int stop = 0;
-            if (w < total) {
-                const int t = (int)(w / nunits);
-                const int b = units[w % nunits].block;
-                if (t > 0) {
-                    const uint64_t t0 = global_ns();
-                    for (int f = -1; f < 6 && !stop; ++f) {
-                        const int n = f < 0 ? b : desc[b].nbr[f];
-                        if (n < 0) continue;
-                        const uint32_t need = (uint32_t)t * (uint32_t)desc[n].ntiles;
-                        unsigned ns = 32;
-                        while (ld_acquire(done + n) < need) {
-                            if (ld_volatile(&st->abort)) {
-                                stop = 1;
-                                break;
-                            }
-                            if ((int64_t)(global_ns() - t0) > wait_ns) {
-                                if (atomicCAS(&st->err, kErrNone, kErrTimeout) == kErrNone) {
-                                    st->where_block = n;
-                                    st->where_iter = t;
-                                }
-                                atomicExch(&st->abort, 1);
-                                stop = 1;
-                                break;
-                            }
-                            __nanosleep(ns);
-                            ns = ns < 1024 ? ns * 2 : ns;
-                        }
-                    }
-                    __threadfence();
-                }
-            }
-            s_stop = stop;
-        }
-        __syncthreads();
-        const long long w = s_w;
-        if (w >= total || s_stop) break;
+        const long long w = s_next;
+        if (w >= total) break;
         const int t = (int)(w / nunits);
         const TileUnit u = units[w % nunits];
+        if (tid == 0) s_stop = 0;
+        __syncthreads();
+        if (t > 0 && tid < 7) {
+            const int n = tid == 0 ? u.block : desc[u.block].nbr[tid - 1];
+            if (n >= 0) {
+                const uint32_t need = (uint32_t)t * (uint32_t)desc[n].ntiles;
+                const uint64_t t0 = global_ns();
+                unsigned ns = 32;
+                while (ld_acquire(done + n) < need) {
+                    if (ld_volatile(&st->abort)) {
+                        s_stop = 1;
+                        break;
+                    }
+                    if ((int64_t)(global_ns() - t0) > wait_ns) {
+                        if (atomicCAS(&st->err, kErrNone, kErrTimeout) == kErrNone) {
+                            st->where_block = n;
+                            st->where_iter = t;
+                        }
+                        atomicExch(&st->abort, 1);
+                        s_stop = 1;
+                        break;
+                    }
+                    __nanosleep(ns);
+                    ns = ns < 1024 ? ns * 2 : ns;
+                }
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_stop) break;
+        // take the next unit now; its index is read after this one finishes
+        if (tid == 0) s_next = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
         tile_engine<T, OP, true, true, kDepth<T>>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
                                                   (typename Elem<T, OP>::type*)sm, &slow);
         __syncthreads();
-        if (lead && !(u.block == hold_block && t >= hold_after)) {
+        if (tid == 0 && !(u.block == hold_block && t >= hold_after)) {
             __threadfence();
             atomicAdd(done + u.block, 1u);
         }
