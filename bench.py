@@ -52,6 +52,11 @@ def parse():
     p.add_argument("--forms", action="store_true", help="also time the unfused / fused / graph forms")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default tile shape (32 wide, whole blocks)")
+    p.add_argument("--workload", default="grid", choices=["grid", "batch"],
+                   help="grid: one overdecomposed grid (default); batch: many independent grids in one launch")
+    p.add_argument("--instances", type=int, default=256, help="batch workload: number of grids")
+    p.add_argument("--batch-iters", type=int, default=500, help="batch workload: iterations per step")
     return p.parse_args()
 
 
@@ -257,6 +262,9 @@ def run_ours(a, rank, world, local, pg):
         J = Jacobi3D(g, b, dtype=a.dtype, bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode,
                      arith=a.arith if a.dtype == "f64" else "seq")
         J.write_device(dev_u0)
+        tune = None
+        if not a.no_autotune:
+            tune = _lib.jac_autotune(J.h, 4)
 
         def step():
             J.iterate(a.iters)
@@ -371,6 +379,7 @@ def run_ours(a, rank, world, local, pg):
         "data": "synthetic",
         "config": {"workload": workload_name(a), "grid": list(g), "block": list(b), "iterations_per_step": a.iters,
                    "mode": a.mode, "arith": a.arith if a.dtype == "f64" else "seq",
+                   "autotune": tune,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (working set %.2f GB vs 129 MB L2)" % (
                        2 * ncell * np.dtype(np_dt).itemsize / 1e9)},
@@ -391,12 +400,103 @@ def run_ours(a, rank, world, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(a, rank, world, local, pg):
+    """Batched workload: many independent FP64 grids, each axis drawn from
+    32, 48, ..., 192 (seeded), split into blocks of at most 64^3, advanced
+    together in one launch per step with the autotuned tile shape and z depth.
+    The same batch is also timed in the plain per-block-launch form."""
+    import torch
+
+    import synth
+    from paper_2202_11819_gb300 import Jacobi3DBatch, use_torch_allocator
+
+    torch.cuda.set_device(local)
+    use_torch_allocator(True)
+    stream = torch.cuda.Stream()
+    dims = synth.batch_instance_dims(a.instances, seed=0)
+    ncell = sum(x * y * z for x, y, z in dims)
+    host = np.empty(ncell, dtype=np.float64)
+    o = 0
+    for i, (x, y, z) in enumerate(dims):
+        n = x * y * z
+        synth.grid_uniform01(i, x, y, z, out=host[o:o + n])
+        o += n
+    dev = torch.from_numpy(host).to(f"cuda:{local}")
+    bcs = [synth.DIRICHLET_X0] * len(dims)
+    with torch.cuda.stream(stream):
+        B = Jacobi3DBatch(dims, a.block, bcs=bcs, stream=stream.cuda_stream, mode=a.mode, arith=a.arith)
+        from paper_2202_11819_gb300 import _lib
+
+        _lib.jac_write_device(B.h, dev.data_ptr(), ncell, _lib.JAC_F64)
+        tune = B.autotune(4)
+        rho = torch.zeros(len(dims), dtype=torch.float64, device=f"cuda:{local}")
+
+        def step():
+            B.iterate(a.batch_iters)
+            _lib.jac_residual_instances_device(B.h, rho.data_ptr())
+
+        for _ in range(a.warmup):
+            step()
+        stream.synchronize()
+        launches0 = B.info()["kernel_launches"]
+        barrier(pg)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            e0.record(stream)
+            for _ in range(a.steps):
+                step()
+            e1.record(stream)
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        B.sync()
+        launches = B.info()["kernel_launches"] - launches0
+        wall = max_over_ranks(pg, wall)
+        value = world * ncell * a.batch_iters * a.steps / wall
+        # the plain form: per-block launches on per-block streams, untuned
+        B.set_mode("unfused")
+        B.set_tile(32, 0)
+        B.iterate(1)
+        stream.synchronize()
+        n_plain = 3
+        t0 = time.perf_counter()
+        B.iterate(n_plain)
+        stream.synchronize()
+        plain = ncell * n_plain / (time.perf_counter() - t0)
+        info = B.info()
+        B.close()
+    if rank != 0:
+        return
+    peak, kind = measured_peaks()
+    achieved = BYTES_PER_UPDATE["f64"] * ncell * a.batch_iters * a.steps / wall / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"batch of {len(dims)} FP64 grids, each axis from 32..192 step 16 (seed 0), "
+                               f"blocks <= {a.block[0]}x{a.block[1]}x{a.block[2]}, {a.batch_iters} iterations "
+                               f"+ per-grid residuals per step, {a.mode} form, autotuned",
+                   "cells": ncell, "blocks": info["n_blocks"], "units": info["n_units"],
+                   "autotune": tune},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None},
+        "plain_form_cell_updates_per_s": plain,
+        "speedup_vs_plain_form": value / plain,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank, world, local, pg = dist_setup(a.gpus)
     try:
         if a.impl == "reference":
             run_reference(a, rank, world, pg)
+        elif a.workload == "batch":
+            run_batch(a, rank, world, local, pg)
         else:
             run_ours(a, rank, world, local, pg)
     finally:

@@ -97,7 +97,23 @@ typedef struct {
     int64_t iterations;      /* iterations completed (enqueued) so far       */
     int64_t device_bytes;    /* device memory held by the context            */
     int64_t kernel_launches; /* kernels this context has launched so far     */
+    int32_t n_instances;     /* grids held by the context                    */
+    int32_t tile_w;          /* tile width of the update engine (16/32/64)  */
+    int32_t zdepth;          /* planes per work unit (0: whole block)        */
+    int32_t n_units;         /* work units (tile x z-chunk) per iteration    */
+    int32_t n_blocks;        /* blocks over all instances                    */
 } jac_info_t;
+
+/* Result of jac_autotune: the chosen configuration and every trial. */
+typedef struct {
+    int32_t tile_w;                 /* chosen tile width                    */
+    int32_t zdepth;                 /* chosen z depth (0: whole block)      */
+    double ms_per_iter;             /* its time per iteration               */
+    int32_t n_trials;
+    int32_t trial_tile_w[16];
+    int32_t trial_zdepth[16];
+    double trial_ms_per_iter[16];
+} jac_tune_t;
 
 /* ------------------------------------------------------------------ */
 /* Memory hook                                                         */
@@ -135,6 +151,19 @@ int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void *user);
  * JAC_ENOMEM if device memory runs out, JAC_ECUDA on other CUDA errors. */
 int jac_create(jac_ctx **out, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by,
                int32_t bz, int32_t dtype, const double bc[6], void *stream);
+
+/* Create a context holding n_inst independent grids that are stored in one
+ * pool, described by one block table and advanced by the same launches
+ * (batching several problems into one persistent or fused launch; the
+ * paper's overdecomposition, Section IV-A, applied across problems).
+ *   dims     3*n_inst values: nx, ny, nz of grid i at dims[3i .. 3i+2].
+ *   bc       6*n_inst Dirichlet values, grid i at bc[6i .. 6i+5].
+ *   others   as jac_create; every grid uses the same requested block dims
+ *            (each axis of each grid is split as jac_create describes).
+ * Dense host/device arrays of the whole context hold the grids back to back
+ * in instance order, each x fastest. */
+int jac_create_batch(jac_ctx **out, int32_t n_inst, const int64_t *dims, int32_t bx, int32_t by,
+                     int32_t bz, int32_t dtype, const double *bc, void *stream);
 
 /* Release the context and all of its device memory after its stream has
  * drained. NULL is accepted. */
@@ -199,8 +228,35 @@ int jac_iterate(jac_ctx *h, int64_t n_iters);
 int jac_residual(jac_ctx *h, double *out);
 
 /* Enqueue the residual computation and write rho into device memory
- * `dev_out` (one double). Stream-ordered, no host sync. */
+ * `dev_out` (one double). Stream-ordered, no host sync. For a batch context
+ * rho covers all grids: sqrt of the sum over every grid's cells. */
 int jac_residual_device(jac_ctx *h, double *dev_out);
+
+/* Per-grid residuals of a batch context: out[i] = rho of grid i, same
+ * definition as jac_residual. The host form synchronises; the device form
+ * writes n_instances doubles to dev_out, stream-ordered. */
+int jac_residual_instances(jac_ctx *h, double *out);
+int jac_residual_instances_device(jac_ctx *h, double *dev_out);
+
+/* Write or read one grid of a batch context (n_cells = that grid's cells,
+ * x fastest); as jac_write / jac_write_device / jac_read /
+ * jac_read_device otherwise. Writing resets that grid's frame only and does
+ * not change the iteration count. */
+int jac_write_instance(jac_ctx *h, int32_t i, const double *host, size_t n_cells);
+int jac_write_instance_device(jac_ctx *h, int32_t i, const void *dev, size_t n_cells, int32_t dtype);
+int jac_read_instance(jac_ctx *h, int32_t i, double *host, size_t n_cells);
+int jac_read_instance_device(jac_ctx *h, int32_t i, void *dev, size_t n_cells, int32_t dtype);
+
+/* Tile shape of the update engine: 512 threads as tile_w x (512/tile_w)
+ * columns (tile_w 16, 32 or 64), each work unit covering zdepth planes of a
+ * block (0: all of them). Results do not depend on it. Synchronises. */
+int jac_set_tile(jac_ctx *h, int32_t tile_w, int32_t zdepth);
+
+/* Autotuner: time trial_iters iterations of the current mode for every tile
+ * width and z depth, keep the fastest (reported in *result, may be NULL),
+ * and restore the grid and iteration count exactly as they were. Needs
+ * temporary device memory for one copy of the block storage. Synchronises. */
+int jac_autotune(jac_ctx *h, int32_t trial_iters, jac_tune_t *result);
 
 /* Wait for the context's stream and report a device-side wait timeout
  * (JAC_ETIMEOUT) or a CUDA error (JAC_ECUDA). */

@@ -23,4 +23,4 @@ from ._lib import (  # noqa: F401
     MODES,
     load,
 )
-from .solver import Jacobi3D, use_torch_allocator  # noqa: F401
+from .solver import Jacobi3D, Jacobi3DBatch, use_torch_allocator  # noqa: F401

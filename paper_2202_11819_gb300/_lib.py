@@ -61,6 +61,23 @@ class jac_info_t(ctypes.Structure):
         ("iterations", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
         ("kernel_launches", ctypes.c_int64),
+        ("n_instances", ctypes.c_int32),
+        ("tile_w", ctypes.c_int32),
+        ("zdepth", ctypes.c_int32),
+        ("n_units", ctypes.c_int32),
+        ("n_blocks", ctypes.c_int32),
+    ]
+
+
+class jac_tune_t(ctypes.Structure):
+    _fields_ = [
+        ("tile_w", ctypes.c_int32),
+        ("zdepth", ctypes.c_int32),
+        ("ms_per_iter", ctypes.c_double),
+        ("n_trials", ctypes.c_int32),
+        ("trial_tile_w", ctypes.c_int32 * 16),
+        ("trial_zdepth", ctypes.c_int32 * 16),
+        ("trial_ms_per_iter", ctypes.c_double * 16),
     ]
 
 
@@ -93,6 +110,19 @@ _SIGS = {
     "jac_last_error": ([], ctypes.c_char_p),
     "jac_set_wait_limit_ns": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
     "jac_debug_withhold_progress": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64], ctypes.c_int),
+    "jac_create_batch": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32,
+                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p],
+                         ctypes.c_int),
+    "jac_write_instance": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_write_instance_device": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.c_int32], ctypes.c_int),
+    "jac_read_instance": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_read_instance_device": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
+                                  ctypes.c_int32], ctypes.c_int),
+    "jac_residual_instances": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "jac_residual_instances_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "jac_set_tile": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "jac_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(jac_tune_t)], ctypes.c_int),
     "jac_residual_dense_noalloc": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
@@ -240,7 +270,68 @@ def jac_info(h) -> dict:
         "iterations": info.iterations,
         "device_bytes": info.device_bytes,
         "kernel_launches": info.kernel_launches,
+        "n_instances": info.n_instances,
+        "tile_w": info.tile_w,
+        "zdepth": info.zdepth,
+        "n_units": info.n_units,
+        "n_blocks": info.n_blocks,
     }
+
+
+def jac_create_batch(dims, bx, by, bz, dtype=JAC_F64, bcs=None, stream=None) -> ctypes.c_void_p:
+    """``dims``: list of (nx, ny, nz); ``bcs``: list of 6-tuples (one per grid)."""
+    lib = load()
+    n = len(dims)
+    d = np.ascontiguousarray(np.asarray(dims, dtype=np.int64).reshape(n, 3))
+    b = np.ascontiguousarray(np.asarray(bcs if bcs is not None else [(0.0,) * 6] * n, dtype=np.float64).reshape(n, 6))
+    h = ctypes.c_void_p()
+    _check(lib.jac_create_batch(ctypes.byref(h), n, d.ctypes.data, int(bx), int(by), int(bz), int(dtype),
+                                b.ctypes.data, ctypes.c_void_p(stream or 0)), "jac_create_batch")
+    return h
+
+
+def jac_write_instance(h, i: int, host: np.ndarray) -> None:
+    a = _host(host, np.float64)
+    _check(load().jac_write_instance(h, int(i), a.ctypes.data, a.size), "jac_write_instance")
+
+
+def jac_write_instance_device(h, i: int, dev_ptr: int, n_cells: int, dtype: int) -> None:
+    _check(load().jac_write_instance_device(h, int(i), ctypes.c_void_p(dev_ptr), int(n_cells), int(dtype)),
+           "jac_write_instance_device")
+
+
+def jac_read_instance(h, i: int, out: np.ndarray) -> np.ndarray:
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array")
+    _check(load().jac_read_instance(h, int(i), out.ctypes.data, out.size), "jac_read_instance")
+    return out
+
+
+def jac_read_instance_device(h, i: int, dev_ptr: int, n_cells: int, dtype: int) -> None:
+    _check(load().jac_read_instance_device(h, int(i), ctypes.c_void_p(dev_ptr), int(n_cells), int(dtype)),
+           "jac_read_instance_device")
+
+
+def jac_residual_instances(h, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.float64)
+    _check(load().jac_residual_instances(h, out.ctypes.data), "jac_residual_instances")
+    return out
+
+
+def jac_residual_instances_device(h, dev_ptr: int) -> None:
+    _check(load().jac_residual_instances_device(h, ctypes.c_void_p(dev_ptr)), "jac_residual_instances_device")
+
+
+def jac_set_tile(h, tile_w: int, zdepth: int) -> None:
+    _check(load().jac_set_tile(h, int(tile_w), int(zdepth)), "jac_set_tile")
+
+
+def jac_autotune(h, trial_iters: int) -> dict:
+    r = jac_tune_t()
+    _check(load().jac_autotune(h, int(trial_iters), ctypes.byref(r)), "jac_autotune")
+    n = min(r.n_trials, 16)
+    return {"tile_w": r.tile_w, "zdepth": r.zdepth, "ms_per_iter": r.ms_per_iter,
+            "trials": [(r.trial_tile_w[i], r.trial_zdepth[i], r.trial_ms_per_iter[i]) for i in range(n)]}
 
 
 def jac_set_wait_limit_ns(h, ns: int) -> None:

@@ -44,10 +44,12 @@ struct BlockDesc {
     int32_t pad;
 };
 
-// One unit of fused / persistent work: a column tile of one block.
+// One unit of fused / persistent work: a column tile of one block over the
+// planes z0 .. z1-1.
 struct TileUnit {
     int32_t block;
     int16_t x0, y0;
+    int16_t z0, z1;
 };
 
 // Error word values written by kernels (read back by the host at syncs).

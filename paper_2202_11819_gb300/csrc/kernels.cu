@@ -32,15 +32,11 @@
 
 namespace jac {
 
-// Tile of the z-marching update: 32 x 16 threads, one column each, so one
-// tile covers 32 x 16 columns of a block (a 128-byte-aligned 256-byte row
-// segment per warp for binary64).
-constexpr int kTX = 32;
-constexpr int kTY = 16;
-constexpr int kVX = 1;
-constexpr int kTW = kTX * kVX;
-constexpr int kSW = kTW + 2;  // shared row with one halo cell on each side
-constexpr int kSmemCells = (kTY + 2) * kSW;
+// Tile of the z-marching update: 512 threads, one column each, as TW x
+// (512 / TW) columns of a block; TW (16, 32 or 64) is chosen per context (the
+// autotuner times the three). Each tile covers a z range [z0, z1) of the
+// block, so the z depth of a work unit is chosen too.
+constexpr int kThreads = 512;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
@@ -212,28 +208,29 @@ struct SlowList {
     uint32_t cell[kSlowMax];  // (k << 9) | tid
 };
 
-// The z-marching engine over one tile (x0 .. x0+31, y0 .. y0+15, all k) of
-// block b, reading buffer p.
+// The z-marching engine over one tile (x0 .. x0+TW-1, y0 .. y0+512/TW-1,
+// planes z0 .. z1-1) of block b, reading buffer p.
 //   OP_SEQ / OP_EXACT: writes the interior of buffer p^1;
 //   OP_RES:           returns this thread's sum of L^2 (thread 0 also adds the
 //                     cells recomputed exactly, in (k, tid) order).
-// Every shared slot of the tile plane (the 32 x 16 interior plus its halo
-// ring) is a stream along z (pointer + plane stride, or a constant): own
-// columns, halo cells that fall inside the tile where it overhangs the block
-// edge, and one extra ring slot for each of the first 96 threads. Values are
+// Every shared slot of the tile plane (the interior plus its halo ring) is a
+// stream along z (pointer + plane stride, or a constant): own columns, halo
+// cells that fall inside the tile where it overhangs the block edge, and one
+// extra ring slot for each of the first 2 (TW + 512/TW) threads. Values are
 // loaded D planes ahead into registers, converted once (to the grid frame for
 // the exact ops), stored in a double-buffered shared plane (one barrier per
 // plane), and the z neighbours are carried in registers.
-template <typename T, int OP, bool PULL, bool CG, int D>
+template <typename T, int OP, bool PULL, bool CG, int D, int TW>
 __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
-                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0,
+                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
                               typename Elem<T, OP>::type* sm, SlowList* slow)
 {
     using E = typename Elem<T, OP>::type;
+    constexpr int kTX = TW, kTY = kThreads / TW, kTW = TW, kSW = TW + 2;
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     const int eref = (OP == OP_SEQ) ? 0 : frame_e[d.inst] + 1;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kTX + tx;
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const int x = x0 + tx, y = y0 + ty;
     const int64_t plane = d.plane;
     if (OP != OP_SEQ && tid == 0) slow->n = 0;
@@ -242,7 +239,7 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     int kind = 0;
     const T* sp = pool;
     int64_t ss = 0;
-    const T* zhi = pool;
+    const T* zhi = pool;  // the value above the last plane of the range
     int64_t oidx = 0;
     E wzm{}, wc{};
     T ring[D + 1];  // interior: planes k+1 .. k+1+D; halo: planes k .. k+D
@@ -252,14 +249,15 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         kind = 1;
         sp = pool + cell_index<T>(d, p, x, y, 0);
         ss = plane;
-        zhi = z_source<T, PULL>(pool, desc, d, p, x, y, 5);
+        zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : sp + z1 * plane;
         oidx = cell_index<T>(d, p ^ 1, x, y, 0);
-        wzm = conv<T, OP>(ldv<T, CG>(z_source<T, PULL>(pool, desc, d, p, x, y, 4)), eref);
-        wc = conv<T, OP>(ldv<T, CG>(sp), eref);
+        const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : sp + (z0 - 1) * plane;
+        wzm = conv<T, OP>(ldv<T, CG>(zlo), eref);
+        wc = conv<T, OP>(ldv<T, CG>(sp + z0 * plane), eref);
 #pragma unroll
         for (int i = 0; i < D; ++i) {
-            const int q = 1 + i;
-            ring[i] = q < bz ? ldv<T, CG>(sp + q * ss) : (q == bz ? ldv<T, CG>(zhi) : T(0));
+            const int q = z0 + 1 + i;
+            ring[i] = q < z1 ? ldv<T, CG>(sp + q * ss) : (q == z1 ? ldv<T, CG>(zhi) : T(0));
         }
     } else if ((x == bx && y < by) || (y == by && x < bx)) {
         kind = 2;
@@ -267,10 +265,10 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         sp = s.p;
         ss = s.stride;
 #pragma unroll
-        for (int i = 0; i < D; ++i) ring[i] = i < bz ? ldv<T, CG>(sp + i * ss) : T(0);
+        for (int i = 0; i < D; ++i) ring[i] = z0 + i < z1 ? ldv<T, CG>(sp + (z0 + i) * ss) : T(0);
     }
-    // one ring slot per thread for tid < 96: row y0-1, row y0+16, column
-    // x0-1, column x0+32 (only the slots some interior cell reads)
+    // one ring slot per thread for tid < 2 (TW + TY): row y0-1, row y0+TY,
+    // column x0-1, column x0+TW (only the slots some interior cell reads)
     int er = -1, ec = 0;
     const T* ep = pool;
     int64_t es = 0;
@@ -312,23 +310,23 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
             ep = s.p;
             es = s.stride;
 #pragma unroll
-            for (int i = 0; i < D; ++i) ering[i] = i < bz ? ldv<T, CG>(ep + i * es) : T(0);
+            for (int i = 0; i < D; ++i) ering[i] = z0 + i < z1 ? ldv<T, CG>(ep + (z0 + i) * es) : T(0);
         }
     }
     if (OP != OP_SEQ) __syncthreads();  // slow->n = 0 visible before any append
 
     double acc = 0.0;
 #pragma unroll 2
-    for (int k = 0; k < bz; ++k) {
+    for (int k = z0; k < z1; ++k) {
         E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
         // issue the loads D planes ahead
         if (kind == 1) {
             const int q = k + 1 + D;
-            ring[D] = q < bz ? ldv<T, CG>(sp + q * ss) : (q == bz ? ldv<T, CG>(zhi) : T(0));
+            ring[D] = q < z1 ? ldv<T, CG>(sp + q * ss) : (q == z1 ? ldv<T, CG>(zhi) : T(0));
         } else if (kind == 2) {
-            ring[D] = k + D < bz ? ldv<T, CG>(sp + (k + D) * ss) : T(0);
+            ring[D] = k + D < z1 ? ldv<T, CG>(sp + (k + D) * ss) : T(0);
         }
-        if (er >= 0) ering[D] = k + D < bz ? ldv<T, CG>(ep + (k + D) * es) : T(0);
+        if (er >= 0) ering[D] = k + D < z1 ? ldv<T, CG>(ep + (k + D) * es) : T(0);
         // this plane's shared slots
         E* slot = buf + (ty + 1) * kSW + tx + 1;
         if (kind == 1) *slot = wc;
@@ -370,7 +368,7 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         if (n > 0) {
             if (n <= kSlowMax) {
                 if constexpr (OP == OP_EXACT) {
-                    for (int i = tid; i < n; i += kTX * kTY) {
+                    for (int i = tid; i < n; i += kThreads) {
                         const uint32_t c = slow->cell[i];
                         const int kk = (int)(c >> 9), t = (int)(c & 511u);
                         const int cx = x0 + t % kTX, cy = y0 + t / kTX;
@@ -400,12 +398,12 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
                 // whole tile with the exact per-cell routines
                 if constexpr (OP == OP_EXACT) {
                     if (kind == 1)
-                        for (int kk = 0; kk < bz; ++kk)
+                        for (int kk = z0; kk < z1; ++kk)
                             pool[oidx + kk * plane] = (T)exact_cell<T, PULL, CG, false>(pool, desc, b, p, x, y, kk);
                 } else {
                     acc = 0.0;
                     if (kind == 1)
-                        for (int kk = 0; kk < bz; ++kk) {
+                        for (int kk = z0; kk < z1; ++kk) {
                             const double L = exact_cell<T, PULL, CG, true>(pool, desc, b, p, x, y, kk);
                             acc = fma(L, L, acc);
                         }
@@ -416,38 +414,37 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     return acc;
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int TW>
 __host__ __device__ constexpr int smem_bytes()
 {
-    return 2 * (kTY + 2) * kSW * (int)sizeof(typename Elem<T, OP>::type);
+    return 2 * (kThreads / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
 }
-
-// ---------------------------------------------------------------- kernels
 
 // prefetch depth: binary32 tiles are bandwidth-bound and need more bytes in
 // flight; binary64 tiles are bound by the arithmetic
 template <typename T>
 constexpr int kDepth = sizeof(T) == 4 ? 6 : 3;
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(kTX * kTY, 2) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
-                                                                int b, int p)
+template <typename T, int OP, int TW>
+__global__ void __launch_bounds__(kThreads, 2) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+                                                               int b, int p)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
-    tile_engine<T, OP, false, false, kDepth<T>>(pool, desc, frame_e, b, p, blockIdx.x * kTW, blockIdx.y * kTY,
-                                                (typename Elem<T, OP>::type*)sm, &slow);
+    tile_engine<T, OP, false, false, kDepth<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
+                                                    blockIdx.y * (kThreads / TW), 0, desc[b].ext[2],
+                                                    (typename Elem<T, OP>::type*)sm, &slow);
 }
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(kTX * kTY, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
-                                                             const TileUnit* units, int p)
+template <typename T, int OP, int TW>
+__global__ void __launch_bounds__(kThreads, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+                                                            const TileUnit* units, int p)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
-    tile_engine<T, OP, true, false, kDepth<T>>(pool, desc, frame_e, u.block, p, u.x0, u.y0,
-                                               (typename Elem<T, OP>::type*)sm, &slow);
+    tile_engine<T, OP, true, false, kDepth<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                   (typename Elem<T, OP>::type*)sm, &slow);
 }
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -479,18 +476,18 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // overwrites (buffer p^1 held iteration t-1). The seven counters are polled
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
-template <typename T, int OP>
-__global__ void __launch_bounds__(kTX * kTY, 2)
+template <typename T, int OP, int TW>
+__global__ void __launch_bounds__(kThreads, 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP>()];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
     __shared__ long long s_next;
     __shared__ int s_stop;
     const long long total = (long long)n_iters * nunits;
-    const int tid = threadIdx.y * kTX + threadIdx.x;
+    const int tid = threadIdx.x;
     if (tid == 0) s_next = (long long)atomicAdd(work, 1ull);
     __syncthreads();
     for (;;) {
@@ -530,8 +527,8 @@ __global__ void __launch_bounds__(kTX * kTY, 2)
         if (s_stop) break;
         // take the next unit now; its index is read after this one finishes
         if (tid == 0) s_next = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
-        tile_engine<T, OP, true, true, kDepth<T>>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
-                                                  (typename Elem<T, OP>::type*)sm, &slow);
+        tile_engine<T, OP, true, true, kDepth<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0,
+                                                      u.z1, (typename Elem<T, OP>::type*)sm, &slow);
         __syncthreads();
         if (tid == 0 && !(u.block == hold_block && t >= hold_after)) {
             __threadfence();
@@ -542,25 +539,42 @@ __global__ void __launch_bounds__(kTX * kTY, 2)
 
 // Residual: per CTA the sum over its tile of L^2 (L the exact Laplacian term
 // rounded once), in a fixed order (per thread over k, then a fixed tree).
-template <typename T>
-__global__ void __launch_bounds__(kTX * kTY, 2) k_residual(const T* pool, const BlockDesc* desc,
-                                                           const int32_t* frame_e, const TileUnit* units, int p,
-                                                           double* partials)
+template <typename T, int TW>
+__global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const BlockDesc* desc,
+                                                          const int32_t* frame_e, const TileUnit* units, int p,
+                                                          double* partials)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP_RES>()];
+    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP_RES, TW>()];
     __shared__ SlowList slow;
-    __shared__ double red[kTX * kTY];
+    __shared__ double red[kThreads];
     const TileUnit u = units[blockIdx.x];
-    const double acc = tile_engine<T, OP_RES, true, false, 2>(const_cast<T*>(pool), desc, frame_e, u.block, p, u.x0,
-                                                              u.y0, (frame::W96*)sm, &slow);
-    const int tid = threadIdx.y * kTX + threadIdx.x;
+    const double acc = tile_engine<T, OP_RES, true, false, 2, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                  u.x0, u.y0, u.z0, u.z1, (frame::W96*)sm, &slow);
+    const int tid = threadIdx.x;
     red[tid] = acc;
     __syncthreads();
-    for (int s = kTX * kTY / 2; s > 0; s >>= 1) {
+    for (int s = kThreads / 2; s > 0; s >>= 1) {
         if (tid < s) red[tid] = red[tid] + red[tid + s];
         __syncthreads();
     }
     if (tid == 0) partials[blockIdx.x] = red[0];
+}
+
+// Per-instance residuals: instance i owns partials [seg[i], seg[i+1]); one
+// CTA per instance sums them in a fixed order.
+__global__ void k_sum_segments(const double* partials, const int32_t* seg, double* out)
+{
+    __shared__ double red[256];
+    const int i = blockIdx.x;
+    double acc = 0.0;
+    for (int j = seg[i] + (int)threadIdx.x; j < seg[i + 1]; j += blockDim.x) acc = acc + partials[j];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = sqrt(red[0]);
 }
 
 __global__ void k_sum_partials(const double* partials, int n, double* out)
@@ -660,14 +674,15 @@ __global__ void k_unpack6(T* pool, const BlockDesc* desc, int b, int p, const T*
 // Dense x-fastest instance arrays <-> block interiors (buffer p). Grid x is
 // the block, grid y strides over the block's rows; threads walk x.
 template <typename TS, typename TD>
-__global__ void k_scatter(const TS* dense, TD* pool, const BlockDesc* desc, int p, int32_t* frame_e)
+__global__ void k_scatter(const TS* dense, TD* pool, const BlockDesc* desc, int b0, int64_t dense_base, int p,
+                          int32_t* frame_e)
 {
-    const BlockDesc& d = desc[blockIdx.x];
+    const BlockDesc& d = desc[b0 + blockIdx.x];
     const int rows = d.ext[1] * d.ext[2];
     int emax = 0;
     for (int r = blockIdx.y; r < rows; r += gridDim.y) {
         const int y = r % d.ext[1], k = r / d.ext[1];
-        const int64_t g = d.dense + (int64_t)d.org[0] +
+        const int64_t g = d.dense - dense_base + (int64_t)d.org[0] +
                           (int64_t)d.gdim[0] * ((int64_t)(d.org[1] + y) + (int64_t)d.gdim[1] * (d.org[2] + k));
         for (int x = threadIdx.x; x < d.ext[0]; x += blockDim.x) {
             const TD v = (TD)dense[g + x];
@@ -681,16 +696,16 @@ __global__ void k_scatter(const TS* dense, TD* pool, const BlockDesc* desc, int 
 }
 
 template <typename TS, typename TD>
-__global__ void k_gather(const TS* pool, TD* dense, const BlockDesc* desc, int p)
+__global__ void k_gather(const TS* pool, TD* dense, const BlockDesc* desc, int b0, int64_t dense_base, int p)
 {
-    const BlockDesc& d = desc[blockIdx.x];
+    const BlockDesc& d = desc[b0 + blockIdx.x];
     const int rows = d.ext[1] * d.ext[2];
     for (int r = blockIdx.y; r < rows; r += gridDim.y) {
         const int y = r % d.ext[1], k = r / d.ext[1];
         const int64_t g = d.dense + (int64_t)d.org[0] +
                           (int64_t)d.gdim[0] * ((int64_t)(d.org[1] + y) + (int64_t)d.gdim[1] * (d.org[2] + k));
         for (int x = threadIdx.x; x < d.ext[0]; x += blockDim.x)
-            dense[g + x] = (TD)pool[cell_index<TS>(d, p, x, y, k)];
+            dense[g - dense_base + x] = (TD)pool[cell_index<TS>(d, p, x, y, k)];
     }
 }
 
@@ -714,94 +729,135 @@ __global__ void k_init_ghosts(T* pool, const BlockDesc* desc)
 
 // ---------------------------------------------------------------- launchers
 
-static inline dim3 tile_block() { return dim3(kTX, kTY, 1); }
+int tile_rows(int tw) { return kThreads / tw; }
+int engine_threads() { return kThreads; }
+bool tile_width_supported(int tw) { return tw == 16 || tw == 32 || tw == 64; }
 
-int tile_width() { return kTW; }
-int tile_height() { return kTY; }
+#define JAC_TW_DISPATCH(tw, CALL) \
+    switch (tw) {                 \
+        case 16: {                \
+            constexpr int TW = 16; \
+            CALL;                 \
+            break;                \
+        }                         \
+        case 64: {                \
+            constexpr int TW = 64; \
+            CALL;                 \
+            break;                \
+        }                         \
+        default: {                \
+            constexpr int TW = 32; \
+            CALL;                 \
+            break;                \
+        }                         \
+    }
 
-template <typename T>
-static cudaError_t stencil_block_t(const LaunchArgs& a, int arith, int b, int nx_tiles, int ny_tiles, int p,
-                                   cudaStream_t s)
+template <typename T, int TW>
+static void stencil_block_t(const LaunchArgs& a, int arith, int b, int nx_tiles, int ny_tiles, int p, cudaStream_t s)
 {
     dim3 grid(nx_tiles, ny_tiles, 1);
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_stencil_block<T, OP_EXACT><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
-            return cudaGetLastError();
+            k_stencil_block<T, OP_EXACT, TW><<<grid, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
+            return;
         }
     }
-    k_stencil_block<T, OP_SEQ><<<grid, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
-    return cudaGetLastError();
+    k_stencil_block<T, OP_SEQ, TW><<<grid, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
 }
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
                                  int p, cudaStream_t s)
 {
-    return dtype_f32 ? stencil_block_t<float>(a, arith, b, nx_tiles, ny_tiles, p, s)
-                     : stencil_block_t<double>(a, arith, b, nx_tiles, ny_tiles, p, s);
+    if (dtype_f32) JAC_TW_DISPATCH(a.tile_w, (stencil_block_t<float, TW>(a, arith, b, nx_tiles, ny_tiles, p, s)))
+    else JAC_TW_DISPATCH(a.tile_w, (stencil_block_t<double, TW>(a, arith, b, nx_tiles, ny_tiles, p, s)))
+    return cudaGetLastError();
 }
 
-template <typename T>
-static cudaError_t fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
+template <typename T, int TW>
+static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
 {
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_fused_step<T, OP_EXACT><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
-            return cudaGetLastError();
+            k_fused_step<T, OP_EXACT, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+            return;
         }
     }
-    k_fused_step<T, OP_SEQ><<<a.nunits, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
-    return cudaGetLastError();
+    k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
 }
 
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
 {
-    return dtype_f32 ? fused_step_t<float>(a, arith, p, s) : fused_step_t<double>(a, arith, p, s);
+    if (dtype_f32) JAC_TW_DISPATCH(a.tile_w, (fused_step_t<float, TW>(a, arith, p, s)))
+    else JAC_TW_DISPATCH(a.tile_w, (fused_step_t<double, TW>(a, arith, p, s)))
+    return cudaGetLastError();
 }
 
-const void* persistent_kernel(int dtype_f32, int arith)
+template <int TW>
+static const void* persistent_fn(int dtype_f32, int arith)
 {
-    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ>;
-    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT> : (const void*)k_persistent<double, OP_SEQ>;
+    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, TW>;
+    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, TW> : (const void*)k_persistent<double, OP_SEQ, TW>;
 }
 
-int persistent_block_threads() { return kTX * kTY; }
+const void* persistent_kernel(int dtype_f32, int arith, int tw)
+{
+    const void* f = nullptr;
+    JAC_TW_DISPATCH(tw, (f = persistent_fn<TW>(dtype_f32, arith)))
+    return f;
+}
 
-template <typename T>
-static cudaError_t persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith, int ctas, cudaStream_t s)
+int persistent_block_threads() { return kThreads; }
+
+template <typename T, int TW>
+static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith, int ctas, cudaStream_t s)
 {
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_persistent<T, OP_EXACT><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
+            k_persistent<T, OP_EXACT, TW><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
                                                                     q.p0, q.n_iters, q.done, q.work, q.status,
                                                                     q.wait_ns, q.hold_block, q.hold_after);
-            return cudaGetLastError();
+            return;
         }
     }
-    k_persistent<T, OP_SEQ><<<ctas, tile_block(), 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+    k_persistent<T, OP_SEQ, TW><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
                                                           q.n_iters, q.done, q.work, q.status, q.wait_ns,
                                                           q.hold_block, q.hold_after);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int dtype_f32, int arith, int ctas,
                               cudaStream_t s)
 {
-    return dtype_f32 ? persistent_t<float>(a, q, arith, ctas, s) : persistent_t<double>(a, q, arith, ctas, s);
+    if (dtype_f32) JAC_TW_DISPATCH(a.tile_w, (persistent_t<float, TW>(a, q, arith, ctas, s)))
+    else JAC_TW_DISPATCH(a.tile_w, (persistent_t<double, TW>(a, q, arith, ctas, s)))
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
+{
+    if (dtype_f32)
+        JAC_TW_DISPATCH(a.tile_w, (k_residual<float, TW><<<a.nunits, kThreads, 0, s>>>(
+                                      (const float*)a.pool, a.desc, a.frame, a.units, p, partials)))
+    else
+        JAC_TW_DISPATCH(a.tile_w, (k_residual<double, TW><<<a.nunits, kThreads, 0, s>>>(
+                                      (const double*)a.pool, a.desc, a.frame, a.units, p, partials)))
+    return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
                             cudaStream_t s)
 {
-    if (dtype_f32)
-        k_residual<float><<<a.nunits, tile_block(), 0, s>>>((const float*)a.pool, a.desc, a.frame, a.units, p,
-                                                             partials);
-    else
-        k_residual<double><<<a.nunits, tile_block(), 0, s>>>((const double*)a.pool, a.desc, a.frame, a.units, p,
-                                                              partials);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_residual_partials(a, dtype_f32, p, partials, s);
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 256, 0, s>>>(partials, a.nunits, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_segments(const LaunchArgs& a, int dtype_f32, int p, double* partials, const int32_t* seg,
+                                     int nseg, double* out, cudaStream_t s)
+{
+    cudaError_t e = launch_residual_partials(a, dtype_f32, p, partials, s);
+    if (e != cudaSuccess) return e;
+    k_sum_segments<<<nseg, 256, 0, s>>>(partials, seg, out);
     return cudaGetLastError();
 }
 
@@ -841,28 +897,37 @@ cudaError_t launch_unpack6(const LaunchArgs& a, int dtype_f32, int b, int p, con
     return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int p, cudaStream_t s)
+cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int b0, int nb,
+                           int64_t dense_base, int p, cudaStream_t s)
 {
-    dim3 grid(a.nblocks, 16, 1);
+    dim3 grid(nb, 16, 1);
     if (dtype_f32) {
         if (src_f32)
-            k_scatter<float, float><<<grid, 256, 0, s>>>((const float*)dense, (float*)a.pool, a.desc, p, a.frame);
+            k_scatter<float, float><<<grid, 256, 0, s>>>((const float*)dense, (float*)a.pool, a.desc, b0, dense_base,
+                                                         p, a.frame);
         else
-            k_scatter<double, float><<<grid, 256, 0, s>>>((const double*)dense, (float*)a.pool, a.desc, p, a.frame);
+            k_scatter<double, float><<<grid, 256, 0, s>>>((const double*)dense, (float*)a.pool, a.desc, b0,
+                                                          dense_base, p, a.frame);
     } else {
-        k_scatter<double, double><<<grid, 256, 0, s>>>((const double*)dense, (double*)a.pool, a.desc, p, a.frame);
+        k_scatter<double, double><<<grid, 256, 0, s>>>((const double*)dense, (double*)a.pool, a.desc, b0, dense_base,
+                                                       p, a.frame);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int p, cudaStream_t s)
+cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int b0, int nb,
+                          int64_t dense_base, int p, cudaStream_t s)
 {
-    dim3 grid(a.nblocks, 16, 1);
+    dim3 grid(nb, 16, 1);
     if (dtype_f32) {
-        if (dst_f32) k_gather<float, float><<<grid, 256, 0, s>>>((const float*)a.pool, (float*)dense, a.desc, p);
-        else k_gather<float, double><<<grid, 256, 0, s>>>((const float*)a.pool, (double*)dense, a.desc, p);
+        if (dst_f32)
+            k_gather<float, float><<<grid, 256, 0, s>>>((const float*)a.pool, (float*)dense, a.desc, b0, dense_base, p);
+        else
+            k_gather<float, double><<<grid, 256, 0, s>>>((const float*)a.pool, (double*)dense, a.desc, b0, dense_base,
+                                                         p);
     } else {
-        k_gather<double, double><<<grid, 256, 0, s>>>((const double*)a.pool, (double*)dense, a.desc, p);
+        k_gather<double, double><<<grid, 256, 0, s>>>((const double*)a.pool, (double*)dense, a.desc, b0, dense_base,
+                                                      p);
     }
     return cudaGetLastError();
 }

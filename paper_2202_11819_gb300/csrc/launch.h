@@ -17,6 +17,7 @@ struct LaunchArgs {
     int32_t* frame;          // per instance: largest exponent field (grid frame)
     int nblocks;
     int nunits;
+    int tile_w;              // tile width of the update engine: 16, 32 or 64
 };
 
 struct PersistentArgs {
@@ -30,10 +31,11 @@ struct PersistentArgs {
     int64_t hold_after;
 };
 
-int tile_width();
-int tile_height();
+int tile_rows(int tw);
+int engine_threads();
+bool tile_width_supported(int tw);
 int persistent_block_threads();
-const void* persistent_kernel(int dtype_f32, int arith);
+const void* persistent_kernel(int dtype_f32, int arith, int tw);
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
                                  int p, cudaStream_t s);
@@ -42,6 +44,8 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
                               cudaStream_t s);
 cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
                             cudaStream_t s);
+cudaError_t launch_residual_segments(const LaunchArgs& a, int dtype_f32, int p, double* partials, const int32_t* seg,
+                                     int nseg, double* out, cudaStream_t s);
 cudaError_t launch_pack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, void* send, int n,
                              cudaStream_t s);
 cudaError_t launch_unpack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, const void* recv, int n,
@@ -50,8 +54,10 @@ cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void*
                          int maxface, cudaStream_t s);
 cudaError_t launch_unpack6(const LaunchArgs& a, int dtype_f32, int b, int p, const void* recv, const int64_t* faceoff,
                            int maxface, cudaStream_t s);
-cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int p, cudaStream_t s);
-cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int p, cudaStream_t s);
+cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int b0, int nb,
+                           int64_t dense_base, int p, cudaStream_t s);
+cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int b0, int nb,
+                          int64_t dense_base, int p, cudaStream_t s);
 cudaError_t launch_init_ghosts(const LaunchArgs& a, int dtype_f32, cudaStream_t s);
 
 }  // namespace jac

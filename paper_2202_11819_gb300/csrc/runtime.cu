@@ -76,11 +76,27 @@ void split_axis(int64_t n, int32_t b, std::vector<int32_t>& size, std::vector<in
 
 }  // namespace
 
+// One grid of a context. A context holds one or more independent grids
+// (instances) whose blocks share one block table, one pool and one launch.
+struct Instance {
+    int64_t dims[3];
+    double bc[6];
+    int32_t bc_frame;   // largest exponent field over the boundary values
+    int64_t dense_off;  // start of this grid in dense concatenated arrays
+    int32_t b0, b1;     // its blocks [b0, b1)
+    int32_t u0, u1;     // its work units [u0, u1)
+    int32_t nb[3];
+};
+
 struct jac_ctx {
     int device = 0;
     int64_t dims[3] = {0, 0, 0};
     int32_t req_block[3] = {0, 0, 0};
     int32_t nb[3] = {0, 0, 0};
+    std::vector<Instance> inst;
+    std::vector<int32_t> hframe;  // per instance: bc_frame, the frame's starting value
+    int tile_w = 32;              // tile width of the update engine
+    int zdepth = 0;               // planes per work unit (0: the whole block)
     int dtype = JAC_F64;
     int esize = 8;
     int mode = JAC_MODE_PERSISTENT;
@@ -106,7 +122,10 @@ struct jac_ctx {
     TileUnit* dunits = nullptr;
     void* pool = nullptr;
     int32_t* frame = nullptr;  // per instance: largest exponent field of the grid and its boundary
-    int32_t bc_frame = 0;      // that field over the boundary values alone
+    int32_t* dseg = nullptr;   // per instance: first work unit (n_inst + 1 entries)
+    double* dres_inst = nullptr;
+    size_t partials_cap = 0;
+    int64_t pool_elems = 0;
     int parity = 0;
     int64_t iters = 0;
     int64_t launches = 0;
@@ -150,9 +169,16 @@ struct jac_ctx {
         a.frame = frame;
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
+        a.tile_w = tile_w;
         return a;
     }
-    int64_t ncells() const { return dims[0] * dims[1] * dims[2]; }
+    int64_t ncells() const
+    {
+        int64_t n = 0;
+        for (const Instance& I : inst) n += I.dims[0] * I.dims[1] * I.dims[2];
+        return n;
+    }
+    int64_t icells(int i) const { return inst[i].dims[0] * inst[i].dims[1] * inst[i].dims[2]; }
 };
 
 namespace {
@@ -200,98 +226,153 @@ bool value_ok(double v, int dtype)
     return std::fabs(v) <= lim;
 }
 
-int build_layout(jac_ctx* h)
+void exponent_field_max(const double* bc, int dtype, int32_t& e)
 {
-    std::vector<int32_t> sx, ox, sy, oy, sz, oz;
-    split_axis(h->dims[0], h->req_block[0], sx, ox);
-    split_axis(h->dims[1], h->req_block[1], sy, oy);
-    split_axis(h->dims[2], h->req_block[2], sz, oz);
-    h->nb[0] = (int32_t)sx.size();
-    h->nb[1] = (int32_t)sy.size();
-    h->nb[2] = (int32_t)sz.size();
-    const int64_t nblocks = (int64_t)h->nb[0] * h->nb[1] * h->nb[2];
-    if (nblocks > (1 << 24)) return fail(JAC_EINVAL, "too many blocks (%lld)", (long long)nblocks);
-    const int OX = 128 / h->esize;
-    const int TW = tile_width(), TH = tile_height();
-    h->hdesc.resize(nblocks);
-    h->ntx.resize(nblocks);
-    h->nty.resize(nblocks);
-    int64_t off = 0;
-    for (int32_t bk = 0; bk < h->nb[2]; ++bk)
-        for (int32_t bj = 0; bj < h->nb[1]; ++bj)
-            for (int32_t bi = 0; bi < h->nb[0]; ++bi) {
-                const int64_t b = bi + (int64_t)h->nb[0] * (bj + (int64_t)h->nb[1] * bk);
-                BlockDesc& d = h->hdesc[b];
-                memset(&d, 0, sizeof d);
-                d.ext[0] = sx[bi];
-                d.ext[1] = sy[bj];
-                d.ext[2] = sz[bk];
-                d.org[0] = ox[bi];
-                d.org[1] = oy[bj];
-                d.org[2] = oz[bk];
-                const int32_t ids[3] = {bi, bj, bk};
-                for (int f = 0; f < 6; ++f) {
-                    const int a = f >> 1, dir = (f & 1) ? 1 : -1;
-                    int32_t q[3] = {bi, bj, bk};
-                    q[a] = ids[a] + dir;
-                    if (q[a] < 0 || q[a] >= h->nb[a]) d.nbr[f] = -1;
-                    else d.nbr[f] = (int32_t)(q[0] + (int64_t)h->nb[0] * (q[1] + (int64_t)h->nb[1] * q[2]));
-                    d.bc[f] = h->bc[f];
-                    d.bcf[f] = (float)h->bc[f];
-                }
-                d.inst = 0;
-                d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
-                d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
-                const int64_t storage = d.plane * (d.ext[2] + 2);
-                d.off[0] = off;
-                d.off[1] = off + storage;
-                off += 2 * storage;
-                d.dense = 0;
-                d.gdim[0] = (int32_t)h->dims[0];
-                d.gdim[1] = (int32_t)h->dims[1];
-                d.gdim[2] = (int32_t)h->dims[2];
-                h->ntx[b] = (d.ext[0] + TW - 1) / TW;
-                h->nty[b] = (d.ext[1] + TH - 1) / TH;
-                d.ntiles = h->ntx[b] * h->nty[b];
-            }
-    h->hunits.clear();
-    for (int64_t b = 0; b < nblocks; ++b)
-        for (int32_t ty = 0; ty < h->nty[b]; ++ty)
-            for (int32_t tx = 0; tx < h->ntx[b]; ++tx) {
-                TileUnit u;
-                u.block = (int32_t)b;
-                u.x0 = (int16_t)(tx * TW);
-                u.y0 = (int16_t)(ty * TH);
-                h->hunits.push_back(u);
-            }
-    int rc;
-    if ((rc = dev_alloc(h, (size_t)off * h->esize, &h->pool))) return rc;
-    if ((rc = dev_alloc(h, nblocks * sizeof(BlockDesc), (void**)&h->ddesc))) return rc;
-    if ((rc = dev_alloc(h, h->hunits.size() * sizeof(TileUnit), (void**)&h->dunits))) return rc;
-    if ((rc = dev_alloc(h, nblocks * sizeof(uint32_t), (void**)&h->done))) return rc;
-    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
-    if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
-    if ((rc = dev_alloc(h, h->hunits.size() * sizeof(double), (void**)&h->partials))) return rc;
-    if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
-    if ((rc = dev_alloc(h, sizeof(int32_t), (void**)&h->frame))) return rc;
-    h->bc_frame = 0;
+    e = 0;
     for (int f = 0; f < 6; ++f) {
-        const double v = h->dtype == JAC_F32 ? (double)(float)h->bc[f] : h->bc[f];
+        const double v = dtype == JAC_F32 ? (double)(float)bc[f] : bc[f];
         uint64_t bits;
         memcpy(&bits, &v, 8);
-        h->bc_frame = std::max(h->bc_frame, (int32_t)((bits >> 52) & 0x7FF));
+        e = std::max(e, (int32_t)((bits >> 52) & 0x7FF));
     }
-    CU(cudaMemcpyAsync(h->frame, &h->bc_frame, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream), "init frame");
+}
+
+// Work units for the current tile width and z depth: per block, its column
+// tiles times its z chunks, blocks in order, so each instance's units are
+// contiguous. Uploads the tile table, the per-block unit counts and the
+// per-instance unit ranges.
+int build_units(jac_ctx* h)
+{
+    const int TW = h->tile_w, TH = tile_rows(h->tile_w);
+    const int64_t nblocks = (int64_t)h->hdesc.size();
+    h->ntx.resize(nblocks);
+    h->nty.resize(nblocks);
+    h->hunits.clear();
+    size_t ii = 0;
+    for (int64_t b = 0; b < nblocks; ++b) {
+        BlockDesc& d = h->hdesc[b];
+        while (ii < h->inst.size() && b >= h->inst[ii].b1) ++ii;
+        if (ii < h->inst.size() && b == h->inst[ii].b0) h->inst[ii].u0 = (int32_t)h->hunits.size();
+        h->ntx[b] = (d.ext[0] + TW - 1) / TW;
+        h->nty[b] = (d.ext[1] + TH - 1) / TH;
+        const int zd = h->zdepth > 0 ? h->zdepth : d.ext[2];
+        const int nzc = (d.ext[2] + zd - 1) / zd;
+        d.ntiles = h->ntx[b] * h->nty[b] * nzc;
+        for (int zc = 0; zc < nzc; ++zc)
+            for (int32_t ty = 0; ty < h->nty[b]; ++ty)
+                for (int32_t tx = 0; tx < h->ntx[b]; ++tx) {
+                    TileUnit u;
+                    u.block = (int32_t)b;
+                    u.x0 = (int16_t)(tx * TW);
+                    u.y0 = (int16_t)(ty * TH);
+                    u.z0 = (int16_t)(zc * zd);
+                    u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
+                    h->hunits.push_back(u);
+                }
+        if (ii < h->inst.size() && b + 1 == h->inst[ii].b1) h->inst[ii].u1 = (int32_t)h->hunits.size();
+    }
+    std::vector<int32_t> seg(h->inst.size() + 1);
+    for (size_t i = 0; i < h->inst.size(); ++i) seg[i] = h->inst[i].u0;
+    seg[h->inst.size()] = (int32_t)h->hunits.size();
+    int rc;
+    if (h->hunits.size() > h->partials_cap) {
+        // earlier, smaller tables stay allocated until the context is destroyed
+        if ((rc = dev_alloc(h, h->hunits.size() * sizeof(TileUnit), (void**)&h->dunits))) return rc;
+        if ((rc = dev_alloc(h, h->hunits.size() * sizeof(double), (void**)&h->partials))) return rc;
+        h->partials_cap = h->hunits.size();
+    }
     CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), nblocks * sizeof(BlockDesc), cudaMemcpyHostToDevice, h->stream),
        "copy block table");
     CU(cudaMemcpyAsync(h->dunits, h->hunits.data(), h->hunits.size() * sizeof(TileUnit), cudaMemcpyHostToDevice,
                        h->stream),
        "copy tile table");
+    CU(cudaMemcpyAsync(h->dseg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
+       "copy unit ranges");
+    // the host tables must stay valid until the copies above have run
+    CU(cudaStreamSynchronize(h->stream), "table sync");
+    h->pctas = 0;
+    return JAC_OK;
+}
+
+int build_layout(jac_ctx* h)
+{
+    const int OX = 128 / h->esize;
+    int64_t off = 0, dense = 0;
+    h->hdesc.clear();
+    for (size_t ii = 0; ii < h->inst.size(); ++ii) {
+        Instance& I = h->inst[ii];
+        std::vector<int32_t> sx, ox, sy, oy, sz, oz;
+        split_axis(I.dims[0], h->req_block[0], sx, ox);
+        split_axis(I.dims[1], h->req_block[1], sy, oy);
+        split_axis(I.dims[2], h->req_block[2], sz, oz);
+        I.nb[0] = (int32_t)sx.size();
+        I.nb[1] = (int32_t)sy.size();
+        I.nb[2] = (int32_t)sz.size();
+        I.b0 = (int32_t)h->hdesc.size();
+        I.dense_off = dense;
+        const int64_t nbi = (int64_t)I.nb[0] * I.nb[1] * I.nb[2];
+        if ((int64_t)h->hdesc.size() + nbi > (1 << 24)) return fail(JAC_EINVAL, "too many blocks");
+        for (int32_t bk = 0; bk < I.nb[2]; ++bk)
+            for (int32_t bj = 0; bj < I.nb[1]; ++bj)
+                for (int32_t bi = 0; bi < I.nb[0]; ++bi) {
+                    BlockDesc d;
+                    memset(&d, 0, sizeof d);
+                    d.ext[0] = sx[bi];
+                    d.ext[1] = sy[bj];
+                    d.ext[2] = sz[bk];
+                    d.org[0] = ox[bi];
+                    d.org[1] = oy[bj];
+                    d.org[2] = oz[bk];
+                    const int32_t ids[3] = {bi, bj, bk};
+                    for (int f = 0; f < 6; ++f) {
+                        const int a = f >> 1, dir = (f & 1) ? 1 : -1;
+                        int32_t q[3] = {bi, bj, bk};
+                        q[a] = ids[a] + dir;
+                        if (q[a] < 0 || q[a] >= I.nb[a]) d.nbr[f] = -1;
+                        else d.nbr[f] = I.b0 + (int32_t)(q[0] + (int64_t)I.nb[0] * (q[1] + (int64_t)I.nb[1] * q[2]));
+                        d.bc[f] = I.bc[f];
+                        d.bcf[f] = (float)I.bc[f];
+                    }
+                    d.inst = (int32_t)ii;
+                    d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
+                    d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
+                    const int64_t storage = d.plane * (d.ext[2] + 2);
+                    d.off[0] = off;
+                    d.off[1] = off + storage;
+                    off += 2 * storage;
+                    d.dense = dense;
+                    d.gdim[0] = (int32_t)I.dims[0];
+                    d.gdim[1] = (int32_t)I.dims[1];
+                    d.gdim[2] = (int32_t)I.dims[2];
+                    h->hdesc.push_back(d);
+                }
+        I.b1 = (int32_t)h->hdesc.size();
+        dense += I.dims[0] * I.dims[1] * I.dims[2];
+    }
+    if (h->inst.size() == 1)
+        for (int a = 0; a < 3; ++a) h->nb[a] = h->inst[0].nb[a];
+    const int64_t nblocks = (int64_t)h->hdesc.size();
+    const size_t ninst = h->inst.size();
+    h->hframe.resize(ninst);
+    for (size_t i = 0; i < ninst; ++i) h->hframe[i] = h->inst[i].bc_frame;
+    int rc;
+    if ((rc = dev_alloc(h, (size_t)off * h->esize, &h->pool))) return rc;
+    if ((rc = dev_alloc(h, nblocks * sizeof(BlockDesc), (void**)&h->ddesc))) return rc;
+    if ((rc = dev_alloc(h, nblocks * sizeof(uint32_t), (void**)&h->done))) return rc;
+    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
+    if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
+    if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
+    if ((rc = dev_alloc(h, ninst * sizeof(double), (void**)&h->dres_inst))) return rc;
+    if ((rc = dev_alloc(h, ninst * sizeof(int32_t), (void**)&h->frame))) return rc;
+    if ((rc = dev_alloc(h, (ninst + 1) * sizeof(int32_t), (void**)&h->dseg))) return rc;
+    CU(cudaMemcpyAsync(h->frame, h->hframe.data(), ninst * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
+       "init frame");
+    if ((rc = build_units(h))) return rc;
     CU(cudaMemsetAsync(h->pool, 0, (size_t)off * h->esize, h->stream), "clear pool");
     CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
     CU(launch_init_ghosts(h->args(), h->dtype == JAC_F32, h->stream), "init ghosts");
     h->launches += 1;
-    // the host tables must stay valid until the copies above have run
+    h->pool_elems = off;
     CU(cudaStreamSynchronize(h->stream), "create sync");
     return JAC_OK;
 }
@@ -505,7 +586,9 @@ int read_status(jac_ctx* h)
     return JAC_OK;
 }
 
-int write_dense(jac_ctx* h, const void* src, size_t n, int src_f32, bool src_on_device)
+// Scatter a dense x-fastest array into the blocks of instances [i0, i1)
+// (their dense data back to back), resetting their frames first.
+int write_dense(jac_ctx* h, int i0, int i1, const void* src, size_t n, int src_f32, bool src_on_device)
 {
     const size_t bytes = n * (src_f32 ? 4 : 8);
     const void* dsrc = src;
@@ -515,16 +598,21 @@ int write_dense(jac_ctx* h, const void* src, size_t n, int src_f32, bool src_on_
         CU(cudaMemcpyAsync(h->dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
         dsrc = h->dense;
     }
-    // the scatter raises the frame to the largest exponent of the new interior
-    CU(cudaMemcpyAsync(h->frame, &h->bc_frame, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream), "reset frame");
-    CU(launch_scatter(h->args(), h->dtype == JAC_F32, src_f32, dsrc, h->parity, h->stream), "scatter");
+    // the scatter raises each frame to the largest exponent of the new interior
+    CU(cudaMemcpyAsync(h->frame + i0, h->hframe.data() + i0, (size_t)(i1 - i0) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, h->stream),
+       "reset frame");
+    const int b0 = h->inst[i0].b0, b1 = h->inst[i1 - 1].b1;
+    CU(launch_scatter(h->args(), h->dtype == JAC_F32, src_f32, dsrc, b0, b1 - b0, h->inst[i0].dense_off, h->parity,
+                      h->stream),
+       "scatter");
     h->launches += 1;
-    h->iters = 0;
+    if (i0 == 0 && i1 == (int)h->inst.size()) h->iters = 0;
     if (!src_on_device) CU(cudaStreamSynchronize(h->stream), "write sync");
     return JAC_OK;
 }
 
-int read_dense(jac_ctx* h, void* dst, size_t n, int dst_f32, bool dst_on_device)
+int read_dense(jac_ctx* h, int i0, int i1, void* dst, size_t n, int dst_f32, bool dst_on_device)
 {
     const size_t bytes = n * (dst_f32 ? 4 : 8);
     void* ddst = dst;
@@ -533,12 +621,91 @@ int read_dense(jac_ctx* h, void* dst, size_t n, int dst_f32, bool dst_on_device)
         if (rc) return rc;
         ddst = h->dense;
     }
-    CU(launch_gather(h->args(), h->dtype == JAC_F32, dst_f32, ddst, h->parity, h->stream), "gather");
+    const int b0 = h->inst[i0].b0, b1 = h->inst[i1 - 1].b1;
+    CU(launch_gather(h->args(), h->dtype == JAC_F32, dst_f32, ddst, b0, b1 - b0, h->inst[i0].dense_off, h->parity,
+                     h->stream),
+       "gather");
     h->launches += 1;
     if (!dst_on_device) {
         CU(cudaMemcpyAsync(dst, h->dense, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
         return read_status(h);
     }
+    return JAC_OK;
+}
+
+int64_t range_cells(const jac_ctx* h, int i0, int i1)
+{
+    int64_t n = 0;
+    for (int i = i0; i < i1; ++i) n += h->icells(i);
+    return n;
+}
+
+int create_ctx(jac_ctx** out, int32_t n_inst, const int64_t* dims, int32_t bx, int32_t by, int32_t bz, int32_t dtype,
+               const double* bc, void* stream)
+{
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (n_inst < 1 || !dims || !bc) return fail(JAC_EINVAL, "need n_inst >= 1, dims and boundary values");
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256)
+        return fail(JAC_EINVAL, "block dims must be in [1, 256]");
+    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "dtype must be JAC_F64 or JAC_F32");
+    for (int32_t i = 0; i < n_inst; ++i) {
+        for (int a = 0; a < 3; ++a) {
+            const int64_t n = dims[3 * i + a];
+            if (n < 1 || n > (1 << 30)) return fail(JAC_EINVAL, "instance %d: grid dims must be in [1, 2^30]", i);
+        }
+        if (n_inst == 1 && (bx > dims[0] || by > dims[1] || bz > dims[2]))
+            return fail(JAC_EINVAL, "block dims must not exceed grid dims");
+        for (int f = 0; f < 6; ++f)
+            if (!value_ok(bc[6 * i + f], dtype))
+                return fail(JAC_EINVAL, "instance %d: boundary value %d not finite or out of range", i, f);
+    }
+    jac_ctx* h = new jac_ctx();
+    h->req_block[0] = bx;
+    h->req_block[1] = by;
+    h->req_block[2] = bz;
+    h->dtype = dtype;
+    h->esize = dtype == JAC_F32 ? 4 : 8;
+    h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
+    h->inst.resize(n_inst);
+    for (int32_t i = 0; i < n_inst; ++i) {
+        Instance& I = h->inst[i];
+        memset(&I, 0, sizeof I);
+        for (int a = 0; a < 3; ++a) I.dims[a] = dims[3 * i + a];
+        for (int f = 0; f < 6; ++f) I.bc[f] = bc[6 * i + f];
+        exponent_field_max(I.bc, dtype, I.bc_frame);
+    }
+    for (int a = 0; a < 3; ++a) h->dims[a] = n_inst == 1 ? dims[a] : 0;
+    for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
+    h->alloc = g_alloc;
+    h->free_fn = g_free;
+    h->alloc_user = g_alloc_user;
+    cudaError_t e;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+        e = cudaStreamGetDevice(h->stream, &h->device);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamGetDevice");
+        }
+        cudaSetDevice(h->device);
+    } else {
+        cudaGetDevice(&h->device);
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        h->own_stream = true;
+    }
+    int rc = build_layout(h);
+    if (rc) {
+        std::string msg = g_last_error;
+        jac_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
     return JAC_OK;
 }
 
@@ -576,58 +743,15 @@ int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void* user)
 int jac_create(jac_ctx** out, int64_t nx, int64_t ny, int64_t nz, int32_t bx, int32_t by, int32_t bz, int32_t dtype,
                const double bc[6], void* stream)
 {
-    if (!out) return fail(JAC_EINVAL, "null output pointer");
-    *out = nullptr;
-    if (nx < 1 || ny < 1 || nz < 1) return fail(JAC_EINVAL, "grid dims must be >= 1");
-    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30)) return fail(JAC_EINVAL, "grid dims too large");
-    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256)
-        return fail(JAC_EINVAL, "block dims must be in [1, 256]");
-    if (bx > nx || by > ny || bz > nz) return fail(JAC_EINVAL, "block dims must not exceed grid dims");
-    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "dtype must be JAC_F64 or JAC_F32");
+    const int64_t dims[3] = {nx, ny, nz};
     if (!bc) return fail(JAC_EINVAL, "null boundary values");
-    for (int f = 0; f < 6; ++f)
-        if (!value_ok(bc[f], dtype)) return fail(JAC_EINVAL, "boundary value %d not finite or out of range", f);
-    jac_ctx* h = new jac_ctx();
-    h->dims[0] = nx;
-    h->dims[1] = ny;
-    h->dims[2] = nz;
-    h->req_block[0] = bx;
-    h->req_block[1] = by;
-    h->req_block[2] = bz;
-    h->dtype = dtype;
-    h->esize = dtype == JAC_F32 ? 4 : 8;
-    h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
-    for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
-    h->alloc = g_alloc;
-    h->free_fn = g_free;
-    h->alloc_user = g_alloc_user;
-    cudaError_t e;
-    if (stream) {
-        h->stream = (cudaStream_t)stream;
-        e = cudaStreamGetDevice(h->stream, &h->device);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "cudaStreamGetDevice");
-        }
-        cudaSetDevice(h->device);
-    } else {
-        cudaGetDevice(&h->device);
-        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "cudaStreamCreate");
-        }
-        h->own_stream = true;
-    }
-    int rc = build_layout(h);
-    if (rc) {
-        std::string msg = g_last_error;
-        jac_destroy(h);
-        g_last_error = msg;
-        return rc;
-    }
-    *out = h;
-    return JAC_OK;
+    return create_ctx(out, 1, dims, bx, by, bz, dtype, bc, stream);
+}
+
+int jac_create_batch(jac_ctx** out, int32_t n_inst, const int64_t* dims, int32_t bx, int32_t by, int32_t bz,
+                     int32_t dtype, const double* bc, void* stream)
+{
+    return create_ctx(out, n_inst, dims, bx, by, bz, dtype, bc, stream);
 }
 
 int jac_destroy(jac_ctx* h)
@@ -681,7 +805,7 @@ int jac_write(jac_ctx* h, const double* host, size_t n_cells)
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
     for (size_t i = 0; i < n_cells; ++i)
         if (!value_ok(host[i], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", i);
-    return write_dense(h, host, n_cells, 0, false);
+    return write_dense(h, 0, (int)h->inst.size(), host, n_cells, 0, false);
 }
 
 int jac_write_f32(jac_ctx* h, const float* host, size_t n_cells)
@@ -693,7 +817,7 @@ int jac_write_f32(jac_ctx* h, const float* host, size_t n_cells)
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
     for (size_t i = 0; i < n_cells; ++i)
         if (!std::isfinite(host[i])) return fail(JAC_EINVAL, "value at %zu not finite", i);
-    return write_dense(h, host, n_cells, 1, false);
+    return write_dense(h, 0, (int)h->inst.size(), host, n_cells, 1, false);
 }
 
 int jac_write_device(jac_ctx* h, const void* dev, size_t n_cells, int32_t dtype)
@@ -703,7 +827,7 @@ int jac_write_device(jac_ctx* h, const void* dev, size_t n_cells, int32_t dtype)
     if (!dev) return fail(JAC_EINVAL, "null device pointer");
     if (dtype != h->dtype) return fail(JAC_EINVAL, "dtype must equal the context's dtype");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return write_dense(h, dev, n_cells, dtype == JAC_F32, true);
+    return write_dense(h, 0, (int)h->inst.size(), dev, n_cells, dtype == JAC_F32, true);
 }
 
 int jac_read(jac_ctx* h, double* host, size_t n_cells)
@@ -712,7 +836,7 @@ int jac_read(jac_ctx* h, double* host, size_t n_cells)
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, host, n_cells, 0, false);
+    return read_dense(h, 0, (int)h->inst.size(), host, n_cells, 0, false);
 }
 
 int jac_read_f32(jac_ctx* h, float* host, size_t n_cells)
@@ -722,7 +846,7 @@ int jac_read_f32(jac_ctx* h, float* host, size_t n_cells)
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_read_f32 needs an F32 context");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, host, n_cells, 1, false);
+    return read_dense(h, 0, (int)h->inst.size(), host, n_cells, 1, false);
 }
 
 int jac_read_device(jac_ctx* h, void* dev, size_t n_cells, int32_t dtype)
@@ -733,7 +857,7 @@ int jac_read_device(jac_ctx* h, void* dev, size_t n_cells, int32_t dtype)
     if (dtype != h->dtype && !(h->dtype == JAC_F32 && dtype == JAC_F64))
         return fail(JAC_EINVAL, "dtype must be the context's dtype (or F64 for an F32 context)");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, dev, n_cells, dtype == JAC_F32, true);
+    return read_dense(h, 0, (int)h->inst.size(), dev, n_cells, dtype == JAC_F32, true);
 }
 
 int jac_iterate(jac_ctx* h, int64_t n)
@@ -786,7 +910,7 @@ int jac_iterate(jac_ctx* h, int64_t n)
         case JAC_MODE_PERSISTENT: {
             if (h->pctas == 0) {
                 int per_sm = 0, sms = 0;
-                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
+                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith, h->tile_w),
                                                                  persistent_block_threads(), 0),
                    "occupancy");
                 CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
@@ -869,6 +993,154 @@ int jac_info(jac_ctx* h, jac_info_t* info)
     info->iterations = h->iters;
     info->device_bytes = h->device_bytes;
     info->kernel_launches = h->launches;
+    info->n_instances = (int32_t)h->inst.size();
+    info->tile_w = h->tile_w;
+    info->zdepth = h->zdepth;
+    info->n_units = (int32_t)h->hunits.size();
+    info->n_blocks = (int32_t)h->hdesc.size();
+    return JAC_OK;
+}
+
+int jac_write_instance(jac_ctx* h, int32_t i, const double* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
+    for (size_t q = 0; q < n_cells; ++q)
+        if (!value_ok(host[q], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", q);
+    return write_dense(h, i, i + 1, host, n_cells, 0, false);
+}
+
+int jac_write_instance_device(jac_ctx* h, int32_t i, const void* dev, size_t n_cells, int32_t dtype)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (!dev) return fail(JAC_EINVAL, "null device pointer");
+    if (dtype != h->dtype) return fail(JAC_EINVAL, "dtype must equal the context's dtype");
+    if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
+    return write_dense(h, i, i + 1, dev, n_cells, dtype == JAC_F32, true);
+}
+
+int jac_read_instance(jac_ctx* h, int32_t i, double* host, size_t n_cells)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (!host) return fail(JAC_EINVAL, "null host pointer");
+    if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
+    return read_dense(h, i, i + 1, host, n_cells, 0, false);
+}
+
+int jac_read_instance_device(jac_ctx* h, int32_t i, void* dev, size_t n_cells, int32_t dtype)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (!dev) return fail(JAC_EINVAL, "null device pointer");
+    if (dtype != h->dtype && !(h->dtype == JAC_F32 && dtype == JAC_F64))
+        return fail(JAC_EINVAL, "dtype must be the context's dtype (or F64 for an F32 context)");
+    if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
+    return read_dense(h, i, i + 1, dev, n_cells, dtype == JAC_F32, true);
+}
+
+int jac_residual_instances_device(jac_ctx* h, double* dev_out)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
+    CU(launch_residual_segments(h->args(), h->dtype == JAC_F32, h->parity, h->partials, h->dseg, (int)h->inst.size(),
+                                dev_out, h->stream),
+       "residual");
+    h->launches += 2;
+    return JAC_OK;
+}
+
+int jac_residual_instances(jac_ctx* h, double* out)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    if ((rc = jac_residual_instances_device(h, h->dres_inst))) return rc;
+    CU(cudaMemcpyAsync(out, h->dres_inst, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+       "copy residuals");
+    return read_status(h);
+}
+
+int jac_set_tile(jac_ctx* h, int32_t tile_w, int32_t zdepth)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!tile_width_supported(tile_w)) return fail(JAC_EINVAL, "tile width must be 16, 32 or 64");
+    if (zdepth < 0 || zdepth > 256) return fail(JAC_EINVAL, "z depth must be in [0, 256]");
+    if (tile_w == h->tile_w && zdepth == h->zdepth) return JAC_OK;
+    CU(cudaStreamSynchronize(h->stream), "tile sync");
+    h->tile_w = tile_w;
+    h->zdepth = zdepth;
+    destroy_graphs(h);
+    return build_units(h);
+}
+
+// Time every (tile width, z depth) pair for the current mode on the context
+// itself, keep the fastest, and put the grid back as it was.
+int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (trial_iters < 1) return fail(JAC_EINVAL, "trial_iters must be >= 1");
+    const size_t bytes = (size_t)h->pool_elems * h->esize;
+    void* snap = nullptr;
+    CU(cudaMallocAsync(&snap, bytes, h->stream), "autotune snapshot");
+    CU(cudaMemcpyAsync(snap, h->pool, bytes, cudaMemcpyDeviceToDevice, h->stream), "snapshot");
+    const int parity0 = h->parity;
+    const int64_t iters0 = h->iters;
+    int32_t max_bz = 1;
+    for (const BlockDesc& d : h->hdesc) max_bz = std::max(max_bz, d.ext[2]);
+    const int widths[3] = {16, 32, 64};
+    const int depths[4] = {0, 64, 32, 16};
+    jac_tune_t best;
+    memset(&best, 0, sizeof best);
+    best.ms_per_iter = 1e300;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0), "event");
+    CU(cudaEventCreate(&e1), "event");
+    for (int wi = 0; wi < 3 && !rc; ++wi)
+        for (int di = 0; di < 4 && !rc; ++di) {
+            const int zd = depths[di];
+            if (zd != 0 && zd >= max_bz) continue;
+            if ((rc = jac_set_tile(h, widths[wi], zd))) break;
+            if ((rc = jac_iterate(h, 1))) break;  // builds graphs / streams outside the timing
+            cudaEventRecord(e0, h->stream);
+            if ((rc = jac_iterate(h, trial_iters))) break;
+            cudaEventRecord(e1, h->stream);
+            if ((rc = read_status(h))) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = (double)ms / trial_iters;
+            if (best.n_trials < 16) {
+                best.trial_tile_w[best.n_trials] = widths[wi];
+                best.trial_zdepth[best.n_trials] = zd;
+                best.trial_ms_per_iter[best.n_trials] = per;
+            }
+            best.n_trials += 1;
+            if (per < best.ms_per_iter) {
+                best.ms_per_iter = per;
+                best.tile_w = widths[wi];
+                best.zdepth = zd;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc && best.tile_w) rc = jac_set_tile(h, best.tile_w, best.zdepth);
+    cudaMemcpyAsync(h->pool, snap, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaFreeAsync(snap, h->stream);
+    h->parity = parity0;
+    h->iters = iters0;
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(h->stream), "autotune sync");
+    if (result) *result = best;
     return JAC_OK;
 }
 

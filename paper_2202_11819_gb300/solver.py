@@ -135,3 +135,77 @@ class Jacobi3D:
 
     def sync(self):
         _lib.jac_sync(self.h)
+
+
+class Jacobi3DBatch:
+    """Several independent grids in one context: one pool, one block table,
+    advanced together by every launch. ``dims`` is a list of (nx, ny, nz),
+    ``bcs`` a list of 6-tuples."""
+
+    def __init__(self, dims, block, dtype: str = "f64", bcs=None, stream=None, mode: str = "persistent",
+                 arith: str | None = None):
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        self.dtype = dtype
+        self._dt = _lib.JAC_F32 if dtype == "f32" else _lib.JAC_F64
+        if bcs is None:
+            bcs = [(1.0, 0.0, 0.0, 0.0, 0.0, 0.0)] * len(self.dims)
+        if stream is None:
+            try:
+                import torch
+
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+            except Exception:  # noqa: BLE001
+                stream = None
+        bx, by, bz = (int(v) for v in block)
+        self.h = _lib.jac_create_batch(self.dims, bx, by, bz, self._dt, bcs, stream)
+        _lib.jac_set_mode(self.h, mode)
+        if arith is not None:
+            _lib.jac_set_arith(self.h, arith)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            _lib.jac_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def shape(self, i):
+        nx, ny, nz = self.dims[i]
+        return (nz, ny, nx)
+
+    def write(self, i, u):
+        _lib.jac_write_instance(self.h, i, u)
+
+    def read(self, i):
+        return _lib.jac_read_instance(self.h, i, np.empty(self.shape(i), dtype=np.float64))
+
+    def iterate(self, n):
+        _lib.jac_iterate(self.h, n)
+
+    def residuals(self):
+        return _lib.jac_residual_instances(self.h, len(self.dims))
+
+    def set_mode(self, mode):
+        _lib.jac_set_mode(self.h, mode)
+
+    def set_tile(self, tile_w, zdepth):
+        _lib.jac_set_tile(self.h, tile_w, zdepth)
+
+    def autotune(self, trial_iters=4):
+        return _lib.jac_autotune(self.h, trial_iters)
+
+    def info(self):
+        return _lib.jac_info(self.h)
+
+    def sync(self):
+        _lib.jac_sync(self.h)

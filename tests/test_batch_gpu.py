@@ -1,0 +1,139 @@
+"""Batched contexts (several grids in one pool and one launch), tile shapes,
+z depths and the autotuner, against the CPU oracle run on each grid alone.
+
+Tolerances as in test_parity_gpu: binary64 bit-exact against the matching
+oracle rule, binary32 bit-exact, residuals 1e-12 relative.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2202_11819_gb300 import Jacobi3DBatch, _lib
+
+pytestmark = pytest.mark.gpu
+
+RULE = {"seq": oracle.RULE_SEQ, "exact": oracle.RULE_EXACT}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _lib.load()
+
+
+def instance_set(n, seed, lo=5, hi=41):
+    rng = np.random.default_rng(seed)
+    dims = [tuple(int(v) for v in rng.integers(lo, hi, size=3)) for _ in range(n)]
+    bcs = [tuple(float(v) for v in rng.random(6)) for _ in range(n)]
+    grids = [synth.grid_uniform01(100 + i, *d).copy() for i, d in enumerate(dims)]
+    return dims, bcs, grids
+
+
+@pytest.mark.parametrize("arith", ["exact", "seq"])
+@pytest.mark.parametrize("mode", ["persistent", "fused", "unfused", "graph_fused"])
+def test_batch_matches_each_grid_alone(mode, arith):
+    dims, bcs, grids = instance_set(6, 1)
+    iters = 7
+    with Jacobi3DBatch(dims, (16, 12, 10), bcs=bcs, mode=mode, arith=arith) as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(iters)
+        outs = [B.read(i) for i in range(len(dims))]
+        rhos = B.residuals()
+    for i, g in enumerate(grids):
+        want = oracle.jacobi(g, bcs[i], iters, RULE[arith])
+        assert np.array_equal(outs[i], want), f"grid {i}"
+        r = oracle.residual(want, bcs[i])
+        assert abs(rhos[i] - r) <= 1e-12 * r
+
+
+@pytest.mark.parametrize("tile_w", [16, 32, 64])
+@pytest.mark.parametrize("zdepth", [0, 16, 7])
+@pytest.mark.parametrize("mode", ["persistent", "fused"])
+def test_tile_shapes_and_z_depths_do_not_change_results(tile_w, zdepth, mode):
+    dims, bcs, grids = instance_set(3, 2, lo=9, hi=80)
+    iters = 5
+    with Jacobi3DBatch(dims, (64, 40, 33), bcs=bcs, mode=mode) as B:
+        B.set_tile(tile_w, zdepth)
+        info = B.info()
+        assert info["tile_w"] == tile_w and info["zdepth"] == zdepth
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(iters)
+        outs = [B.read(i) for i in range(len(dims))]
+        rhos = B.residuals()
+    for i, g in enumerate(grids):
+        want = oracle.jacobi(g, bcs[i], iters, oracle.RULE_EXACT)
+        assert np.array_equal(outs[i], want), f"grid {i}"
+        assert abs(rhos[i] - oracle.residual(want, bcs[i])) <= 1e-12 * rhos[i]
+
+
+def test_f32_batch():
+    dims, bcs, grids = instance_set(4, 3)
+    iters = 6
+    with Jacobi3DBatch(dims, (16, 16, 16), dtype="f32", bcs=bcs, mode="persistent") as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(iters)
+        outs = [B.read(i) for i in range(len(dims))]
+    for i, g in enumerate(grids):
+        want = oracle.jacobi_f32(g.astype(np.float32), bcs[i], iters).astype(np.float64)
+        assert np.array_equal(outs[i], want), f"grid {i}"
+
+
+def test_autotune_restores_state_and_keeps_results():
+    dims, bcs, grids = instance_set(5, 4, lo=20, hi=70)
+    with Jacobi3DBatch(dims, (32, 32, 32), bcs=bcs, mode="persistent") as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(3)
+        before = [B.read(i) for i in range(len(dims))]
+        it_before = B.info()["iterations"]
+        res = B.autotune(2)
+        assert res["tile_w"] in (16, 32, 64)
+        assert len(res["trials"]) >= 3
+        assert B.info()["iterations"] == it_before
+        after = [B.read(i) for i in range(len(dims))]
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        B.iterate(4)
+        outs = [B.read(i) for i in range(len(dims))]
+    for i, g in enumerate(grids):
+        assert np.array_equal(outs[i], oracle.jacobi(g, bcs[i], 7, oracle.RULE_EXACT))
+
+
+def test_rewriting_one_grid_leaves_the_others():
+    dims, bcs, grids = instance_set(4, 5)
+    with Jacobi3DBatch(dims, (16, 16, 16), bcs=bcs) as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(4)
+        fresh = synth.grid_uniform01(999, *dims[2]).copy()
+        B.write(2, fresh)
+        B.iterate(3)
+        outs = [B.read(i) for i in range(len(dims))]
+    for i, g in enumerate(grids):
+        if i == 2:
+            want = oracle.jacobi(fresh, bcs[i], 3, oracle.RULE_EXACT)
+        else:
+            want = oracle.jacobi(g, bcs[i], 7, oracle.RULE_EXACT)
+        assert np.array_equal(outs[i], want), f"grid {i}"
+
+
+def test_batch_of_configured_shapes_small():
+    """Shapes drawn as the batched workload draws them (each axis from
+    32, 48, ..., 192), a few grids, blocks of at most 64^3, parity on a
+    few sampled grids."""
+    dims = synth.batch_instance_dims(6, seed=0)
+    grids = [synth.grid_uniform01(i, *d) for i, d in enumerate(dims)]
+    bc = synth.DIRICHLET_X0
+    with Jacobi3DBatch(dims, (64, 64, 64), bcs=[bc] * len(dims), mode="persistent") as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(3)
+        for i in (0, 3):
+            assert np.array_equal(B.read(i), oracle.jacobi(grids[i], bc, 3, oracle.RULE_EXACT))
