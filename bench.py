@@ -53,10 +53,15 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default tile shape (32 wide, whole blocks)")
-    p.add_argument("--workload", default="grid", choices=["grid", "batch"],
+    p.add_argument("--workload", default="grid", choices=["grid", "batch", "f32", "serve"],
                    help="grid: one overdecomposed grid (default); batch: many independent grids in one launch")
     p.add_argument("--instances", type=int, default=256, help="batch workload: number of grids")
     p.add_argument("--batch-iters", type=int, default=500, help="batch workload: iterations per step")
+    p.add_argument("--f32-iters", type=int, default=2000, help="f32 workload: iterations per step")
+    p.add_argument("--residual-every", type=int, default=50, help="f32 workload: binary64 residual period")
+    p.add_argument("--requests", type=int, default=120, help="serve workload: requests in the trace")
+    p.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
+    p.add_argument("--budget-gb", type=float, default=120.0, help="serve workload: HBM budget")
     return p.parse_args()
 
 
@@ -489,6 +494,234 @@ def run_batch(a, rank, world, local, pg):
     print(json.dumps(line), flush=True)
 
 
+def run_f32(a, rank, world, local, pg):
+    """Precision workload: a binary32 grid (default 1024^3 in 64^3 blocks)
+    iterated a.f32_iters times per step with the binary64 residual every
+    a.residual_every iterations; afterwards the same grid is run in binary64
+    (correctly rounded mean) and the max-abs and relative-L2 differences are
+    reported next to the proven bound k (27/7 + 1) 2^-24 + 2^-25."""
+    import torch
+
+    import synth
+    from paper_2202_11819_gb300 import Jacobi3D, _lib, use_torch_allocator
+
+    torch.cuda.set_device(local)
+    use_torch_allocator(True)
+    stream = torch.cuda.Stream()
+    g, b = a.grid, a.block
+    ncell = g[0] * g[1] * g[2]
+    dev64 = torch.from_numpy(synth.grid_uniform01(0, *g).reshape(-1)).to(f"cuda:{local}")
+    dev32 = dev64.to(torch.float32)
+    n_res = a.f32_iters // a.residual_every
+    with torch.cuda.stream(stream):
+        J = Jacobi3D(g, b, dtype="f32", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode)
+        tune = _lib.jac_autotune(J.h, 4) if not a.no_autotune else None
+        rho = torch.zeros(max(1, n_res), dtype=torch.float64, device=f"cuda:{local}")
+
+        def step():
+            for r in range(n_res):
+                J.iterate(a.residual_every)
+                _lib.jac_residual_device(J.h, rho[r:r + 1].data_ptr())
+            rest = a.f32_iters - n_res * a.residual_every
+            if rest:
+                J.iterate(rest)
+
+        J.write_device(dev32)
+        for _ in range(a.warmup):
+            step()
+        stream.synchronize()
+        launches0 = J.info()["kernel_launches"]
+        barrier(pg)
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for _ in range(a.steps):
+                J.write_device(dev32)  # every step starts from the same state: the error check below applies to it
+                step()
+            stream.synchronize()
+            wall = time.perf_counter() - t0
+        J.sync()
+        launches = J.info()["kernel_launches"] - launches0
+        rhos = rho.cpu().tolist()
+        out32 = torch.empty(ncell, dtype=torch.float64, device=f"cuda:{local}")
+        J.read_device(out32)
+        J.close()
+        # binary64 run of the same grid for the error report
+        K = Jacobi3D(g, b, dtype="f64", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode, arith="exact")
+        K.write_device(dev64)
+        t1 = time.perf_counter()
+        K.iterate(a.f32_iters)
+        stream.synchronize()
+        t64 = time.perf_counter() - t1
+        out64 = torch.empty(ncell, dtype=torch.float64, device=f"cuda:{local}")
+        K.read_device(out64)
+        K.close()
+        stream.synchronize()
+        diff = out32 - out64
+        max_abs = float(diff.abs().max())
+        rel_l2 = float(diff.norm() / out64.norm())
+    wall = max_over_ranks(pg, wall)
+    if rank != 0:
+        return
+    value = world * ncell * a.f32_iters * a.steps / wall
+    bound = a.f32_iters * (27.0 / 7.0 + 1.0) * 2.0 ** -24 + 2.0 ** -25
+    peak, kind = measured_peaks()
+    achieved = BYTES_PER_UPDATE["f32"] * ncell * a.f32_iters * a.steps / wall / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"Jacobi3D {g[0]}x{g[1]}x{g[2]} FP32 storage and arithmetic, blocks of "
+                               f"{b[0]}x{b[1]}x{b[2]}, {a.f32_iters} iterations per step with the FP64 residual "
+                               f"every {a.residual_every}, {a.mode} form",
+                   "autotune": tune},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "bytes_per_update": 8},
+        "error_vs_f64": {"max_abs": max_abs, "rel_l2": rel_l2, "proven_max_abs_bound": bound,
+                         "within_bound": max_abs <= bound},
+        "f64_same_grid_cell_updates_per_s": ncell * a.f32_iters / t64,
+        "speedup_vs_f64": value / (ncell * a.f32_iters / t64),
+        "residual_f64_every": {"period": a.residual_every, "first": rhos[0], "last": rhos[-1],
+                               "monotone": all(rhos[i + 1] <= rhos[i] * (1 + 1e-6) for i in range(len(rhos) - 1))},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def replay(srv_lib, trace, inits, rate_scale, budget, chunk, tol=1e-6, cap=3000):
+    """Submit the trace's requests at their arrival times (times divided by
+    rate_scale) to a fresh server and step it until every request is done.
+    Returns per-request latencies (arrival to completion) and the totals."""
+    _lib = srv_lib
+    s = _lib.jac_server_create(budget, 1024, 64, 64, 64, chunk)
+    try:
+        t_start = _lib.jac_server_now(s)
+        order = sorted(range(len(trace)), key=lambda i: trace[i].arrival_s)
+        arrive = {i: t_start + trace[i].arrival_s / rate_scale for i in order}
+        nxt = 0
+        ids = {}
+        lat = {}
+        iters = {}
+        stats = None
+        while len(lat) < len(trace):
+            now = _lib.jac_server_now(s)
+            while nxt < len(order) and arrive[order[nxt]] <= now:
+                i = order[nxt]
+                r = trace[i]
+                dt = _lib.JAC_F32 if r.dtype == "f32" else _lib.JAC_F64
+                ids[_lib.jac_server_submit(s, r.dims, dt, DIRICHLET, inits[i], tol, cap)] = i
+                nxt += 1
+            if stats is not None and stats["running"] == 0 and stats["queued"] == 0 and nxt < len(order):
+                time.sleep(max(0.0, arrive[order[nxt]] - _lib.jac_server_now(s)))
+                stats = {"running": 0, "queued": 1}
+                continue
+            stats = _lib.jac_server_step(s)
+            while True:
+                r = _lib.jac_server_poll(s)
+                if r is None:
+                    break
+                i = ids[r["id"]]
+                lat[i] = r["t_done"] - arrive[i]
+                iters[i] = r["iterations"]
+                _lib.jac_server_result(s, r["id"], None)
+        t_end = _lib.jac_server_now(s)
+        updates = sum(trace[i].dims[0] * trace[i].dims[1] * trace[i].dims[2] * iters[i] for i in lat)
+        makespan = t_end - t_start
+        return lat, iters, updates, makespan, stats
+    finally:
+        _lib.jac_server_destroy(s)
+
+
+DIRICHLET = (1.0, 0.0, 0.0, 0.0, 0.0, 0.0)
+
+
+def pctl(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def run_serve(a, rank, world, local, pg):
+    """Serving workload: a seeded Poisson trace of solve requests (mean
+    a.rate per second), each axis log-uniform in [32, 384], binary32 or
+    binary64 with probability 1/2, each iterated until its binary64 residual
+    is below 1e-6 or 3000 iterations, admitted against a.budget_gb of HBM;
+    continuous batching in shared persistent launches (chunks of 50)."""
+    import torch
+
+    import synth
+    from paper_2202_11819_gb300 import Jacobi3D, _lib
+
+    torch.cuda.set_device(local)
+    trace = synth.serving_trace(a.requests, rate_per_s=a.rate, seed=0)
+    inits = [synth.grid_uniform01(r.seed, *r.dims) for r in trace]
+    budget = int(a.budget_gb * (1 << 30))
+    chunk = 50
+    # specified rate
+    lat, iters, updates, makespan, _ = replay(_lib, trace, inits, 1.0, budget, chunk)
+    thr = updates / makespan
+    mean_updates = updates / len(trace)
+    # a sustainable rate: 0.7 x the measured capacity (requests per second)
+    cap_rps = thr / mean_updates
+    scale = 0.7 * cap_rps / a.rate
+    lat2, iters2, updates2, makespan2, _ = replay(_lib, trace, inits, scale, budget, chunk)
+    # the plain form: binary64, per-block launches on per-block streams, one
+    # request at a time (first come, first served). Its per-iteration time is
+    # measured for every request shape (5 iterations after 1 untimed), its
+    # service time is that times the iterations the request needs, and the
+    # FIFO queue is replayed with the trace's arrivals.
+    svc = []
+    per_shape = {}
+    for i, r in enumerate(trace):
+        if r.dims not in per_shape:
+            with Jacobi3D(r.dims, (64, 64, 64), dtype="f64", bc=DIRICHLET, mode="unfused", arith="seq") as J:
+                J.write(inits[i])
+                J.iterate(1)
+                J.sync()
+                t0 = time.perf_counter()
+                J.iterate(5)
+                J.sync()
+                per_shape[r.dims] = (time.perf_counter() - t0) / 5
+        svc.append(per_shape[r.dims] * iters[i])
+
+    def fifo(scale_):
+        t_free = 0.0
+        out = []
+        for i in sorted(range(len(trace)), key=lambda j: trace[j].arrival_s):
+            arr = trace[i].arrival_s / scale_
+            start = max(arr, t_free)
+            t_free = start + svc[i]
+            out.append(t_free - arr)
+        return out
+
+    plain = fifo(1.0)
+    plain2 = fifo(scale)
+    if rank != 0:
+        return
+    lv, lv2 = list(lat.values()), list(lat2.values())
+    line = {
+        "metric": "serve p50/p99 latency and cell-updates/s", "value": thr, "unit": UNIT, "n_gpus": world,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{len(trace)} requests, Poisson mean {a.rate}/s, axes log-uniform [32, 384], "
+                               f"f32/f64 50/50, until residual < 1e-6 or 3000 iterations, {a.budget_gb} GB budget, "
+                               f"chunks of {chunk} iterations in shared persistent launches"},
+        "specified_rate": {"rate_per_s": a.rate, "p50_s": pctl(lv, 50), "p99_s": pctl(lv, 99),
+                           "cell_updates_per_s": thr, "makespan_s": makespan,
+                           "converged": sum(1 for i in iters if iters[i] < 3000)},
+        "sustainable_rate": {"rate_per_s": a.rate * scale, "p50_s": pctl(lv2, 50), "p99_s": pctl(lv2, 99),
+                             "cell_updates_per_s": updates2 / makespan2, "makespan_s": makespan2},
+        "plain_form_fifo": {"note": "binary64 per-block launches, one request at a time; measured per-iteration "
+                                    "time per shape x iterations, FIFO replay of the same arrivals",
+                            "specified_rate": {"p50_s": pctl(plain, 50), "p99_s": pctl(plain, 99)},
+                            "sustainable_rate": {"p50_s": pctl(plain2, 50), "p99_s": pctl(plain2, 99)},
+                            "cell_updates_per_s": updates / sum(svc)},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank, world, local, pg = dist_setup(a.gpus)
@@ -497,6 +730,12 @@ def main():
             run_reference(a, rank, world, pg)
         elif a.workload == "batch":
             run_batch(a, rank, world, local, pg)
+        elif a.workload == "serve":
+            run_serve(a, rank, world, local, pg)
+        elif a.workload == "f32":
+            if a.grid == [512, 512, 512]:
+                a.grid = [1024, 1024, 1024]
+            run_f32(a, rank, world, local, pg)
         else:
             run_ours(a, rank, world, local, pg)
     finally:

@@ -293,6 +293,94 @@ int jac_residual_dense_noalloc(const void *u, int32_t dtype, int64_t nx, int64_t
                                const double bc[6], double *out, void *stream);
 
 /* ------------------------------------------------------------------ */
+/* Pools: grids that join and leave                                    */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of block storage a grid of `dims` needs with these block dims and
+ * dtype (both buffers, ghost layers and row padding). */
+int jac_storage_bytes(const int64_t dims[3], int32_t bx, int32_t by, int32_t bz, int32_t dtype, int64_t *bytes);
+
+/* An empty context with `capacity_bytes` of block storage and up to
+ * `max_grids` grid slots. Grids are added and removed between launches
+ * (jac_pool_add / jac_pool_remove); a resident grid's storage never moves,
+ * and every launch (fused or persistent forms only) advances all resident
+ * grids. Slots index the per-grid calls (jac_write_instance, ...,
+ * jac_residual_instances, whose output has one entry per slot, NaN for a
+ * free slot). */
+int jac_create_pool(jac_ctx **out, int32_t dtype, int64_t capacity_bytes, int32_t max_grids, int32_t bx,
+                    int32_t by, int32_t bz, void *stream);
+
+/* Make a grid resident: JAC_EBUDGET if no slot or no free region of the
+ * pool fits it. Its interior starts at 0 until written. */
+int jac_pool_add(jac_ctx *h, const int64_t dims[3], const double bc[6], int32_t *slot);
+
+/* Release a grid's slot and storage (after the context's stream drains). */
+int jac_pool_remove(jac_ctx *h, int32_t slot);
+
+/* Bytes of the pool in use and its capacity, and the resident grids. */
+int jac_pool_usage(jac_ctx *h, int64_t *used_bytes, int64_t *capacity_bytes, int32_t *grids);
+
+/* ------------------------------------------------------------------ */
+/* Server: continuous batching of solve requests                       */
+/* ------------------------------------------------------------------ */
+
+/* Solve requests (a grid, its boundary values and initial interior, a
+ * residual tolerance and an iteration cap) are queued first come first
+ * served and admitted while a slot (max_active) and room in an HBM budget
+ * of budget_bytes are free. Every admitted grid stays resident until it
+ * finishes. Each jac_server_step admits what fits, then advances every
+ * resident grid by chunk_iters iterations in shared launches (one persistent
+ * launch for the binary64 grids and one for the binary32 grids, on two
+ * streams so they overlap) and reads every grid's binary64 residual: a grid
+ * finishes after the first chunk whose residual is below its tolerance, or
+ * when it reaches its cap. A grid's result therefore does not depend on
+ * which other grids shared its launches. There is no counterpart of this
+ * loop in the paper, which runs fixed iteration counts (Section IV-A). */
+typedef struct jac_server jac_server;
+
+typedef struct {
+    int32_t running;       /* resident grids                              */
+    int32_t queued;        /* requests waiting for admission              */
+    int32_t finished_now;  /* grids retired by this step                  */
+    int64_t cell_updates;  /* cell updates done since creation            */
+    int64_t used_bytes;    /* bytes of the budget in use                  */
+    int64_t budget_bytes;  /* the budget                                  */
+} jac_server_stats_t;
+
+typedef struct {
+    int64_t id;
+    int64_t iterations;    /* iterations run (a multiple of chunk_iters)  */
+    double residual;       /* binary64 residual of the final state        */
+    double t_submit;       /* seconds since the server was created        */
+    double t_admit;
+    double t_done;
+    int32_t status;        /* JAC_OK, or the code that failed the request */
+} jac_request_t;
+
+int jac_server_create(jac_server **out, int64_t budget_bytes, int32_t max_active, int32_t bx, int32_t by,
+                      int32_t bz, int32_t chunk_iters);
+int jac_server_destroy(jac_server *s);
+
+/* Queue a request; `init` (nx*ny*nz binary64 values, x fastest) is copied.
+ * dtype JAC_F32 grids are stored and iterated in binary32 (values rounded
+ * to nearest); their residual is still binary64. */
+int jac_server_submit(jac_server *s, const int64_t dims[3], int32_t dtype, const double bc[6],
+                      const double *init, double tol, int64_t max_iters, int64_t *req_id);
+
+/* One admission + chunk + retirement round (synchronises). */
+int jac_server_step(jac_server *s, jac_server_stats_t *stats);
+
+/* Take one finished request's summary; JAC_ESTATE when none is waiting. */
+int jac_server_poll(jac_server *s, jac_request_t *done);
+
+/* Copy a finished request's final interior (binary64, x fastest; NULL to
+ * discard it) and forget the request. */
+int jac_server_result(jac_server *s, int64_t req_id, double *host_out, size_t n_cells);
+
+/* Seconds since the server was created (the clock of jac_request_t). */
+int jac_server_now(jac_server *s, double *seconds);
+
+/* ------------------------------------------------------------------ */
 /* Diagnostics                                                         */
 /* ------------------------------------------------------------------ */
 

@@ -81,6 +81,29 @@ class jac_tune_t(ctypes.Structure):
     ]
 
 
+class jac_server_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("running", ctypes.c_int32),
+        ("queued", ctypes.c_int32),
+        ("finished_now", ctypes.c_int32),
+        ("cell_updates", ctypes.c_int64),
+        ("used_bytes", ctypes.c_int64),
+        ("budget_bytes", ctypes.c_int64),
+    ]
+
+
+class jac_request_t(ctypes.Structure):
+    _fields_ = [
+        ("id", ctypes.c_int64),
+        ("iterations", ctypes.c_int64),
+        ("residual", ctypes.c_double),
+        ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double),
+        ("t_done", ctypes.c_double),
+        ("status", ctypes.c_int32),
+    ]
+
+
 JAC_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 JAC_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -123,6 +146,24 @@ _SIGS = {
     "jac_residual_instances_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "jac_set_tile": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "jac_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(jac_tune_t)], ctypes.c_int),
+    "jac_storage_bytes": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "jac_create_pool": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                         ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p], ctypes.c_int),
+    "jac_pool_add": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32)],
+                     ctypes.c_int),
+    "jac_pool_remove": ([ctypes.c_void_p, ctypes.c_int32], ctypes.c_int),
+    "jac_pool_usage": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                        ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "jac_server_create": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "jac_server_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "jac_server_submit": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_double, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "jac_server_step": ([ctypes.c_void_p, ctypes.POINTER(jac_server_stats_t)], ctypes.c_int),
+    "jac_server_poll": ([ctypes.c_void_p, ctypes.POINTER(jac_request_t)], ctypes.c_int),
+    "jac_server_result": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "jac_server_now": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "jac_residual_dense_noalloc": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
                                    ctypes.c_int),
@@ -332,6 +373,92 @@ def jac_autotune(h, trial_iters: int) -> dict:
     n = min(r.n_trials, 16)
     return {"tile_w": r.tile_w, "zdepth": r.zdepth, "ms_per_iter": r.ms_per_iter,
             "trials": [(r.trial_tile_w[i], r.trial_zdepth[i], r.trial_ms_per_iter[i]) for i in range(n)]}
+
+
+def _i64x3(dims):
+    return (ctypes.c_int64 * 3)(*[int(v) for v in dims])
+
+
+def _f64x6(bc):
+    return (ctypes.c_double * 6)(*[float(v) for v in bc])
+
+
+def jac_storage_bytes(dims, bx, by, bz, dtype=JAC_F64) -> int:
+    out = ctypes.c_int64()
+    _check(load().jac_storage_bytes(_i64x3(dims), int(bx), int(by), int(bz), int(dtype), ctypes.byref(out)),
+           "jac_storage_bytes")
+    return out.value
+
+
+def jac_create_pool(dtype, capacity_bytes, max_grids, bx, by, bz, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().jac_create_pool(ctypes.byref(h), int(dtype), int(capacity_bytes), int(max_grids), int(bx),
+                                  int(by), int(bz), ctypes.c_void_p(stream or 0)), "jac_create_pool")
+    return h
+
+
+def jac_pool_add(h, dims, bc) -> int:
+    slot = ctypes.c_int32()
+    _check(load().jac_pool_add(h, _i64x3(dims), _f64x6(bc), ctypes.byref(slot)), "jac_pool_add")
+    return slot.value
+
+
+def jac_pool_remove(h, slot: int) -> None:
+    _check(load().jac_pool_remove(h, int(slot)), "jac_pool_remove")
+
+
+def jac_pool_usage(h) -> tuple:
+    u, c, g = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(load().jac_pool_usage(h, ctypes.byref(u), ctypes.byref(c), ctypes.byref(g)), "jac_pool_usage")
+    return u.value, c.value, g.value
+
+
+def jac_server_create(budget_bytes, max_active, bx, by, bz, chunk_iters) -> ctypes.c_void_p:
+    s = ctypes.c_void_p()
+    _check(load().jac_server_create(ctypes.byref(s), int(budget_bytes), int(max_active), int(bx), int(by), int(bz),
+                                    int(chunk_iters)), "jac_server_create")
+    return s
+
+
+def jac_server_destroy(s) -> None:
+    _check(load().jac_server_destroy(s), "jac_server_destroy")
+
+
+def jac_server_submit(s, dims, dtype, bc, init: np.ndarray, tol: float, max_iters: int) -> int:
+    a = _host(init, np.float64)
+    rid = ctypes.c_int64()
+    _check(load().jac_server_submit(s, _i64x3(dims), int(dtype), _f64x6(bc), a.ctypes.data, float(tol),
+                                    int(max_iters), ctypes.byref(rid)), "jac_server_submit")
+    return rid.value
+
+
+def jac_server_step(s) -> dict:
+    st = jac_server_stats_t()
+    _check(load().jac_server_step(s, ctypes.byref(st)), "jac_server_step")
+    return {k: getattr(st, k) for k, _ in jac_server_stats_t._fields_}
+
+
+def jac_server_poll(s):
+    r = jac_request_t()
+    rc = load().jac_server_poll(s, ctypes.byref(r))
+    if rc == JAC_ESTATE:
+        return None
+    _check(rc, "jac_server_poll")
+    return {k: getattr(r, k) for k, _ in jac_request_t._fields_}
+
+
+def jac_server_result(s, req_id: int, out: np.ndarray | None) -> np.ndarray | None:
+    if out is None:
+        _check(load().jac_server_result(s, int(req_id), None, 0), "jac_server_result")
+        return None
+    _check(load().jac_server_result(s, int(req_id), out.ctypes.data, out.size), "jac_server_result")
+    return out
+
+
+def jac_server_now(s) -> float:
+    t = ctypes.c_double()
+    _check(load().jac_server_now(s, ctypes.byref(t)), "jac_server_now")
+    return t.value
 
 
 def jac_set_wait_limit_ns(h, ns: int) -> None:

@@ -560,9 +560,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
     if (tid == 0) partials[blockIdx.x] = red[0];
 }
 
-// Per-instance residuals: instance i owns partials [seg[i], seg[i+1]); one
-// CTA per instance sums them in a fixed order.
-__global__ void k_sum_segments(const double* partials, const int32_t* seg, double* out)
+// Per-grid residuals: resident grid i (slot slot[i]) owns partials
+// [seg[i], seg[i+1]); one CTA per grid sums them in a fixed order.
+__global__ void k_sum_segments(const double* partials, const int32_t* seg, const int32_t* slot, double* out)
 {
     __shared__ double red[256];
     const int i = blockIdx.x;
@@ -574,7 +574,7 @@ __global__ void k_sum_segments(const double* partials, const int32_t* seg, doubl
         if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[i] = sqrt(red[0]);
+    if (threadIdx.x == 0) out[slot[i]] = sqrt(red[0]);
 }
 
 __global__ void k_sum_partials(const double* partials, int n, double* out)
@@ -853,11 +853,11 @@ cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* p
 }
 
 cudaError_t launch_residual_segments(const LaunchArgs& a, int dtype_f32, int p, double* partials, const int32_t* seg,
-                                     int nseg, double* out, cudaStream_t s)
+                                     const int32_t* slot, int nseg, double* out, cudaStream_t s)
 {
     cudaError_t e = launch_residual_partials(a, dtype_f32, p, partials, s);
     if (e != cudaSuccess) return e;
-    k_sum_segments<<<nseg, 256, 0, s>>>(partials, seg, out);
+    k_sum_segments<<<nseg, 256, 0, s>>>(partials, seg, slot, out);
     return cudaGetLastError();
 }
 

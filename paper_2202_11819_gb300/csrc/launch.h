@@ -45,7 +45,7 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
 cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
                             cudaStream_t s);
 cudaError_t launch_residual_segments(const LaunchArgs& a, int dtype_f32, int p, double* partials, const int32_t* seg,
-                                     int nseg, double* out, cudaStream_t s);
+                                     const int32_t* slot, int nseg, double* out, cudaStream_t s);
 cudaError_t launch_pack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, void* send, int n,
                              cudaStream_t s);
 cudaError_t launch_unpack_face(const LaunchArgs& a, int dtype_f32, int b, int f, int p, const void* recv, int n,

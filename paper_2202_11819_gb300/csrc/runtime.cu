@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -77,15 +78,72 @@ void split_axis(int64_t n, int32_t b, std::vector<int32_t>& size, std::vector<in
 }  // namespace
 
 // One grid of a context. A context holds one or more independent grids
-// (instances) whose blocks share one block table, one pool and one launch.
+// (instances, addressed by slot) whose blocks share one block table, one
+// pool and one launch. Each grid's block storage is one region of the pool
+// that never moves while the grid is resident; the block table is rebuilt
+// from the resident grids when the set changes.
 struct Instance {
+    bool active;
     int64_t dims[3];
     double bc[6];
     int32_t bc_frame;   // largest exponent field over the boundary values
+    int64_t region;     // byte offset of its storage in the pool
+    int64_t bytes;      // bytes of its storage (both buffers, all blocks)
+    std::vector<BlockDesc> geom;  // its blocks; nbr[] are indices within the grid
     int64_t dense_off;  // start of this grid in dense concatenated arrays
-    int32_t b0, b1;     // its blocks [b0, b1)
+    int32_t b0, b1;     // its blocks [b0, b1) in the current table
     int32_t u0, u1;     // its work units [u0, u1)
     int32_t nb[3];
+};
+
+// First-fit allocator of pool regions (bytes, 256-byte granules).
+struct Arena {
+    char* base = nullptr;
+    int64_t capacity = 0;
+    int64_t used = 0;
+    std::map<int64_t, int64_t> free_;  // offset -> size
+    void init(void* b, int64_t cap)
+    {
+        base = (char*)b;
+        capacity = cap;
+        used = 0;
+        free_.clear();
+        if (cap > 0) free_[0] = cap;
+    }
+    bool alloc(int64_t bytes, int64_t* off)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const int64_t rest = it->second - bytes;
+                const int64_t noff = it->first + bytes;
+                free_.erase(it);
+                if (rest > 0) free_[noff] = rest;
+                used += bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(int64_t off, int64_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        used -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
 };
 
 struct jac_ctx {
@@ -93,8 +151,15 @@ struct jac_ctx {
     int64_t dims[3] = {0, 0, 0};
     int32_t req_block[3] = {0, 0, 0};
     int32_t nb[3] = {0, 0, 0};
-    std::vector<Instance> inst;
-    std::vector<int32_t> hframe;  // per instance: bc_frame, the frame's starting value
+    std::vector<Instance> inst;   // by slot
+    std::vector<int32_t> hframe;  // per slot: bc_frame, the frame's starting value
+    int32_t max_slots = 0;
+    bool is_pool = false;         // grids can be added and removed
+    bool dirty = true;            // the block table must be rebuilt
+    Arena own_arena;
+    Arena* arena = nullptr;       // own_arena, or one shared with other pools
+    int32_t* dslot = nullptr;     // per table segment: its slot
+    size_t done_cap = 0;
     int tile_w = 32;              // tile width of the update engine
     int zdepth = 0;               // planes per work unit (0: the whole block)
     int dtype = JAC_F64;
@@ -122,7 +187,7 @@ struct jac_ctx {
     TileUnit* dunits = nullptr;
     void* pool = nullptr;
     int32_t* frame = nullptr;  // per instance: largest exponent field of the grid and its boundary
-    int32_t* dseg = nullptr;   // per instance: first work unit (n_inst + 1 entries)
+    int32_t* dseg = nullptr;   // per resident grid: first work unit (+1 entry)
     double* dres_inst = nullptr;
     size_t partials_cap = 0;
     int64_t pool_elems = 0;
@@ -175,7 +240,26 @@ struct jac_ctx {
     int64_t ncells() const
     {
         int64_t n = 0;
-        for (const Instance& I : inst) n += I.dims[0] * I.dims[1] * I.dims[2];
+        for (const Instance& I : inst)
+            if (I.active) n += I.dims[0] * I.dims[1] * I.dims[2];
+        return n;
+    }
+    int first_active() const
+    {
+        for (size_t i = 0; i < inst.size(); ++i)
+            if (inst[i].active) return (int)i;
+        return -1;
+    }
+    int last_active() const
+    {
+        for (int i = (int)inst.size() - 1; i >= 0; --i)
+            if (inst[i].active) return i;
+        return -1;
+    }
+    int n_active() const
+    {
+        int n = 0;
+        for (const Instance& I : inst) n += I.active ? 1 : 0;
         return n;
     }
     int64_t icells(int i) const { return inst[i].dims[0] * inst[i].dims[1] * inst[i].dims[2]; }
@@ -238,9 +322,9 @@ void exponent_field_max(const double* bc, int dtype, int32_t& e)
 }
 
 // Work units for the current tile width and z depth: per block, its column
-// tiles times its z chunks, blocks in order, so each instance's units are
+// tiles times its z chunks, blocks in table order, so each grid's units are
 // contiguous. Uploads the tile table, the per-block unit counts and the
-// per-instance unit ranges.
+// per-grid unit ranges.
 int build_units(jac_ctx* h)
 {
     const int TW = h->tile_w, TH = tile_rows(h->tile_w);
@@ -248,133 +332,212 @@ int build_units(jac_ctx* h)
     h->ntx.resize(nblocks);
     h->nty.resize(nblocks);
     h->hunits.clear();
-    size_t ii = 0;
-    for (int64_t b = 0; b < nblocks; ++b) {
-        BlockDesc& d = h->hdesc[b];
-        while (ii < h->inst.size() && b >= h->inst[ii].b1) ++ii;
-        if (ii < h->inst.size() && b == h->inst[ii].b0) h->inst[ii].u0 = (int32_t)h->hunits.size();
-        h->ntx[b] = (d.ext[0] + TW - 1) / TW;
-        h->nty[b] = (d.ext[1] + TH - 1) / TH;
-        const int zd = h->zdepth > 0 ? h->zdepth : d.ext[2];
-        const int nzc = (d.ext[2] + zd - 1) / zd;
-        d.ntiles = h->ntx[b] * h->nty[b] * nzc;
-        for (int zc = 0; zc < nzc; ++zc)
-            for (int32_t ty = 0; ty < h->nty[b]; ++ty)
-                for (int32_t tx = 0; tx < h->ntx[b]; ++tx) {
-                    TileUnit u;
-                    u.block = (int32_t)b;
-                    u.x0 = (int16_t)(tx * TW);
-                    u.y0 = (int16_t)(ty * TH);
-                    u.z0 = (int16_t)(zc * zd);
-                    u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
-                    h->hunits.push_back(u);
-                }
-        if (ii < h->inst.size() && b + 1 == h->inst[ii].b1) h->inst[ii].u1 = (int32_t)h->hunits.size();
+    std::vector<int32_t> seg, slot;
+    for (size_t ii = 0; ii < h->inst.size(); ++ii) {
+        Instance& I = h->inst[ii];
+        if (!I.active) continue;
+        I.u0 = (int32_t)h->hunits.size();
+        seg.push_back(I.u0);
+        slot.push_back((int32_t)ii);
+        for (int32_t b = I.b0; b < I.b1; ++b) {
+            BlockDesc& d = h->hdesc[b];
+            h->ntx[b] = (d.ext[0] + TW - 1) / TW;
+            h->nty[b] = (d.ext[1] + TH - 1) / TH;
+            const int zd = h->zdepth > 0 ? h->zdepth : d.ext[2];
+            const int nzc = (d.ext[2] + zd - 1) / zd;
+            d.ntiles = h->ntx[b] * h->nty[b] * nzc;
+            for (int zc = 0; zc < nzc; ++zc)
+                for (int32_t ty = 0; ty < h->nty[b]; ++ty)
+                    for (int32_t tx = 0; tx < h->ntx[b]; ++tx) {
+                        TileUnit u;
+                        u.block = b;
+                        u.x0 = (int16_t)(tx * TW);
+                        u.y0 = (int16_t)(ty * TH);
+                        u.z0 = (int16_t)(zc * zd);
+                        u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
+                        h->hunits.push_back(u);
+                    }
+        }
+        I.u1 = (int32_t)h->hunits.size();
     }
-    std::vector<int32_t> seg(h->inst.size() + 1);
-    for (size_t i = 0; i < h->inst.size(); ++i) seg[i] = h->inst[i].u0;
-    seg[h->inst.size()] = (int32_t)h->hunits.size();
+    seg.push_back((int32_t)h->hunits.size());
     int rc;
-    if (h->hunits.size() > h->partials_cap) {
+    const size_t need = std::max<size_t>(1, h->hunits.size());
+    if (need > h->partials_cap) {
         // earlier, smaller tables stay allocated until the context is destroyed
-        if ((rc = dev_alloc(h, h->hunits.size() * sizeof(TileUnit), (void**)&h->dunits))) return rc;
-        if ((rc = dev_alloc(h, h->hunits.size() * sizeof(double), (void**)&h->partials))) return rc;
-        h->partials_cap = h->hunits.size();
+        if ((rc = dev_alloc(h, need * sizeof(TileUnit), (void**)&h->dunits))) return rc;
+        if ((rc = dev_alloc(h, need * sizeof(double), (void**)&h->partials))) return rc;
+        h->partials_cap = need;
     }
-    CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), nblocks * sizeof(BlockDesc), cudaMemcpyHostToDevice, h->stream),
-       "copy block table");
-    CU(cudaMemcpyAsync(h->dunits, h->hunits.data(), h->hunits.size() * sizeof(TileUnit), cudaMemcpyHostToDevice,
-                       h->stream),
-       "copy tile table");
+    if (nblocks > 0)
+        CU(cudaMemcpyAsync(h->ddesc, h->hdesc.data(), nblocks * sizeof(BlockDesc), cudaMemcpyHostToDevice, h->stream),
+           "copy block table");
+    if (!h->hunits.empty())
+        CU(cudaMemcpyAsync(h->dunits, h->hunits.data(), h->hunits.size() * sizeof(TileUnit), cudaMemcpyHostToDevice,
+                           h->stream),
+           "copy tile table");
     CU(cudaMemcpyAsync(h->dseg, seg.data(), seg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
        "copy unit ranges");
+    if (!slot.empty())
+        CU(cudaMemcpyAsync(h->dslot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
+           "copy slot map");
     // the host tables must stay valid until the copies above have run
     CU(cudaStreamSynchronize(h->stream), "table sync");
     h->pctas = 0;
     return JAC_OK;
 }
 
-int build_layout(jac_ctx* h)
+// Blocks of one grid and the bytes of its storage; block offsets are relative
+// to the grid's region (elements), neighbours are indices within the grid.
+int64_t instance_geometry(const jac_ctx* h, Instance& I)
 {
     const int OX = 128 / h->esize;
-    int64_t off = 0, dense = 0;
+    std::vector<int32_t> sx, ox, sy, oy, sz, oz;
+    split_axis(I.dims[0], h->req_block[0], sx, ox);
+    split_axis(I.dims[1], h->req_block[1], sy, oy);
+    split_axis(I.dims[2], h->req_block[2], sz, oz);
+    I.nb[0] = (int32_t)sx.size();
+    I.nb[1] = (int32_t)sy.size();
+    I.nb[2] = (int32_t)sz.size();
+    I.geom.clear();
+    int64_t off = 0;
+    for (int32_t bk = 0; bk < I.nb[2]; ++bk)
+        for (int32_t bj = 0; bj < I.nb[1]; ++bj)
+            for (int32_t bi = 0; bi < I.nb[0]; ++bi) {
+                BlockDesc d;
+                memset(&d, 0, sizeof d);
+                d.ext[0] = sx[bi];
+                d.ext[1] = sy[bj];
+                d.ext[2] = sz[bk];
+                d.org[0] = ox[bi];
+                d.org[1] = oy[bj];
+                d.org[2] = oz[bk];
+                const int32_t ids[3] = {bi, bj, bk};
+                for (int f = 0; f < 6; ++f) {
+                    const int a = f >> 1, dir = (f & 1) ? 1 : -1;
+                    int32_t q[3] = {bi, bj, bk};
+                    q[a] = ids[a] + dir;
+                    if (q[a] < 0 || q[a] >= I.nb[a]) d.nbr[f] = -1;
+                    else d.nbr[f] = (int32_t)(q[0] + (int64_t)I.nb[0] * (q[1] + (int64_t)I.nb[1] * q[2]));
+                    d.bc[f] = I.bc[f];
+                    d.bcf[f] = (float)I.bc[f];
+                }
+                d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
+                d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
+                const int64_t storage = d.plane * (d.ext[2] + 2);
+                d.off[0] = off;
+                d.off[1] = off + storage;
+                off += 2 * storage;
+                d.gdim[0] = (int32_t)I.dims[0];
+                d.gdim[1] = (int32_t)I.dims[1];
+                d.gdim[2] = (int32_t)I.dims[2];
+                I.geom.push_back(d);
+            }
+    return off * h->esize;
+}
+
+// Place a grid in a free slot and a free region of the pool (zeroed).
+int add_instance(jac_ctx* h, const int64_t dims[3], const double bc[6], int32_t* slot_out)
+{
+    Instance I;
+    I.active = true;
+    for (int a = 0; a < 3; ++a) I.dims[a] = dims[a];
+    for (int f = 0; f < 6; ++f) I.bc[f] = bc[f];
+    exponent_field_max(I.bc, h->dtype, I.bc_frame);
+    I.bytes = instance_geometry(h, I);
+    if (!h->arena->alloc(I.bytes, &I.region))
+        return fail(JAC_EBUDGET, "grid of %lld bytes does not fit the pool (%lld of %lld bytes in use)",
+                    (long long)I.bytes, (long long)h->arena->used, (long long)h->arena->capacity);
+    const int64_t elem0 = I.region / h->esize;
+    for (BlockDesc& d : I.geom) {
+        d.off[0] += elem0;
+        d.off[1] += elem0;
+    }
+    int32_t s = -1;
+    for (size_t i = 0; i < h->inst.size(); ++i)
+        if (!h->inst[i].active) {
+            s = (int32_t)i;
+            break;
+        }
+    if (s < 0) {
+        if ((int32_t)h->inst.size() >= h->max_slots) {
+            h->arena->release(I.region, I.bytes);
+            return fail(JAC_EBUDGET, "all %d grid slots are in use", h->max_slots);
+        }
+        s = (int32_t)h->inst.size();
+        h->inst.emplace_back();
+        h->hframe.push_back(0);
+    }
+    h->inst[s] = std::move(I);
+    h->hframe[s] = h->inst[s].bc_frame;
+    CU(cudaMemsetAsync(h->arena->base + h->inst[s].region, 0, (size_t)h->inst[s].bytes, h->stream), "clear region");
+    CU(cudaMemcpyAsync(h->frame + s, h->hframe.data() + s, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
+       "init frame");
+    CU(cudaStreamSynchronize(h->stream), "add sync");
+    h->dirty = true;
+    *slot_out = s;
+    return JAC_OK;
+}
+
+int remove_instance(jac_ctx* h, int32_t s)
+{
+    if (s < 0 || s >= (int32_t)h->inst.size() || !h->inst[s].active) return fail(JAC_EINVAL, "slot %d not in use", s);
+    CU(cudaStreamSynchronize(h->stream), "remove sync");
+    h->arena->release(h->inst[s].region, h->inst[s].bytes);
+    h->inst[s].active = false;
+    h->inst[s].geom.clear();
+    h->dirty = true;
+    return JAC_OK;
+}
+
+void destroy_graphs(jac_ctx* h);
+
+// Rebuild the block table from the resident grids (slot order).
+int refresh(jac_ctx* h)
+{
+    if (!h->dirty) return JAC_OK;
     h->hdesc.clear();
+    int64_t dense = 0;
     for (size_t ii = 0; ii < h->inst.size(); ++ii) {
         Instance& I = h->inst[ii];
-        std::vector<int32_t> sx, ox, sy, oy, sz, oz;
-        split_axis(I.dims[0], h->req_block[0], sx, ox);
-        split_axis(I.dims[1], h->req_block[1], sy, oy);
-        split_axis(I.dims[2], h->req_block[2], sz, oz);
-        I.nb[0] = (int32_t)sx.size();
-        I.nb[1] = (int32_t)sy.size();
-        I.nb[2] = (int32_t)sz.size();
+        if (!I.active) continue;
         I.b0 = (int32_t)h->hdesc.size();
         I.dense_off = dense;
-        const int64_t nbi = (int64_t)I.nb[0] * I.nb[1] * I.nb[2];
-        if ((int64_t)h->hdesc.size() + nbi > (1 << 24)) return fail(JAC_EINVAL, "too many blocks");
-        for (int32_t bk = 0; bk < I.nb[2]; ++bk)
-            for (int32_t bj = 0; bj < I.nb[1]; ++bj)
-                for (int32_t bi = 0; bi < I.nb[0]; ++bi) {
-                    BlockDesc d;
-                    memset(&d, 0, sizeof d);
-                    d.ext[0] = sx[bi];
-                    d.ext[1] = sy[bj];
-                    d.ext[2] = sz[bk];
-                    d.org[0] = ox[bi];
-                    d.org[1] = oy[bj];
-                    d.org[2] = oz[bk];
-                    const int32_t ids[3] = {bi, bj, bk};
-                    for (int f = 0; f < 6; ++f) {
-                        const int a = f >> 1, dir = (f & 1) ? 1 : -1;
-                        int32_t q[3] = {bi, bj, bk};
-                        q[a] = ids[a] + dir;
-                        if (q[a] < 0 || q[a] >= I.nb[a]) d.nbr[f] = -1;
-                        else d.nbr[f] = I.b0 + (int32_t)(q[0] + (int64_t)I.nb[0] * (q[1] + (int64_t)I.nb[1] * q[2]));
-                        d.bc[f] = I.bc[f];
-                        d.bcf[f] = (float)I.bc[f];
-                    }
-                    d.inst = (int32_t)ii;
-                    d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
-                    d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
-                    const int64_t storage = d.plane * (d.ext[2] + 2);
-                    d.off[0] = off;
-                    d.off[1] = off + storage;
-                    off += 2 * storage;
-                    d.dense = dense;
-                    d.gdim[0] = (int32_t)I.dims[0];
-                    d.gdim[1] = (int32_t)I.dims[1];
-                    d.gdim[2] = (int32_t)I.dims[2];
-                    h->hdesc.push_back(d);
-                }
+        for (const BlockDesc& g : I.geom) {
+            BlockDesc d = g;
+            for (int f = 0; f < 6; ++f)
+                if (d.nbr[f] >= 0) d.nbr[f] += I.b0;
+            d.inst = (int32_t)ii;
+            d.dense = dense;
+            h->hdesc.push_back(d);
+        }
         I.b1 = (int32_t)h->hdesc.size();
         dense += I.dims[0] * I.dims[1] * I.dims[2];
     }
-    if (h->inst.size() == 1)
-        for (int a = 0; a < 3; ++a) h->nb[a] = h->inst[0].nb[a];
     const int64_t nblocks = (int64_t)h->hdesc.size();
-    const size_t ninst = h->inst.size();
-    h->hframe.resize(ninst);
-    for (size_t i = 0; i < ninst; ++i) h->hframe[i] = h->inst[i].bc_frame;
+    if (nblocks > (1 << 24)) return fail(JAC_EINVAL, "too many blocks");
     int rc;
-    if ((rc = dev_alloc(h, (size_t)off * h->esize, &h->pool))) return rc;
-    if ((rc = dev_alloc(h, nblocks * sizeof(BlockDesc), (void**)&h->ddesc))) return rc;
-    if ((rc = dev_alloc(h, nblocks * sizeof(uint32_t), (void**)&h->done))) return rc;
-    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
-    if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
-    if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
-    if ((rc = dev_alloc(h, ninst * sizeof(double), (void**)&h->dres_inst))) return rc;
-    if ((rc = dev_alloc(h, ninst * sizeof(int32_t), (void**)&h->frame))) return rc;
-    if ((rc = dev_alloc(h, (ninst + 1) * sizeof(int32_t), (void**)&h->dseg))) return rc;
-    CU(cudaMemcpyAsync(h->frame, h->hframe.data(), ninst * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
-       "init frame");
+    if ((size_t)nblocks > h->done_cap) {
+        const size_t cap = std::max<size_t>(64, (size_t)nblocks * 2);
+        if ((rc = dev_alloc(h, cap * sizeof(BlockDesc), (void**)&h->ddesc))) return rc;
+        if ((rc = dev_alloc(h, cap * sizeof(uint32_t), (void**)&h->done))) return rc;
+        h->done_cap = cap;
+    }
+    destroy_graphs(h);
     if ((rc = build_units(h))) return rc;
-    CU(cudaMemsetAsync(h->pool, 0, (size_t)off * h->esize, h->stream), "clear pool");
-    CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
-    CU(launch_init_ghosts(h->args(), h->dtype == JAC_F32, h->stream), "init ghosts");
-    h->launches += 1;
-    h->pool_elems = off;
-    CU(cudaStreamSynchronize(h->stream), "create sync");
+    if (nblocks > 0) {
+        CU(launch_init_ghosts(h->args(), h->dtype == JAC_F32, h->stream), "init ghosts");
+        h->launches += 1;
+    }
+    h->dirty = false;
     return JAC_OK;
+}
+
+int check_ready(jac_ctx* h)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    return refresh(h);
 }
 
 int ensure_halo(jac_ctx* h)
@@ -590,6 +753,7 @@ int read_status(jac_ctx* h)
 // (their dense data back to back), resetting their frames first.
 int write_dense(jac_ctx* h, int i0, int i1, const void* src, size_t n, int src_f32, bool src_on_device)
 {
+    if (i0 < 0 || i1 <= i0) return fail(JAC_ESTATE, "no resident grid");
     const size_t bytes = n * (src_f32 ? 4 : 8);
     const void* dsrc = src;
     if (!src_on_device) {
@@ -607,13 +771,14 @@ int write_dense(jac_ctx* h, int i0, int i1, const void* src, size_t n, int src_f
                       h->stream),
        "scatter");
     h->launches += 1;
-    if (i0 == 0 && i1 == (int)h->inst.size()) h->iters = 0;
+    if (i0 == h->first_active() && i1 == h->last_active() + 1) h->iters = 0;
     if (!src_on_device) CU(cudaStreamSynchronize(h->stream), "write sync");
     return JAC_OK;
 }
 
 int read_dense(jac_ctx* h, int i0, int i1, void* dst, size_t n, int dst_f32, bool dst_on_device)
 {
+    if (i0 < 0 || i1 <= i0) return fail(JAC_ESTATE, "no resident grid");
     const size_t bytes = n * (dst_f32 ? 4 : 8);
     void* ddst = dst;
     if (!dst_on_device) {
@@ -630,6 +795,72 @@ int read_dense(jac_ctx* h, int i0, int i1, void* dst, size_t n, int dst_f32, boo
         CU(cudaMemcpyAsync(dst, h->dense, bytes, cudaMemcpyDeviceToHost, h->stream), "copy out");
         return read_status(h);
     }
+    return JAC_OK;
+}
+
+int sync_stream(jac_ctx* h)
+{
+    CU(cudaStreamSynchronize(h->stream), "sync");
+    return JAC_OK;
+}
+
+// Stream, allocator and the fixed-size device tables (per slot and status).
+int open_ctx(jac_ctx* h, void* stream)
+{
+    h->alloc = g_alloc;
+    h->free_fn = g_free;
+    h->alloc_user = g_alloc_user;
+    cudaError_t e;
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+        e = cudaStreamGetDevice(h->stream, &h->device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamGetDevice");
+        cudaSetDevice(h->device);
+    } else {
+        cudaGetDevice(&h->device);
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        h->own_stream = true;
+    }
+    const size_t ns = (size_t)std::max(1, h->max_slots);
+    int rc;
+    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
+    if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
+    if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
+    if ((rc = dev_alloc(h, ns * sizeof(double), (void**)&h->dres_inst))) return rc;
+    if ((rc = dev_alloc(h, ns * sizeof(int32_t), (void**)&h->frame))) return rc;
+    if ((rc = dev_alloc(h, (ns + 1) * sizeof(int32_t), (void**)&h->dseg))) return rc;
+    if ((rc = dev_alloc(h, ns * sizeof(int32_t), (void**)&h->dslot))) return rc;
+    CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
+    return JAC_OK;
+}
+
+// A pool context whose regions come from an arena owned by someone else
+// (the server shares one arena between its binary64 and binary32 pools).
+int create_pool_shared(jac_ctx** out, int32_t dtype, Arena* arena, int32_t max_grids, int32_t bx, int32_t by,
+                       int32_t bz, void* stream)
+{
+    jac_ctx* h = new jac_ctx();
+    h->req_block[0] = bx;
+    h->req_block[1] = by;
+    h->req_block[2] = bz;
+    h->dtype = dtype;
+    h->esize = dtype == JAC_F32 ? 4 : 8;
+    h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
+    h->max_slots = max_grids;
+    h->is_pool = true;
+    h->arena = arena;
+    h->pool = arena->base;
+    int rc = open_ctx(h, stream);
+    if (!rc) rc = refresh(h);
+    if (!rc) rc = sync_stream(h);
+    if (rc) {
+        std::string msg = g_last_error;
+        jac_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
     return JAC_OK;
 }
 
@@ -667,38 +898,36 @@ int create_ctx(jac_ctx** out, int32_t n_inst, const int64_t* dims, int32_t bx, i
     h->dtype = dtype;
     h->esize = dtype == JAC_F32 ? 4 : 8;
     h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
-    h->inst.resize(n_inst);
-    for (int32_t i = 0; i < n_inst; ++i) {
-        Instance& I = h->inst[i];
-        memset(&I, 0, sizeof I);
-        for (int a = 0; a < 3; ++a) I.dims[a] = dims[3 * i + a];
-        for (int f = 0; f < 6; ++f) I.bc[f] = bc[6 * i + f];
-        exponent_field_max(I.bc, dtype, I.bc_frame);
-    }
+    h->max_slots = n_inst;
     for (int a = 0; a < 3; ++a) h->dims[a] = n_inst == 1 ? dims[a] : 0;
     for (int f = 0; f < 6; ++f) h->bc[f] = bc[f];
-    h->alloc = g_alloc;
-    h->free_fn = g_free;
-    h->alloc_user = g_alloc_user;
-    cudaError_t e;
-    if (stream) {
-        h->stream = (cudaStream_t)stream;
-        e = cudaStreamGetDevice(h->stream, &h->device);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "cudaStreamGetDevice");
-        }
-        cudaSetDevice(h->device);
-    } else {
-        cudaGetDevice(&h->device);
-        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) {
-            delete h;
-            return cuda_fail(e, "cudaStreamCreate");
-        }
-        h->own_stream = true;
+    int rc = open_ctx(h, stream);
+    if (rc) {
+        std::string msg = g_last_error;
+        jac_destroy(h);
+        g_last_error = msg;
+        return rc;
     }
-    int rc = build_layout(h);
+    // one region per grid, back to back: size the pool to their sum
+    int64_t total = 0;
+    for (int32_t i = 0; i < n_inst; ++i) {
+        Instance I;
+        for (int a = 0; a < 3; ++a) I.dims[a] = dims[3 * i + a];
+        for (int f = 0; f < 6; ++f) I.bc[f] = bc[6 * i + f];
+        total += (instance_geometry(h, I) + 255) / 256 * 256;
+    }
+    void* pool = nullptr;
+    if (!(rc = dev_alloc(h, (size_t)total, &pool))) {
+        h->own_arena.init(pool, total);
+        h->arena = &h->own_arena;
+        h->pool = pool;
+        for (int32_t i = 0; i < n_inst && !rc; ++i) {
+            int32_t slot;
+            rc = add_instance(h, dims + 3 * i, bc + 6 * i, &slot);
+        }
+    }
+    if (!rc) rc = refresh(h);
+    if (!rc) rc = sync_stream(h);
     if (rc) {
         std::string msg = g_last_error;
         jac_destroy(h);
@@ -782,6 +1011,8 @@ int jac_set_mode(jac_ctx* h, int32_t mode)
     int rc = check_ctx(h);
     if (rc) return rc;
     if (mode < JAC_MODE_UNFUSED || mode > JAC_MODE_GRAPH_FUSED) return fail(JAC_EINVAL, "unknown mode %d", mode);
+    if (h->is_pool && (mode == JAC_MODE_UNFUSED || mode == JAC_MODE_GRAPH))
+        return fail(JAC_EINVAL, "pools run the fused or persistent forms only");
     h->mode = mode;
     return JAC_OK;
 }
@@ -799,73 +1030,73 @@ int jac_set_arith(jac_ctx* h, int32_t arith)
 
 int jac_write(jac_ctx* h, const double* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
     for (size_t i = 0; i < n_cells; ++i)
         if (!value_ok(host[i], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", i);
-    return write_dense(h, 0, (int)h->inst.size(), host, n_cells, 0, false);
+    return write_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 0, false);
 }
 
 int jac_write_f32(jac_ctx* h, const float* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_write_f32 needs an F32 context");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
     for (size_t i = 0; i < n_cells; ++i)
         if (!std::isfinite(host[i])) return fail(JAC_EINVAL, "value at %zu not finite", i);
-    return write_dense(h, 0, (int)h->inst.size(), host, n_cells, 1, false);
+    return write_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 1, false);
 }
 
 int jac_write_device(jac_ctx* h, const void* dev, size_t n_cells, int32_t dtype)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!dev) return fail(JAC_EINVAL, "null device pointer");
     if (dtype != h->dtype) return fail(JAC_EINVAL, "dtype must equal the context's dtype");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return write_dense(h, 0, (int)h->inst.size(), dev, n_cells, dtype == JAC_F32, true);
+    return write_dense(h, h->first_active(), h->last_active() + 1, dev, n_cells, dtype == JAC_F32, true);
 }
 
 int jac_read(jac_ctx* h, double* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, 0, (int)h->inst.size(), host, n_cells, 0, false);
+    return read_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 0, false);
 }
 
 int jac_read_f32(jac_ctx* h, float* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_read_f32 needs an F32 context");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, 0, (int)h->inst.size(), host, n_cells, 1, false);
+    return read_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 1, false);
 }
 
 int jac_read_device(jac_ctx* h, void* dev, size_t n_cells, int32_t dtype)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!dev) return fail(JAC_EINVAL, "null device pointer");
     if (dtype != h->dtype && !(h->dtype == JAC_F32 && dtype == JAC_F64))
         return fail(JAC_EINVAL, "dtype must be the context's dtype (or F64 for an F32 context)");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    return read_dense(h, 0, (int)h->inst.size(), dev, n_cells, dtype == JAC_F32, true);
+    return read_dense(h, h->first_active(), h->last_active() + 1, dev, n_cells, dtype == JAC_F32, true);
 }
 
 int jac_iterate(jac_ctx* h, int64_t n)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (n < 0) return fail(JAC_EINVAL, "n_iters must be >= 0");
-    if (n == 0) return JAC_OK;
+    if (n == 0 || h->hunits.empty()) return JAC_OK;
     const int f32 = h->dtype == JAC_F32;
     switch (h->mode) {
         case JAC_MODE_FUSED:
@@ -950,9 +1181,10 @@ int jac_iterate(jac_ctx* h, int64_t n)
 
 int jac_residual_device(jac_ctx* h, double* dev_out)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
+    if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
     CU(launch_residual(h->args(), h->dtype == JAC_F32, h->parity, h->partials, dev_out, h->stream), "residual");
     h->launches += 2;
     return JAC_OK;
@@ -960,7 +1192,7 @@ int jac_residual_device(jac_ctx* h, double* dev_out)
 
 int jac_residual(jac_ctx* h, double* out)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!out) return fail(JAC_EINVAL, "null output pointer");
     if ((rc = jac_residual_device(h, h->dres))) return rc;
@@ -993,7 +1225,7 @@ int jac_info(jac_ctx* h, jac_info_t* info)
     info->iterations = h->iters;
     info->device_bytes = h->device_bytes;
     info->kernel_launches = h->launches;
-    info->n_instances = (int32_t)h->inst.size();
+    info->n_instances = h->n_active();
     info->tile_w = h->tile_w;
     info->zdepth = h->zdepth;
     info->n_units = (int32_t)h->hunits.size();
@@ -1003,9 +1235,9 @@ int jac_info(jac_ctx* h, jac_info_t* info)
 
 int jac_write_instance(jac_ctx* h, int32_t i, const double* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
-    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (i < 0 || i >= (int32_t)h->inst.size() || !h->inst[i].active) return fail(JAC_EINVAL, "grid slot %d not in use", i);
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
     for (size_t q = 0; q < n_cells; ++q)
@@ -1015,9 +1247,9 @@ int jac_write_instance(jac_ctx* h, int32_t i, const double* host, size_t n_cells
 
 int jac_write_instance_device(jac_ctx* h, int32_t i, const void* dev, size_t n_cells, int32_t dtype)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
-    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (i < 0 || i >= (int32_t)h->inst.size() || !h->inst[i].active) return fail(JAC_EINVAL, "grid slot %d not in use", i);
     if (!dev) return fail(JAC_EINVAL, "null device pointer");
     if (dtype != h->dtype) return fail(JAC_EINVAL, "dtype must equal the context's dtype");
     if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
@@ -1026,9 +1258,9 @@ int jac_write_instance_device(jac_ctx* h, int32_t i, const void* dev, size_t n_c
 
 int jac_read_instance(jac_ctx* h, int32_t i, double* host, size_t n_cells)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
-    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (i < 0 || i >= (int32_t)h->inst.size() || !h->inst[i].active) return fail(JAC_EINVAL, "grid slot %d not in use", i);
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
     return read_dense(h, i, i + 1, host, n_cells, 0, false);
@@ -1036,9 +1268,9 @@ int jac_read_instance(jac_ctx* h, int32_t i, double* host, size_t n_cells)
 
 int jac_read_instance_device(jac_ctx* h, int32_t i, void* dev, size_t n_cells, int32_t dtype)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
-    if (i < 0 || i >= (int32_t)h->inst.size()) return fail(JAC_EINVAL, "instance %d out of range", i);
+    if (i < 0 || i >= (int32_t)h->inst.size() || !h->inst[i].active) return fail(JAC_EINVAL, "grid slot %d not in use", i);
     if (!dev) return fail(JAC_EINVAL, "null device pointer");
     if (dtype != h->dtype && !(h->dtype == JAC_F32 && dtype == JAC_F64))
         return fail(JAC_EINVAL, "dtype must be the context's dtype (or F64 for an F32 context)");
@@ -1048,11 +1280,12 @@ int jac_read_instance_device(jac_ctx* h, int32_t i, void* dev, size_t n_cells, i
 
 int jac_residual_instances_device(jac_ctx* h, double* dev_out)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
-    CU(launch_residual_segments(h->args(), h->dtype == JAC_F32, h->parity, h->partials, h->dseg, (int)h->inst.size(),
-                                dev_out, h->stream),
+    if (h->hunits.empty()) return JAC_OK;
+    CU(launch_residual_segments(h->args(), h->dtype == JAC_F32, h->parity, h->partials, h->dseg, h->dslot,
+                                h->n_active(), dev_out, h->stream),
        "residual");
     h->launches += 2;
     return JAC_OK;
@@ -1060,18 +1293,22 @@ int jac_residual_instances_device(jac_ctx* h, double* dev_out)
 
 int jac_residual_instances(jac_ctx* h, double* out)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!out) return fail(JAC_EINVAL, "null output pointer");
     if ((rc = jac_residual_instances_device(h, h->dres_inst))) return rc;
-    CU(cudaMemcpyAsync(out, h->dres_inst, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
-       "copy residuals");
-    return read_status(h);
+    if (!h->inst.empty())
+        CU(cudaMemcpyAsync(out, h->dres_inst, h->inst.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream),
+           "copy residuals");
+    rc = read_status(h);
+    for (size_t i = 0; i < h->inst.size(); ++i)
+        if (!h->inst[i].active) out[i] = std::nan("");
+    return rc;
 }
 
 int jac_set_tile(jac_ctx* h, int32_t tile_w, int32_t zdepth)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (!tile_width_supported(tile_w)) return fail(JAC_EINVAL, "tile width must be 16, 32 or 64");
     if (zdepth < 0 || zdepth > 256) return fail(JAC_EINVAL, "z depth must be in [0, 256]");
@@ -1087,10 +1324,14 @@ int jac_set_tile(jac_ctx* h, int32_t tile_w, int32_t zdepth)
 // itself, keep the fastest, and put the grid back as it was.
 int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
 {
-    int rc = check_ctx(h);
+    int rc = check_ready(h);
     if (rc) return rc;
     if (trial_iters < 1) return fail(JAC_EINVAL, "trial_iters must be >= 1");
-    const size_t bytes = (size_t)h->pool_elems * h->esize;
+    if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
+    int64_t extent = 0;
+    for (const Instance& I : h->inst)
+        if (I.active) extent = std::max(extent, I.region + I.bytes);
+    const size_t bytes = (size_t)extent;
     void* snap = nullptr;
     CU(cudaMallocAsync(&snap, bytes, h->stream), "autotune snapshot");
     CU(cudaMemcpyAsync(snap, h->pool, bytes, cudaMemcpyDeviceToDevice, h->stream), "snapshot");
@@ -1144,6 +1385,95 @@ int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
     return JAC_OK;
 }
 
+int jac_storage_bytes(const int64_t dims[3], int32_t bx, int32_t by, int32_t bz, int32_t dtype, int64_t* bytes)
+{
+    if (!dims || !bytes) return fail(JAC_EINVAL, "null argument");
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256) return fail(JAC_EINVAL, "bad block dims");
+    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "bad dtype");
+    jac_ctx tmp;
+    tmp.req_block[0] = bx;
+    tmp.req_block[1] = by;
+    tmp.req_block[2] = bz;
+    tmp.dtype = dtype;
+    tmp.esize = dtype == JAC_F32 ? 4 : 8;
+    Instance I;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > (1 << 30)) return fail(JAC_EINVAL, "bad grid dims");
+        I.dims[a] = dims[a];
+    }
+    *bytes = (instance_geometry(&tmp, I) + 255) / 256 * 256;
+    return JAC_OK;
+}
+
+int jac_create_pool(jac_ctx** out, int32_t dtype, int64_t capacity_bytes, int32_t max_grids, int32_t bx, int32_t by,
+                    int32_t bz, void* stream)
+{
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "dtype must be JAC_F64 or JAC_F32");
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256)
+        return fail(JAC_EINVAL, "block dims must be in [1, 256]");
+    if (capacity_bytes < 256 || max_grids < 1 || max_grids > (1 << 20)) return fail(JAC_EINVAL, "bad pool size");
+    jac_ctx* h = new jac_ctx();
+    h->req_block[0] = bx;
+    h->req_block[1] = by;
+    h->req_block[2] = bz;
+    h->dtype = dtype;
+    h->esize = dtype == JAC_F32 ? 4 : 8;
+    h->arith = dtype == JAC_F32 ? JAC_ARITH_SEQ : JAC_ARITH_EXACT;
+    h->max_slots = max_grids;
+    h->is_pool = true;
+    int rc = open_ctx(h, stream);
+    void* pool = nullptr;
+    if (!rc) rc = dev_alloc(h, (size_t)capacity_bytes, &pool);
+    if (!rc) {
+        h->own_arena.init(pool, capacity_bytes);
+        h->arena = &h->own_arena;
+        h->pool = pool;
+        rc = refresh(h);
+    }
+    if (!rc) rc = sync_stream(h);
+    if (rc) {
+        std::string msg = g_last_error;
+        jac_destroy(h);
+        g_last_error = msg;
+        return rc;
+    }
+    *out = h;
+    return JAC_OK;
+}
+
+int jac_pool_add(jac_ctx* h, const int64_t dims[3], const double bc[6], int32_t* slot)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!h->is_pool) return fail(JAC_ESTATE, "grids can be added to pools only");
+    if (!dims || !bc || !slot) return fail(JAC_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (1 << 30)) return fail(JAC_EINVAL, "grid dims must be in [1, 2^30]");
+    for (int f = 0; f < 6; ++f)
+        if (!value_ok(bc[f], h->dtype)) return fail(JAC_EINVAL, "boundary value %d not finite or out of range", f);
+    return add_instance(h, dims, bc, slot);
+}
+
+int jac_pool_remove(jac_ctx* h, int32_t slot)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (!h->is_pool) return fail(JAC_ESTATE, "grids can be removed from pools only");
+    return remove_instance(h, slot);
+}
+
+int jac_pool_usage(jac_ctx* h, int64_t* used_bytes, int64_t* capacity_bytes, int32_t* grids)
+{
+    int rc = check_ctx(h);
+    if (rc) return rc;
+    if (used_bytes) *used_bytes = h->arena ? h->arena->used : 0;
+    if (capacity_bytes) *capacity_bytes = h->arena ? h->arena->capacity : 0;
+    if (grids) *grids = h->n_active();
+    return JAC_OK;
+}
+
 int jac_set_wait_limit_ns(jac_ctx* h, int64_t ns)
 {
     int rc = check_ctx(h);
@@ -1160,6 +1490,258 @@ int jac_debug_withhold_progress(jac_ctx* h, int32_t block, int64_t after_iter)
     if (block >= (int32_t)h->hdesc.size()) return fail(JAC_EINVAL, "block out of range");
     h->hold_block = block < 0 ? -1 : block;
     h->hold_after = after_iter;
+    return JAC_OK;
+}
+
+
+// ====================================================================== server
+
+}  // extern "C"
+
+#include <chrono>
+#include <deque>
+
+struct ServeReq {
+    int64_t id = 0;
+    int64_t dims[3] = {0, 0, 0};
+    int32_t dtype = JAC_F64;
+    double bc[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<double> init, result;
+    double tol = 0.0;
+    int64_t max_iters = 0;
+    int64_t iters = 0;
+    double residual = 0.0;
+    int32_t slot = -1;
+    int32_t state = 0;  // 0 queued, 1 running, 2 done, 3 failed
+    double t_submit = 0, t_admit = 0, t_done = 0;
+};
+
+struct jac_server {
+    int device = 0;
+    Arena arena;
+    void* base = nullptr;
+    size_t base_bytes = 0;
+    jac_ctx* pool[2] = {nullptr, nullptr};  // binary64, binary32
+    cudaStream_t stream[2] = {nullptr, nullptr};
+    double* hres[2] = {nullptr, nullptr};  // pinned per-slot residuals
+    int32_t max_active = 0, bx = 64, by = 64, bz = 64, chunk = 50;
+    std::deque<int64_t> queue;
+    std::map<int64_t, ServeReq> reqs;
+    std::deque<int64_t> finished;
+    int64_t next_id = 1;
+    int32_t running = 0;
+    int64_t cell_updates = 0;
+    std::chrono::steady_clock::time_point t0;
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+extern "C" {
+
+int jac_server_destroy(jac_server* s)
+{
+    if (!s) return JAC_OK;
+    cudaSetDevice(s->device);
+    for (int d = 0; d < 2; ++d) {
+        if (s->pool[d]) jac_destroy(s->pool[d]);
+        if (s->stream[d]) {
+            cudaStreamSynchronize(s->stream[d]);
+            cudaStreamDestroy(s->stream[d]);
+        }
+        if (s->hres[d]) cudaFreeHost(s->hres[d]);
+    }
+    if (s->base) cudaFree(s->base);
+    delete s;
+    return JAC_OK;
+}
+
+int jac_server_create(jac_server** out, int64_t budget_bytes, int32_t max_active, int32_t bx, int32_t by, int32_t bz,
+                      int32_t chunk_iters)
+{
+    if (!out) return fail(JAC_EINVAL, "null output pointer");
+    *out = nullptr;
+    if (budget_bytes < 4096 || max_active < 1 || max_active > 65536 || chunk_iters < 1)
+        return fail(JAC_EINVAL, "bad server parameters");
+    if (bx < 1 || by < 1 || bz < 1 || bx > 256 || by > 256 || bz > 256) return fail(JAC_EINVAL, "bad block dims");
+    jac_server* s = new jac_server();
+    cudaGetDevice(&s->device);
+    s->max_active = max_active;
+    s->bx = bx;
+    s->by = by;
+    s->bz = bz;
+    s->chunk = chunk_iters;
+    s->t0 = std::chrono::steady_clock::now();
+    cudaError_t e = cudaMalloc(&s->base, (size_t)budget_bytes);
+    if (e != cudaSuccess) {
+        jac_server_destroy(s);
+        return cuda_fail(e, "server arena");
+    }
+    s->base_bytes = (size_t)budget_bytes;
+    s->arena.init(s->base, budget_bytes);
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    for (int d = 0; d < 2; ++d) {
+        e = cudaStreamCreateWithPriority(&s->stream[d], cudaStreamNonBlocking, lo);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->hres[d], sizeof(double) * (size_t)max_active);
+        if (e != cudaSuccess) {
+            jac_server_destroy(s);
+            return cuda_fail(e, "server streams");
+        }
+        int rc = create_pool_shared(&s->pool[d], d == 0 ? JAC_F64 : JAC_F32, &s->arena, max_active, bx, by, bz,
+                                    (void*)s->stream[d]);
+        if (rc) {
+            std::string msg = g_last_error;
+            jac_server_destroy(s);
+            g_last_error = msg;
+            return rc;
+        }
+    }
+    *out = s;
+    return JAC_OK;
+}
+
+int jac_server_submit(jac_server* s, const int64_t dims[3], int32_t dtype, const double bc[6], const double* init,
+                      double tol, int64_t max_iters, int64_t* req_id)
+{
+    if (!s || !dims || !bc || !init || !req_id) return fail(JAC_EINVAL, "null argument");
+    if (dtype != JAC_F64 && dtype != JAC_F32) return fail(JAC_EINVAL, "bad dtype");
+    if (!(tol >= 0.0) || max_iters < 0) return fail(JAC_EINVAL, "bad stopping rule");
+    int64_t n = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (dims[a] < 1 || dims[a] > (1 << 30)) return fail(JAC_EINVAL, "bad grid dims");
+        n *= dims[a];
+    }
+    for (int f = 0; f < 6; ++f)
+        if (!value_ok(bc[f], dtype)) return fail(JAC_EINVAL, "boundary value %d not finite or out of range", f);
+    for (int64_t q = 0; q < n; ++q)
+        if (!value_ok(init[q], dtype)) return fail(JAC_EINVAL, "value at %lld not finite or out of range", (long long)q);
+    int64_t bytes = 0;
+    int rc = jac_storage_bytes(dims, s->bx, s->by, s->bz, dtype, &bytes);
+    if (rc) return rc;
+    if (bytes > s->arena.capacity) return fail(JAC_EBUDGET, "grid of %lld bytes exceeds the budget", (long long)bytes);
+    ServeReq r;
+    r.id = s->next_id++;
+    for (int a = 0; a < 3; ++a) r.dims[a] = dims[a];
+    for (int f = 0; f < 6; ++f) r.bc[f] = bc[f];
+    r.dtype = dtype;
+    r.init.assign(init, init + n);
+    r.tol = tol;
+    r.max_iters = max_iters;
+    r.t_submit = s->now();
+    s->queue.push_back(r.id);
+    *req_id = r.id;
+    s->reqs.emplace(r.id, std::move(r));
+    return JAC_OK;
+}
+
+// One round: admit queued requests (first come, first served) while a slot
+// and room in the arena are free, advance every resident grid by one chunk
+// (binary64 and binary32 pools on their own streams, so their launches
+// overlap), read the per-grid binary64 residuals, and retire every grid
+// whose residual fell below its tolerance or that reached its iteration cap.
+int jac_server_step(jac_server* s, jac_server_stats_t* stats)
+{
+    if (!s) return fail(JAC_EINVAL, "null server");
+    cudaSetDevice(s->device);
+    int rc;
+    while (!s->queue.empty() && s->running < s->max_active) {
+        ServeReq& r = s->reqs[s->queue.front()];
+        const int d = r.dtype == JAC_F32 ? 1 : 0;
+        int32_t slot = -1;
+        rc = jac_pool_add(s->pool[d], r.dims, r.bc, &slot);
+        if (rc == JAC_EBUDGET) break;  // wait until a running grid frees its region
+        if (!rc) rc = jac_write_instance(s->pool[d], slot, r.init.data(), r.init.size());
+        s->queue.pop_front();
+        if (rc) {
+            r.state = 3;
+            r.t_done = s->now();
+            s->finished.push_back(r.id);
+            if (slot >= 0) jac_pool_remove(s->pool[d], slot);
+            continue;
+        }
+        r.slot = slot;
+        r.state = 1;
+        r.t_admit = s->now();
+        r.init.clear();
+        r.init.shrink_to_fit();
+        s->running += 1;
+    }
+    bool any[2] = {false, false};
+    for (int d = 0; d < 2; ++d) {
+        jac_ctx* h = s->pool[d];
+        if (h->n_active() == 0) continue;
+        any[d] = true;
+        if ((rc = jac_iterate(h, s->chunk))) return rc;
+        if ((rc = jac_residual_instances_device(h, h->dres_inst))) return rc;
+        CU(cudaMemcpyAsync(s->hres[d], h->dres_inst, sizeof(double) * h->inst.size(), cudaMemcpyDeviceToHost,
+                           h->stream),
+           "copy residuals");
+    }
+    for (int d = 0; d < 2; ++d)
+        if (any[d] && (rc = jac_sync(s->pool[d]))) return rc;
+    int32_t done_now = 0;
+    for (auto& kv : s->reqs) {
+        ServeReq& r = kv.second;
+        if (r.state != 1) continue;
+        const int d = r.dtype == JAC_F32 ? 1 : 0;
+        r.iters += s->chunk;
+        r.residual = s->hres[d][r.slot];
+        s->cell_updates += r.dims[0] * r.dims[1] * r.dims[2] * (int64_t)s->chunk;
+        if (r.residual < r.tol || r.iters >= r.max_iters) {
+            r.result.resize((size_t)(r.dims[0] * r.dims[1] * r.dims[2]));
+            rc = jac_read_instance(s->pool[d], r.slot, r.result.data(), r.result.size());
+            jac_pool_remove(s->pool[d], r.slot);
+            r.state = rc ? 3 : 2;
+            r.t_done = s->now();
+            s->running -= 1;
+            s->finished.push_back(r.id);
+            done_now += 1;
+        }
+    }
+    if (stats) {
+        stats->running = s->running;
+        stats->queued = (int32_t)s->queue.size();
+        stats->finished_now = done_now;
+        stats->cell_updates = s->cell_updates;
+        stats->used_bytes = s->arena.used;
+        stats->budget_bytes = s->arena.capacity;
+    }
+    return JAC_OK;
+}
+
+int jac_server_poll(jac_server* s, jac_request_t* out)
+{
+    if (!s || !out) return fail(JAC_EINVAL, "null argument");
+    if (s->finished.empty()) return JAC_ESTATE;
+    const ServeReq& r = s->reqs[s->finished.front()];
+    s->finished.pop_front();
+    out->id = r.id;
+    out->iterations = r.iters;
+    out->residual = r.residual;
+    out->t_submit = r.t_submit;
+    out->t_admit = r.t_admit;
+    out->t_done = r.t_done;
+    out->status = r.state == 2 ? JAC_OK : JAC_ECUDA;
+    return JAC_OK;
+}
+
+int jac_server_result(jac_server* s, int64_t req_id, double* host_out, size_t n_cells)
+{
+    if (!s) return fail(JAC_EINVAL, "null server");
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end() || it->second.state < 2) return fail(JAC_ESTATE, "request %lld not finished", (long long)req_id);
+    ServeReq& r = it->second;
+    if (host_out) {
+        if (n_cells != r.result.size()) return fail(JAC_EINVAL, "n_cells %zu != %zu", n_cells, r.result.size());
+        memcpy(host_out, r.result.data(), n_cells * sizeof(double));
+    }
+    s->reqs.erase(it);  // the result is handed over once
+    return JAC_OK;
+}
+
+int jac_server_now(jac_server* s, double* seconds)
+{
+    if (!s || !seconds) return fail(JAC_EINVAL, "null argument");
+    *seconds = s->now();
     return JAC_OK;
 }
 

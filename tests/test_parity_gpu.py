@@ -271,3 +271,25 @@ def test_full_size_forms_agree_and_invariants_hold():
         assert np.array_equal(outs[m], outs["persistent"])
     u = outs["persistent"]
     assert u.min() >= 0.0 and u.max() <= 1.0
+
+
+def test_f32_error_against_f64_within_proven_bound():
+    """Binary32 storage and arithmetic against the binary64 correctly rounded
+    mean on the same grid: max|u32 - u64| <= k (27/7 + 1) 2^-24 + 2^-25."""
+    dims, block = (96, 80, 72), (32, 40, 24)
+    u0 = grid(29, dims)
+    k = 300
+    with Jacobi3D(dims, block, dtype="f32", bc=synth.DIRICHLET_X0, mode="persistent") as J:
+        J.write(u0.astype(np.float32))
+        J.iterate(k)
+        u32 = J.read()
+        r32 = J.residual()
+    with Jacobi3D(dims, block, dtype="f64", bc=synth.DIRICHLET_X0, mode="persistent") as K:
+        K.write(u0)
+        K.iterate(k)
+        u64 = K.read()
+        r64 = K.residual()
+    bound = k * (27.0 / 7.0 + 1.0) * 2.0 ** -24 + 2.0 ** -25
+    err = np.max(np.abs(u32 - u64))
+    assert 0 < err <= bound
+    assert abs(r32 - r64) <= 0.05 * r64
