@@ -677,7 +677,8 @@ def run_serve(a, rank, world, local, pg):
     per_shape = {}
     for i, r in enumerate(trace):
         if r.dims not in per_shape:
-            with Jacobi3D(r.dims, (64, 64, 64), dtype="f64", bc=DIRICHLET, mode="unfused", arith="seq") as J:
+            blk = tuple(min(64, v) for v in r.dims)
+            with Jacobi3D(r.dims, blk, dtype="f64", bc=DIRICHLET, mode="unfused", arith="seq") as J:
                 J.write(inits[i])
                 J.iterate(1)
                 J.sync()
