@@ -88,6 +88,62 @@ __device__ __forceinline__ double mean7_seq(double c, double xm, double xp, doub
     return __ddiv_rn(s, 7.0);
 }
 
+// RN(s / 7) in binary32 without a division routine (so without the call its
+// rare slow path makes, which costs registers in a loop). For |s| >= 2^-100
+// one product and one fused multiply-add with a two-word reciprocal of 7
+// (zh = RN(1/7), zl = RN(1/7 - zh); the method of Brisebarre, Muller and
+// Raina, "Accelerating correctly rounded floating-point division when the
+// divisor is known in advance", IEEE Trans. Computers 53(8), 2004). Below
+// that, and for zero, exact integer division in units of 2^-149. Checked
+// bit for bit against the correctly rounded quotient for every finite
+// binary32 value (tests/test_div7f_exhaustive.py).
+JAC_HD inline float div7f(float s)
+{
+    const float zh = 0x1.24924ap-3f;
+    const float zl = -0x1.b6db6ep-28f;
+    if (fabsf(s) >= 0x1p-100f) {
+#if defined(__CUDA_ARCH__)
+        return __fmaf_rn(s, zh, __fmul_rn(s, zl));
+#else
+        return fmaf(s, zh, s * zl);
+#endif
+    }
+    if (s == 0.0f) return s;
+    uint32_t b;
+    memcpy(&b, &s, 4);
+    const uint32_t sign = b & 0x80000000u;
+    const uint32_t e = (b >> 23) & 0xFFu;  // <= 27 here
+    const uint32_t f = b & 0x7FFFFFu;
+    const uint64_t S = e ? ((uint64_t)(f | 0x800000u) << (e - 1)) : (uint64_t)f;  // s / 2^-149, < 2^50
+    uint64_t Q = S / 7u;
+    const uint64_t R = S - 7u * Q;
+    uint32_t out;
+    if (Q < (1ull << 23)) {
+        // subnormal (or the smallest normal after rounding): units of 2^-149,
+        // the fraction R/7 is never exactly one half
+        out = (uint32_t)(Q + (R >= 4u ? 1u : 0u));
+    } else {
+        int L = 0;
+        for (uint64_t t = Q; t; t >>= 1) ++L;  // 24 .. 47
+        const int sh = L - 24;
+        uint64_t mant = Q >> sh;
+        bool up;
+        if (sh == 0) {
+            up = R >= 4u;
+        } else {
+            const bool rbit = (Q >> (sh - 1)) & 1u;
+            const bool sticky = (Q & ((1ull << (sh - 1)) - 1ull)) != 0ull || R != 0u;
+            up = rbit && (sticky || (mant & 1u));
+        }
+        mant += up ? 1u : 0u;
+        out = ((uint32_t)sh << 23) + (uint32_t)mant;  // the implicit bit lifts the exponent to sh + 1
+    }
+    out |= sign;
+    float r;
+    memcpy(&r, &out, 4);
+    return r;
+}
+
 __device__ __forceinline__ float mean7_seq_f32(float c, float xm, float xp, float ym, float yp,
                                                float zm, float zp)
 {
@@ -97,7 +153,7 @@ __device__ __forceinline__ float mean7_seq_f32(float c, float xm, float xp, floa
     s = __fadd_rn(s, yp);
     s = __fadd_rn(s, zm);
     s = __fadd_rn(s, zp);
-    return __fdiv_rn(s, 7.0f);
+    return div7f(s);
 }
 
 // ------------------------------------------------------------------------

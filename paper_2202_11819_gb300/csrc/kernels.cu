@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "arith.cuh"
 #include "jac_common.cuh"
@@ -420,6 +421,131 @@ __host__ __device__ constexpr int smem_bytes()
     return 2 * (kThreads / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
 }
 
+// ---------------------------------------------------------------- lean engine
+// For binary32 (the floating-point rule, cheap arithmetic) the
+// arithmetic is cheap and the kernel must simply keep enough bytes in flight.
+// Each thread owns one column of the tile and walks it along z with no
+// shared memory and no barrier: its own values stream from DRAM DC planes
+// ahead; its four x/y neighbours are read from short streams DN planes ahead,
+// which hit L1 (their lines were requested DC - DN planes earlier by the
+// neighbouring column's own stream); the z neighbours are carried in
+// registers. Neighbours across a block face come from the neighbouring block
+// (or are the Dirichlet constant, stride 0).
+template <typename T>
+constexpr int kLeanDC = 11;
+constexpr int kLeanDN = 1;
+
+template <typename T, bool PULL, bool CG, int TW>
+__device__ __forceinline__ void lean_tile(T* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p,
+                                          int x0, int y0, int z0, int z1)
+{
+    constexpr int DC = kLeanDC<T>, DN = kLeanDN;
+    const BlockDesc& d = desc[b];
+    const int tid = threadIdx.x;
+    const int x = x0 + tid % TW, y = y0 + tid / TW;
+    if (x >= d.ext[0] || y >= d.ext[1]) return;
+    const int bz = d.ext[2];
+    const int64_t plane = d.plane;
+    const T* pc = pool + cell_index<T>(d, p, x, y, 0);
+    const int32_t plane32 = (int32_t)plane;
+    const Src<T> s0 = xy_source<T, PULL>(pool, desc, d, p, x - 1, y);
+    const Src<T> s1 = xy_source<T, PULL>(pool, desc, d, p, x + 1, y);
+    const Src<T> s2 = xy_source<T, PULL>(pool, desc, d, p, x, y - 1);
+    const Src<T> s3 = xy_source<T, PULL>(pool, desc, d, p, x, y + 1);
+    // plane strides fit 32 bits (at most (256 + 2) x 512 elements)
+    struct {
+        const T* p;
+        int32_t stride;
+    } sxm{s0.p, (int32_t)s0.stride}, sxp{s1.p, (int32_t)s1.stride}, sym{s2.p, (int32_t)s2.stride},
+        syp{s3.p, (int32_t)s3.stride};
+    const T* zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : pc + z1 * plane;
+    const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : pc + (z0 - 1) * plane;
+    T* out = pool + cell_index<T>(d, p ^ 1, x, y, 0);
+    // Ring slots are fixed registers: the z loop is unrolled by the ring length
+    // R so every slot index is a compile-time constant (moving a register whose
+    // load is still in flight would wait for that load and undo the prefetch).
+    // Own column: plane q sits in slot (q - z0 - 1) % R; neighbours: plane q
+    // in slot (q - z0) % RN, with RN dividing R. Every stream walks with a
+    // running pointer; chunks whose loads all fall inside [z0, z1) run without
+    // range checks.
+    constexpr int R = DC + 1, RN = DN + 1;
+    static_assert(R % RN == 0, "neighbour ring must divide the column ring");
+    T rc[R], rxm[RN], rxp[RN], rym[RN], ryp[RN];
+#pragma unroll
+    for (int i = 0; i < DC; ++i) {
+        const int q = z0 + 1 + i;
+        rc[i] = q < z1 ? ld<T, CG>(pc + q * plane32) : (q == z1 ? ld<T, CG>(zhi) : T(0));
+    }
+    const T* po = pc + (z0 + 1 + DC) * plane32;  // own stream: plane k + 1 + DC
+    const T* pxm = sxm.p + z0 * sxm.stride;       // neighbour streams: plane k + DN
+    const T* pxp = sxp.p + z0 * sxp.stride;
+    const T* pym = sym.p + z0 * sym.stride;
+    const T* pyp = syp.p + z0 * syp.stride;
+#pragma unroll
+    for (int i = 0; i < DN; ++i) {
+        const bool in = z0 + i < z1;
+        rxm[i] = in ? ld<T, CG>(pxm) : T(0);
+        rxp[i] = in ? ld<T, CG>(pxp) : T(0);
+        rym[i] = in ? ld<T, CG>(pym) : T(0);
+        ryp[i] = in ? ld<T, CG>(pyp) : T(0);
+        pxm += sxm.stride;
+        pxp += sxp.stride;
+        pym += sym.stride;
+        pyp += syp.stride;
+    }
+    T zm = ld<T, CG>(zlo);
+    T c = ld<T, CG>(pc + z0 * plane32);
+    T* po_out = out + z0 * plane32;
+    auto step = [&](auto full, int j, int k) {
+        constexpr bool FULL = decltype(full)::value;
+        const int sn = (j + R - 1) % R, sl = (j + DN) % RN, su = j % RN;
+        if (FULL) {
+            rc[sn] = ld<T, CG>(po);
+            rxm[sl] = ld<T, CG>(pxm);
+            rxp[sl] = ld<T, CG>(pxp);
+            rym[sl] = ld<T, CG>(pym);
+            ryp[sl] = ld<T, CG>(pyp);
+        } else {
+            const int q = k + 1 + DC;
+            rc[sn] = q < z1 ? ld<T, CG>(po) : (q == z1 ? ld<T, CG>(zhi) : T(0));
+            if (k + DN < z1) {
+                rxm[sl] = ld<T, CG>(pxm);
+                rxp[sl] = ld<T, CG>(pxp);
+                rym[sl] = ld<T, CG>(pym);
+                ryp[sl] = ld<T, CG>(pyp);
+            }
+        }
+        po += plane32;
+        pxm += sxm.stride;
+        pxp += sxp.stride;
+        pym += sym.stride;
+        pyp += syp.stride;
+        const T zp = rc[j];
+        *po_out = mean7<T, 0>(c, rxm[su], rxp[su], rym[su], ryp[su], zm, zp);
+        po_out += plane32;
+        zm = c;
+        c = zp;
+    };
+    int kb = z0;
+    // full chunks: the last own load of the chunk, plane kb + R + DC, is < z1
+    for (; kb + R + DC < z1; kb += R) {
+#pragma unroll
+        for (int j = 0; j < R; ++j) step(std::true_type{}, j, kb + j);
+    }
+    for (; kb < z1; kb += R) {
+#pragma unroll
+        for (int j = 0; j < R; ++j)
+            if (kb + j < z1) step(std::false_type{}, j, kb + j);
+    }
+}
+
+template <typename T, int TW>
+__global__ void __launch_bounds__(kThreads, 2) k_fused_lean(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
+{
+    const TileUnit u = units[blockIdx.x];
+    lean_tile<T, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
+}
+
 // prefetch depth: binary32 tiles are bandwidth-bound and need more bytes in
 // flight; binary64 tiles are bound by the arithmetic
 template <typename T>
@@ -476,7 +602,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // overwrites (buffer p^1 held iteration t-1). The seven counters are polled
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
-template <typename T, int OP, int TW>
+template <typename T, int OP, int TW, bool LEAN>
 __global__ void __launch_bounds__(kThreads, 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
@@ -527,8 +653,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (s_stop) break;
         // take the next unit now; its index is read after this one finishes
         if (tid == 0) s_next = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
-        tile_engine<T, OP, true, true, kDepth<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0,
-                                                      u.z1, (typename Elem<T, OP>::type*)sm, &slow);
+        if constexpr (LEAN) {
+            // plain (L1-cached) loads are safe here: the acquire and the
+            // barrier above order them after the neighbours' releases
+            lean_tile<T, true, false, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
+        } else {
+            tile_engine<T, OP, true, true, kDepth<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
+                                                          u.z0, u.z1, (typename Elem<T, OP>::type*)sm, &slow);
+        }
         __syncthreads();
         if (tid == 0 && !(u.block == hold_block && t >= hold_after)) {
             __threadfence();
@@ -782,7 +914,10 @@ static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
             return;
         }
     }
-    k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+    if constexpr (sizeof(T) == 4)
+        k_fused_lean<T, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.units, p);
+    else
+        k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
 }
 
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
@@ -795,8 +930,9 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
 template <int TW>
 static const void* persistent_fn(int dtype_f32, int arith)
 {
-    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, TW>;
-    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, TW> : (const void*)k_persistent<double, OP_SEQ, TW>;
+    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, TW, true>;
+    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, TW, false>
+                      : (const void*)k_persistent<double, OP_SEQ, TW, false>;
 }
 
 const void* persistent_kernel(int dtype_f32, int arith, int tw)
@@ -813,13 +949,13 @@ static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith
 {
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_persistent<T, OP_EXACT, TW><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
+            k_persistent<T, OP_EXACT, TW, false><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
                                                                     q.p0, q.n_iters, q.done, q.work, q.status,
                                                                     q.wait_ns, q.hold_block, q.hold_after);
             return;
         }
     }
-    k_persistent<T, OP_SEQ, TW><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
                                                           q.n_iters, q.done, q.work, q.status, q.wait_ns,
                                                           q.hold_block, q.hold_after);
 }
