@@ -65,12 +65,12 @@ JAC_HD inline int clz64(uint64_t x)  // x != 0
 #endif
 }
 
-JAC_HD inline int clz32(uint32_t x)  // x != 0
+JAC_HD inline int clz32(uint32_t x)  // 32 for x == 0
 {
 #if defined(__CUDA_ARCH__)
     return __clz((int)x);
 #else
-    return __builtin_clz(x);
+    return x ? __builtin_clz(x) : 32;
 #endif
 }
 
@@ -454,8 +454,8 @@ namespace frame {
 
 constexpr uint32_t kMarker = 1u << 29;  // w2 of an unrepresentable value (2^93)
 
-struct W96 {
-    uint32_t w0, w1, w2, w3;  // w3 is padding (16-byte slots in shared memory)
+struct __align__(16) W96 {
+    uint32_t w0, w1, w2, w3;  // w3 is padding (one 16-byte load per value)
 };
 
 JAC_HD inline uint32_t fsl(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) << s) >> 32, 0 <= s <= 31
@@ -473,6 +473,24 @@ JAC_HD inline uint32_t fsr(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) >> s) &
     return __funnelshift_r(lo, hi, s);
 #else
     return (uint32_t)((((uint64_t)hi << 32) | lo) >> s);
+#endif
+}
+
+JAC_HD inline uint32_t fsrc(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) >> min(s, 32)) & 0xffffffff, s >= 0
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_rc(lo, hi, s);
+#else
+    return (uint32_t)((((uint64_t)hi << 32) | lo) >> (s < 32 ? s : 32));
+#endif
+}
+
+JAC_HD inline uint32_t shlc(uint32_t x, int s)  // x << min(s, 32) (0 for s >= 32), s >= 0
+{
+#if defined(__CUDA_ARCH__)
+    return __funnelshift_lc(0u, x, s);
+#else
+    return s < 32 ? x << s : 0u;
 #endif
 }
 
@@ -532,50 +550,84 @@ JAC_HD inline double u64_to_double_rn(uint64_t q)
 #endif
 }
 
-// RN((c + xm + xp + ym + yp + zm + zp) / 7) from frame values. Returns false
-// when the exact per-cell path must be taken (a marker, or a subnormal
-// result).
+// S = a + b + c + d + e + f + g over 96 bits, in one carry chain.
+JAC_HD inline void sum7(const W96& a, const W96& b, const W96& c, const W96& d, const W96& e, const W96& f,
+                        const W96& g, uint32_t& s0, uint32_t& s1, uint32_t& s2)
+{
+#if defined(__CUDA_ARCH__)
+    asm("add.cc.u32 %0, %3, %6;\n\t"
+        "addc.cc.u32 %1, %4, %7;\n\t"
+        "addc.u32 %2, %5, %8;\n\t"
+        "add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.u32 %2, %2, %11;\n\t"
+        "add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.u32 %2, %2, %14;\n\t"
+        "add.cc.u32 %0, %0, %15;\n\t"
+        "addc.cc.u32 %1, %1, %16;\n\t"
+        "addc.u32 %2, %2, %17;\n\t"
+        "add.cc.u32 %0, %0, %18;\n\t"
+        "addc.cc.u32 %1, %1, %19;\n\t"
+        "addc.u32 %2, %2, %20;\n\t"
+        "add.cc.u32 %0, %0, %21;\n\t"
+        "addc.cc.u32 %1, %1, %22;\n\t"
+        "addc.u32 %2, %2, %23;"
+        : "=&r"(s0), "=&r"(s1), "=&r"(s2)
+        : "r"(a.w0), "r"(a.w1), "r"(a.w2), "r"(b.w0), "r"(b.w1), "r"(b.w2), "r"(c.w0), "r"(c.w1), "r"(c.w2),
+          "r"(d.w0), "r"(d.w1), "r"(d.w2), "r"(e.w0), "r"(e.w1), "r"(e.w2), "r"(f.w0), "r"(f.w1), "r"(f.w2),
+          "r"(g.w0), "r"(g.w1), "r"(g.w2));
+#else
+    uint64_t lo = 0;
+    uint32_t hi = 0;
+    const W96* v[7] = {&a, &b, &c, &d, &e, &f, &g};
+    for (const W96* w : v) {
+        const uint64_t x = ((uint64_t)w->w1 << 32) | w->w0;
+        lo += x;
+        hi += w->w2 + (lo < x ? 1u : 0u);
+    }
+    s0 = (uint32_t)lo;
+    s1 = (uint32_t)(lo >> 32);
+    s2 = hi;
+#endif
+}
+
+// RN((c + xm + xp + ym + yp + zm + zp) / 7) from frame values, without
+// branches. Returns false when the exact per-cell path must be taken (a
+// marker, or a subnormal result).
+//   S (96 bits, below 2^87 unless a marker is present) is normalised so its
+//   top bit is bit 63 of N (a sum below 2^64 is first moved up 32 bits; a
+//   nonzero in-frame value is at least 2^52, so S is then zero or has a
+//   nonzero top word); the bits shifted out become a sticky flag.
+//   Q = floor(N / 7) by multiply-high with the magic 2^66/7 and the usual
+//   add-back, Q in [2^60.2, 2^61.2). Q has 61 or 62 bits and is rounded to
+//   53: its last bit lies below the rounding position, so OR-ing the sticky
+//   information (nonzero remainder or dropped bits) into it lets one correctly
+//   rounded integer -> binary64 conversion round the exact quotient.
+//   S/7 = (Q + fraction) * 2^(L-64) units of 2^(eref-1106): that scale is
+//   added to the exponent field of the converted value.
 JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& ym, const W96& yp, const W96& zm,
                          const W96& zp, int eref, double& out)
 {
-    W96 S = add(add(add(c, xm), add(xp, ym)), add(add(yp, zm), zp));
-    if (S.w2 >= kMarker) return false;
-    uint64_t N;
-    bool st0;
-    int L;
-    if (S.w2 != 0u) {
-        const int r = 32 - clz32(S.w2);  // 1 .. 22
-        N = ((uint64_t)fsr(S.w1, S.w2, r) << 32) | fsr(S.w0, S.w1, r);
-        st0 = (S.w0 << (32 - r)) != 0u;
-        L = 64 + r;
-    } else {
-        const uint64_t s64 = ((uint64_t)S.w1 << 32) | S.w0;
-        if (s64 == 0ull) {
-            out = 0.0;
-            return true;
-        }
-        const int lz = clz64(s64);
-        N = s64 << lz;
-        st0 = false;
-        L = 64 - lz;
-    }
-    // N in [2^63, 2^64): Q = N / 7 (multiply-high by the magic 2^66/7 with
-    // the usual add-back), Q in [2^60.2, 2^61.2)
-    const uint64_t t = umulhi64(N, 0x2492492492492493ull);
-    const uint64_t Q = (((N - t) >> 1) + t) >> 2;
-    const uint64_t R = N - Q * 7ull;
-    // Q has 61 or 62 bits and is rounded to 53: its last bit lies below the
-    // rounding position, so OR-ing the sticky information (nonzero remainder
-    // or bits dropped from S) into it lets one correctly rounded conversion
-    // round the exact quotient Q + fraction.
-    const uint64_t qj = Q | ((R != 0ull || st0) ? 1ull : 0ull);
-    const double dq = u64_to_double_rn(qj);
-    // S/7 = (Q + fraction) * 2^(L-64) units of 2^(eref-1106): add that scale
-    // to the exponent field of dq (a normal number near 2^61)
-    const int biased = (int)(dbits(dq) >> 52) + L - 64 + eref - 1106;
-    if (biased < 1) return false;
-    out = bitsd(dbits(dq) + ((uint64_t)(int64_t)(L - 64 + eref - 1106) << 52));
-    return true;
+    uint32_t s0, s1, s2;
+    sum7(c, xm, xp, ym, yp, zm, zp, s0, s1, s2);
+    const bool marker = s2 >= kMarker;
+    const bool z2 = s2 == 0u;
+    const uint32_t t2 = z2 ? s1 : s2, t1 = z2 ? s0 : s1, t0 = z2 ? 0u : s0;
+    const bool zero = t2 == 0u;                 // S == 0
+    const int r = 32 - clz32(t2);               // 1 .. 32 (0 when S == 0)
+    const uint64_t Nn = ((uint64_t)fsrc(t1, t2, r) << 32) | fsrc(t0, t1, r);
+    const bool st0 = shlc(t0, 32 - r) != 0u;
+    const int L = r + (z2 ? 32 : 64);
+    const uint64_t t = umulhi64(Nn, 0x2492492492492493ull);
+    const uint64_t Q = (((Nn - t) >> 1) + t) >> 2;
+    const uint32_t R = (uint32_t)Nn - 7u * (uint32_t)Q;  // the remainder (< 7) from the low words
+    const uint64_t qj = Q | ((R != 0u || st0) ? 1ull : 0ull);
+    const uint64_t qb = dbits(u64_to_double_rn(qj));
+    const int adj = L - 64 + eref - 1106;
+    const int biased = (int)(qb >> 52) + adj;
+    out = zero ? 0.0 : bitsd(qb + ((uint64_t)(int64_t)adj << 52));
+    return !marker && (zero || biased >= 1);
 }
 
 // RN(xm + xp + ym + yp + zm + zp - 6c) from frame values. Returns false for

@@ -209,160 +209,120 @@ struct SlowList {
     uint32_t cell[kSlowMax];  // (k << 9) | tid
 };
 
-// The z-marching engine over one tile (x0 .. x0+TW-1, y0 .. y0+512/TW-1,
-// planes z0 .. z1-1) of block b, reading buffer p.
-//   OP_SEQ / OP_EXACT: writes the interior of buffer p^1;
-//   OP_RES:           returns this thread's sum of L^2 (thread 0 also adds the
-//                     cells recomputed exactly, in (k, tid) order).
-// Every shared slot of the tile plane (the interior plus its halo ring) is a
-// stream along z (pointer + plane stride, or a constant): own columns, halo
-// cells that fall inside the tile where it overhangs the block edge, and one
-// extra ring slot for each of the first 2 (TW + 512/TW) threads. Values are
-// loaded D planes ahead into registers, converted once (to the grid frame for
-// the exact ops), stored in a double-buffered shared plane (one barrier per
-// plane), and the z neighbours are carried in registers.
-template <typename T, int OP, bool PULL, bool CG, int D, int TW>
-__device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
-                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
-                              typename Elem<T, OP>::type* sm, SlowList* slow)
+template <typename T, int OP, int TW>
+__host__ __device__ constexpr int smem_bytes()
 {
-    using E = typename Elem<T, OP>::type;
-    constexpr int kTX = TW, kTY = kThreads / TW, kTW = TW, kSW = TW + 2;
-    const BlockDesc& d = desc[b];
-    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int eref = (OP == OP_SEQ) ? 0 : frame_e[d.inst] + 1;
-    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
-    const int x = x0 + tx, y = y0 + ty;
+    return 2 * (kThreads / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
+}
+
+// Extra ring slots of a tile (the halo ring around the TW x 512/TW interior).
+template <int TW>
+__host__ __device__ constexpr int ring_extra()
+{
+    return 2 * TW + 2 * (kThreads / TW);
+}
+
+// Shared memory of the engine: the double-buffered exchange plane, then the
+// prefetch rings (RD planes of one value per thread, and RD planes of the halo
+// ring slots), all in dynamic shared memory.
+template <typename T, int OP, int TW, int RD>
+__host__ __device__ constexpr int engine_bytes()
+{
+    return smem_bytes<T, OP, TW>() + RD * (kThreads + ring_extra<TW>()) * (int)sizeof(T);
+}
+
+// Planes in flight per stream: binary64 values are 8 bytes and the exact
+// arithmetic hides latency itself; binary32 needs more.
+template <typename T>
+constexpr int kRing = sizeof(T) == 8 ? 8 : 12;
+constexpr int kRingRes = 6;
+
+extern __shared__ __align__(16) unsigned char jac_dyn_sm[];
+
+// Asynchronous global -> shared copies of one value (cp.async, cached in L1;
+// completion is tracked per thread by commit / wait groups, so a thread that
+// reads only its own copies needs no barrier).
+template <int N>
+__device__ __forceinline__ void cp_async(void* dst, const void* src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(N) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// One halo-ring slot of the tile plane per thread for tid < 2 (TW + TY): row
+// y0-1, row y0+TY, column x0-1, column x0+TW (only the slots some interior
+// cell reads). er < 0: this thread has none; else (er, ec) is the slot in the
+// shared plane and p + k * stride the value of plane k (z0 based).
+template <typename T>
+struct HaloSlot {
+    int er, ec;
+    const T* p;
+    int64_t stride;
+};
+
+template <typename T, bool PULL, int TW>
+__device__ __forceinline__ HaloSlot<T> halo_slot(const T* pool, const BlockDesc* desc, const BlockDesc& d, int p,
+                                                 int x0, int y0, int z0, int tid)
+{
+    constexpr int kTW = TW, kTY = kThreads / TW;
+    const int bx = d.ext[0], by = d.ext[1];
+    HaloSlot<T> h{-1, 0, pool, 0};
+    if (tid >= ring_extra<TW>()) return h;
+    int hx, hy;
+    if (tid < kTW) {
+        h.er = 0;
+        h.ec = tid + 1;
+        hx = x0 + tid;
+        hy = y0 - 1;
+        if (hx >= bx) h.er = -1;
+    } else if (tid < 2 * kTW) {
+        const int c = tid - kTW;
+        h.er = kTY + 1;
+        h.ec = c + 1;
+        hx = x0 + c;
+        hy = y0 + kTY;
+        if (hx >= bx || hy > by) h.er = -1;
+    } else if (tid < 2 * kTW + kTY) {
+        const int r = tid - 2 * kTW;
+        h.er = r + 1;
+        h.ec = 0;
+        hx = x0 - 1;
+        hy = y0 + r;
+        if (hy >= by) h.er = -1;
+    } else {
+        const int r = tid - 2 * kTW - kTY;
+        h.er = r + 1;
+        h.ec = kTW + 1;
+        hx = x0 + kTW;
+        hy = y0 + r;
+        if (hy >= by || hx > bx) h.er = -1;
+    }
+    if (h.er >= 0) {
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, hx, hy);
+        h.p = s.p + z0 * s.stride;
+        h.stride = s.stride;
+    }
+    return h;
+}
+
+// After a tile's z loop: recompute the cells recorded in the slow list (or
+// the whole tile when the list overflowed) with the exact per-cell routines.
+template <typename T, int OP, bool PULL, bool CG, int TW>
+__device__ __forceinline__ double slow_cells(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                                             const BlockDesc& d, int b, int p, int x0, int y0, int z0, int z1,
+                                             bool interior, int x, int y, int64_t oidx, double acc, SlowList* slow)
+{
+    constexpr int kTX = TW;
+    const int tid = threadIdx.x;
     const int64_t plane = d.plane;
-    if (OP != OP_SEQ && tid == 0) slow->n = 0;
-
-    // own column: 0 unused, 1 interior cell, 2 halo cell inside the tile
-    int kind = 0;
-    const T* sp = pool;
-    int64_t ss = 0;
-    const T* zhi = pool;  // the value above the last plane of the range
-    int64_t oidx = 0;
-    E wzm{}, wc{};
-    T ring[D + 1];  // interior: planes k+1 .. k+1+D; halo: planes k .. k+D
-#pragma unroll
-    for (int i = 0; i <= D; ++i) ring[i] = T(0);
-    if (x < bx && y < by) {
-        kind = 1;
-        sp = pool + cell_index<T>(d, p, x, y, 0);
-        ss = plane;
-        zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : sp + z1 * plane;
-        oidx = cell_index<T>(d, p ^ 1, x, y, 0);
-        const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : sp + (z0 - 1) * plane;
-        wzm = conv<T, OP>(ldv<T, CG>(zlo), eref);
-        wc = conv<T, OP>(ldv<T, CG>(sp + z0 * plane), eref);
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            const int q = z0 + 1 + i;
-            ring[i] = q < z1 ? ldv<T, CG>(sp + q * ss) : (q == z1 ? ldv<T, CG>(zhi) : T(0));
-        }
-    } else if ((x == bx && y < by) || (y == by && x < bx)) {
-        kind = 2;
-        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
-        sp = s.p;
-        ss = s.stride;
-#pragma unroll
-        for (int i = 0; i < D; ++i) ring[i] = z0 + i < z1 ? ldv<T, CG>(sp + (z0 + i) * ss) : T(0);
-    }
-    // one ring slot per thread for tid < 2 (TW + TY): row y0-1, row y0+TY,
-    // column x0-1, column x0+TW (only the slots some interior cell reads)
-    int er = -1, ec = 0;
-    const T* ep = pool;
-    int64_t es = 0;
-    T ering[D + 1];  // planes k .. k+D
-#pragma unroll
-    for (int i = 0; i <= D; ++i) ering[i] = T(0);
-    if (tid < 2 * kTW + 2 * kTY) {
-        int hx, hy;
-        if (tid < kTW) {
-            er = 0;
-            ec = tid + 1;
-            hx = x0 + tid;
-            hy = y0 - 1;
-            if (hx >= bx) er = -1;
-        } else if (tid < 2 * kTW) {
-            const int c = tid - kTW;
-            er = kTY + 1;
-            ec = c + 1;
-            hx = x0 + c;
-            hy = y0 + kTY;
-            if (hx >= bx || hy > by) er = -1;
-        } else if (tid < 2 * kTW + kTY) {
-            const int r = tid - 2 * kTW;
-            er = r + 1;
-            ec = 0;
-            hx = x0 - 1;
-            hy = y0 + r;
-            if (hy >= by) er = -1;
-        } else {
-            const int r = tid - 2 * kTW - kTY;
-            er = r + 1;
-            ec = kTW + 1;
-            hx = x0 + kTW;
-            hy = y0 + r;
-            if (hy >= by || hx > bx) er = -1;
-        }
-        if (er >= 0) {
-            const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, hx, hy);
-            ep = s.p;
-            es = s.stride;
-#pragma unroll
-            for (int i = 0; i < D; ++i) ering[i] = z0 + i < z1 ? ldv<T, CG>(ep + (z0 + i) * es) : T(0);
-        }
-    }
-    if (OP != OP_SEQ) __syncthreads();  // slow->n = 0 visible before any append
-
-    double acc = 0.0;
-#pragma unroll 2
-    for (int k = z0; k < z1; ++k) {
-        E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
-        // issue the loads D planes ahead
-        if (kind == 1) {
-            const int q = k + 1 + D;
-            ring[D] = q < z1 ? ldv<T, CG>(sp + q * ss) : (q == z1 ? ldv<T, CG>(zhi) : T(0));
-        } else if (kind == 2) {
-            ring[D] = k + D < z1 ? ldv<T, CG>(sp + (k + D) * ss) : T(0);
-        }
-        if (er >= 0) ering[D] = k + D < z1 ? ldv<T, CG>(ep + (k + D) * es) : T(0);
-        // this plane's shared slots
-        E* slot = buf + (ty + 1) * kSW + tx + 1;
-        if (kind == 1) *slot = wc;
-        else if (kind == 2) *slot = conv<T, OP>(ring[0], eref);
-        if (er >= 0) buf[er * kSW + ec] = conv<T, OP>(ering[0], eref);
-        __syncthreads();
-        if (kind == 1) {
-            const E wzp = conv<T, OP>(ring[0], eref);
-            const int sc = (ty + 1) * kSW + tx + 1;
-            if constexpr (OP == OP_SEQ) {
-                pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
-            } else {
-                double o;
-                bool ok;
-                if constexpr (OP == OP_EXACT) {
-                    ok = frame::mean7(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
-                    if (ok) pool[oidx + k * plane] = (T)o;
-                } else {
-                    ok = frame::laplacian(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
-                    if (ok) acc = fma(o, o, acc);
-                }
-                if (!ok) {
-                    const int i = atomicAdd(&slow->n, 1);
-                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
-                }
-            }
-            wzm = wc;
-            wc = wzp;
-        }
-#pragma unroll
-        for (int i = 0; i < D; ++i) {
-            ring[i] = ring[i + 1];
-            ering[i] = ering[i + 1];
-        }
-    }
     if constexpr (OP != OP_SEQ) {
         __syncthreads();
         const int n = slow->n;
@@ -398,12 +358,12 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
                 // more cells outside the frame than the list holds: redo the
                 // whole tile with the exact per-cell routines
                 if constexpr (OP == OP_EXACT) {
-                    if (kind == 1)
+                    if (interior)
                         for (int kk = z0; kk < z1; ++kk)
                             pool[oidx + kk * plane] = (T)exact_cell<T, PULL, CG, false>(pool, desc, b, p, x, y, kk);
                 } else {
                     acc = 0.0;
-                    if (kind == 1)
+                    if (interior)
                         for (int kk = z0; kk < z1; ++kk) {
                             const double L = exact_cell<T, PULL, CG, true>(pool, desc, b, p, x, y, kk);
                             acc = fma(L, L, acc);
@@ -415,10 +375,286 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     return acc;
 }
 
-template <typename T, int OP, int TW>
-__host__ __device__ constexpr int smem_bytes()
+// The z-marching engine over one tile (x0 .. x0+TW-1, y0 .. y0+512/TW-1,
+// planes z0 .. z1-1) of block b, reading buffer p.
+//   OP_SEQ / OP_EXACT: writes the interior of buffer p^1;
+//   OP_RES:           returns this thread's sum of L^2 (thread 0 also adds the
+//                     cells recomputed exactly, in (k, tid) order).
+// Every shared slot of the tile plane (the interior plus its halo ring) is a
+// stream along z (pointer + plane stride, or a constant): own columns, halo
+// cells that fall inside the tile where it overhangs the block edge, and one
+// extra ring slot for each of the first 2 (TW + 512/TW) threads. Each stream
+// is copied RD - 1 planes ahead into a per-thread ring in shared memory
+// (cp.async: the data in flight holds no registers and the loop needs no
+// register rotation); each value is converted once (to the grid frame for
+// the exact ops), stored in a double-buffered shared plane (one barrier per
+// plane), and the z neighbours are carried in registers.
+template <typename T, int OP, bool PULL, bool CG, int RD, int TW>
+__device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
+                              unsigned char* smraw, SlowList* slow)
 {
-    return 2 * (kThreads / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
+    using E = typename Elem<T, OP>::type;
+    constexpr int kTX = TW, kTY = kThreads / TW, kTW = TW, kSW = TW + 2, kEr = ring_extra<TW>();
+    static_assert(RD >= 2, "ring depth");
+    E* sm = (E*)smraw;
+    T* rc = (T*)(smraw + smem_bytes<T, OP, TW>());  // [RD][kThreads]
+    T* re = rc + RD * kThreads;                      // [RD][kEr]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int eref = (OP == OP_SEQ) ? 0 : frame_e[d.inst] + 1;
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int64_t plane = d.plane;
+    if (OP != OP_SEQ && tid == 0) slow->n = 0;
+
+    // own column: 0 unused, 1 interior cell, 2 halo cell inside the tile.
+    // The value consumed at iteration k is at sp + (k - z0) * ss: kind 1 the
+    // plane above (plane k + 1, and zhi for the last plane), kind 2 plane k.
+    int kind = 0;
+    const T* sp = pool;
+    int64_t ss = 0;
+    const T* zhi = pool;  // the value above the last plane of the range
+    int64_t oidx = 0;
+    E wzm{}, wc{};
+    if (x < bx && y < by) {
+        kind = 1;
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        ss = plane;
+        sp = col + (z0 + 1) * plane;
+        zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane;
+        oidx = cell_index<T>(d, p ^ 1, x, y, 0);
+        const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
+        wzm = conv<T, OP>(ldv<T, CG>(zlo), eref);
+        wc = conv<T, OP>(ldv<T, CG>(col + z0 * plane), eref);
+    } else if ((x == bx && y < by) || (y == by && x < bx)) {
+        kind = 2;
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
+        sp = s.p + z0 * s.stride;
+        ss = s.stride;
+    }
+    const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid);
+    const int er = hs.er, ec = hs.ec;
+    const T* ep = hs.p;
+    const int64_t es = hs.stride;
+    T* const myc = rc + tid;                     // ring slot s: myc[s * kThreads]
+    T* const mye = re + (tid < kEr ? tid : 0);   // ring slot s: mye[s * kEr]
+    int next = z0;                               // the next iteration to copy
+    auto issue = [&](int s) {
+        if (next < z1) {
+            if (kind == 1) cp_async<sizeof(T)>(myc + s * kThreads, next + 1 == z1 ? zhi : sp);
+            else if (kind == 2) cp_async<sizeof(T)>(myc + s * kThreads, sp);
+            if (er >= 0) cp_async<sizeof(T)>(mye + s * kEr, ep);
+        }
+        cp_async_commit();  // one group per iteration, empty past the range
+        sp += ss;
+        ep += es;
+        ++next;
+    };
+#pragma unroll
+    for (int i = 0; i < RD - 1; ++i) issue(i);
+    if (OP != OP_SEQ) __syncthreads();  // slow->n = 0 visible before any append
+
+    double acc = 0.0;
+    int s = 0;  // ring slot of iteration k; iteration k + RD - 1 goes to s - 1
+#pragma unroll 2
+    for (int k = z0; k < z1; ++k) {
+        issue(s == 0 ? RD - 1 : s - 1);
+        cp_async_wait<RD - 1>();  // this thread's copies for iteration k have landed
+        E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
+        E* slot = buf + (ty + 1) * kSW + tx + 1;
+        if (kind == 1) *slot = wc;
+        else if (kind == 2) *slot = conv<T, OP>(myc[s * kThreads], eref);
+        if (er >= 0) buf[er * kSW + ec] = conv<T, OP>(mye[s * kEr], eref);
+        __syncthreads();
+        if (kind == 1) {
+            const E wzp = conv<T, OP>(myc[s * kThreads], eref);
+            const int sc = (ty + 1) * kSW + tx + 1;
+            if constexpr (OP == OP_SEQ) {
+                pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
+            } else {
+                double o;
+                bool ok;
+                if constexpr (OP == OP_EXACT) {
+                    ok = frame::mean7(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
+                    if (ok) pool[oidx + k * plane] = (T)o;
+                } else {
+                    ok = frame::laplacian(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
+                    if (ok) acc = fma(o, o, acc);
+                }
+                if (!ok) {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
+                }
+            }
+            wzm = wc;
+            wc = wzp;
+        }
+        s = s == RD - 1 ? 0 : s + 1;
+    }
+    cp_async_wait<0>();  // only empty groups remain; the ring is free for the next tile
+    return slow_cells<T, OP, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc, slow);
+}
+
+// The engine above for the exact mean, two planes per step: each thread
+// computes cells (k, k+1) of its column between one pair of barriers, so the
+// per-plane bookkeeping (copies, waits, barrier, addressing) is shared by two
+// cells and the two cells' integer chains interleave. The exchange buffer
+// holds two planes, double-buffered; the ring, its slots and the slow list
+// are those of the single-plane engine (RD even). A range with an odd number
+// of planes ends with a single-plane step.
+template <int TW>
+__host__ __device__ constexpr int pair_smem_bytes()
+{
+    return 4 * ((kThreads / TW + 2) * (TW + 2) + 1) * (int)sizeof(frame::W96);
+}
+
+template <typename T, int TW, int RD>
+__host__ __device__ constexpr int pair_engine_bytes()
+{
+    return pair_smem_bytes<TW>() + RD * (kThreads + ring_extra<TW>()) * (int)sizeof(T);
+}
+
+// cp.async of one 8- or 4-byte value, issued only when `on` (a predicated
+// instruction, no branch).
+template <int N>
+__device__ __forceinline__ void cp_async_if(uint32_t dst, const void* src, bool on)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q cp.async.ca.shared.global [%0], [%1], %3;\n\t}\n" ::"r"(dst),
+        "l"(src), "r"((int)on), "n"(N)
+        : "memory");
+}
+
+template <typename T, bool PULL, bool CG, int RD, int TW>
+__device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                                 const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
+                                 unsigned char* smraw, SlowList* slow)
+{
+    using E = frame::W96;
+    constexpr int kTX = TW, kTY = kThreads / TW, kSW = TW + 2, kEr = ring_extra<TW>();
+    constexpr int kPlane = (kTY + 2) * kSW + 1;  // + one slot written by threads without a halo slot
+    constexpr uint32_t kRowC = kThreads * sizeof(T), kRowE = kEr * sizeof(T);
+    static_assert(RD >= 4 && RD % 2 == 0, "ring depth");
+    E* const sm = (E*)smraw;                                   // [2 buffers][2 planes][kPlane]
+    T* const rc = (T*)(smraw + pair_smem_bytes<TW>());         // [RD][kThreads]
+    T* const re = rc + RD * kThreads;                          // [RD][kEr]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int eref = frame_e[d.inst] + 1;
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int64_t plane = d.plane;
+    if (tid == 0) slow->n = 0;
+
+    // own stream (kind 1: the plane above, planes z0+1 .. z1-1, the value
+    // above the range held in a register; kind 2: a halo cell inside the
+    // tile, planes z0 .. z1-1)
+    const bool k1 = x < bx && y < by;
+    const bool k2 = (x == bx && y < by) || (y == by && x < bx);
+    const T* osrc = pool;
+    int64_t ostr = 0;
+    int olim = z0;  // copies for plane-iterations below olim
+    T zhiv = T(0);
+    T* out = pool;
+    E wzm{}, wc{};
+    if (k1) {
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        osrc = col + (z0 + 1) * plane;
+        ostr = plane;
+        olim = z1 - 1;
+        zhiv = ldv<T, CG>(z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane);
+        out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
+        const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
+        wzm = frame::of((double)ldv<T, CG>(zlo), eref);
+        wc = frame::of((double)ldv<T, CG>(col + z0 * plane), eref);
+    } else if (k2) {
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
+        osrc = s.p + z0 * s.stride;
+        ostr = s.stride;
+        olim = z1;
+    }
+    const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid);
+    const bool hv = hs.er >= 0;
+    const int hslot = hv ? hs.er * kSW + hs.ec : kPlane - 1;
+    const T* hsrc = hs.p;
+    const int64_t hstr = hs.stride;
+    const int hlim = hv ? z1 : z0;
+    const bool halo_warp = (tid & ~31) < kEr;  // warp-uniform
+    const int own = (ty + 1) * kSW + tx + 1;
+    const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + tid);
+    const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(re + (tid < kEr ? tid : 0));
+    int next = z0;  // the next plane-iteration to copy
+    auto copy_pair = [&](int sl) {  // plane-iterations next, next + 1 into slots sl, sl + 1
+        cp_async_if<sizeof(T)>(rc_s + sl * kRowC, osrc, next < olim);
+        cp_async_if<sizeof(T)>(rc_s + (sl + 1) * kRowC, osrc + ostr, next + 1 < olim);
+        cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
+        cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+        cp_async_commit();
+        osrc += 2 * ostr;
+        hsrc += 2 * hstr;
+        next += 2;
+    };
+#pragma unroll
+    for (int i = 0; i < RD - 2; i += 2) copy_pair(i);
+    __syncthreads();  // slow->n = 0 visible before any append
+
+    int s = 0;  // ring slot of plane-iteration k (even)
+    int bsel = 0;
+    auto step = [&](auto two_c, int k) {
+        constexpr bool TWO = decltype(two_c)::value;
+        copy_pair(s == 0 ? RD - 2 : s - 2);
+        cp_async_wait<RD / 2 - 1>();  // this thread's copies for k, k+1 have landed
+        E* const b0 = sm + bsel * (2 * kPlane);
+        E* const b1 = b0 + kPlane;
+        const T v0 = rc[s * kThreads + tid];
+        const T v1 = rc[(s + 1) * kThreads + tid];
+        // kind 1: u1, u2 are planes k+1, k+2 (the last one from the register)
+        const E c0 = frame::of((double)(k1 && k + 1 >= z1 ? zhiv : v0), eref);
+        const E c1 = frame::of((double)(k1 && k + 2 >= z1 ? zhiv : v1), eref);
+        b0[own] = k1 ? wc : c0;
+        if (TWO) b1[own] = k1 ? c0 : c1;
+        if (halo_warp) {
+            b0[hslot] = frame::of((double)re[s * kEr + (tid < kEr ? tid : 0)], eref);
+            if (TWO) b1[hslot] = frame::of((double)re[(s + 1) * kEr + (tid < kEr ? tid : 0)], eref);
+        }
+        __syncthreads();
+        double o0, o1 = 0.0;
+        bool ok0 = frame::mean7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, eref, o0);
+        bool ok1 = true;
+        if (TWO) ok1 = frame::mean7(c0, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], wc, c1, eref, o1);
+        if (k1 && ok0) out[0] = (T)o0;
+        if (TWO && k1 && ok1) out[plane] = (T)o1;
+        if (k1 && !(ok0 && ok1)) {
+            if (!ok0) {
+                const int i = atomicAdd(&slow->n, 1);
+                if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
+            }
+            if (!ok1) {
+                const int i = atomicAdd(&slow->n, 1);
+                if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+            }
+        }
+        out += 2 * plane;
+        wzm = c0;
+        wc = c1;
+        s = s == RD - 2 ? 0 : s + 2;
+        bsel ^= 1;
+    };
+    int k = z0;
+    for (; k + 1 < z1; k += 2) step(std::true_type{}, k);
+    if (k < z1) step(std::false_type{}, k);
+    cp_async_wait<0>();
+    slow_cells<T, OP_EXACT, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y,
+                                          cell_index<T>(d, p ^ 1, x, y, 0), 0.0, slow);
+}
+
+// Dynamic shared memory of the update kernels for op OP.
+template <typename T, int OP, int TW>
+__host__ __device__ constexpr int kernel_bytes()
+{
+    if constexpr (OP == OP_EXACT) return pair_engine_bytes<T, TW, kRing<T>>();
+    else return engine_bytes<T, OP, TW, kRing<T>>();
 }
 
 // ---------------------------------------------------------------- lean engine
@@ -546,31 +782,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_lean(T* pool, const Block
     lean_tile<T, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
 }
 
-// prefetch depth: binary32 tiles are bandwidth-bound and need more bytes in
-// flight; binary64 tiles are bound by the arithmetic
-template <typename T>
-constexpr int kDepth = sizeof(T) == 4 ? 6 : 3;
-
 template <typename T, int OP, int TW>
 __global__ void __launch_bounds__(kThreads, 2) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                                int b, int p)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
-    tile_engine<T, OP, false, false, kDepth<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                    blockIdx.y * (kThreads / TW), 0, desc[b].ext[2],
-                                                    (typename Elem<T, OP>::type*)sm, &slow);
+    if constexpr (OP == OP_EXACT)
+        tile_engine_pair<T, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
+                                                        blockIdx.y * (kThreads / TW), 0, desc[b].ext[2], jac_dyn_sm,
+                                                        &slow);
+    else
+        tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
+                                                       blockIdx.y * (kThreads / TW), 0, desc[b].ext[2], jac_dyn_sm,
+                                                       &slow);
 }
 
 template <typename T, int OP, int TW>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
-    tile_engine<T, OP, true, false, kDepth<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
-                                                   (typename Elem<T, OP>::type*)sm, &slow);
+    if constexpr (OP == OP_EXACT)
+        tile_engine_pair<T, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                       jac_dyn_sm, &slow);
+    else
+        tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                      jac_dyn_sm, &slow);
 }
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -608,7 +846,6 @@ __global__ void __launch_bounds__(kThreads, 2)
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP, TW>()];
     __shared__ SlowList slow;
     __shared__ long long s_next;
     __shared__ int s_stop;
@@ -658,8 +895,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             // barrier above order them after the neighbours' releases
             lean_tile<T, true, false, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
         } else {
-            tile_engine<T, OP, true, true, kDepth<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
-                                                          u.z0, u.z1, (typename Elem<T, OP>::type*)sm, &slow);
+            if constexpr (OP == OP_EXACT)
+                tile_engine_pair<T, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
+                                                              u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+            else
+                tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
+                                                             u.z0, u.z1, jac_dyn_sm, &slow);
         }
         __syncthreads();
         if (tid == 0 && !(u.block == hold_block && t >= hold_after)) {
@@ -676,12 +917,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
                                                           const int32_t* frame_e, const TileUnit* units, int p,
                                                           double* partials)
 {
-    __shared__ __align__(16) unsigned char sm[smem_bytes<T, OP_RES, TW>()];
     __shared__ SlowList slow;
     __shared__ double red[kThreads];
     const TileUnit u = units[blockIdx.x];
-    const double acc = tile_engine<T, OP_RES, true, false, 2, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                  u.x0, u.y0, u.z0, u.z1, (frame::W96*)sm, &slow);
+    const double acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
+                                                                         p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
     const int tid = threadIdx.x;
     red[tid] = acc;
     __syncthreads();
@@ -890,11 +1130,11 @@ static void stencil_block_t(const LaunchArgs& a, int arith, int b, int nx_tiles,
     dim3 grid(nx_tiles, ny_tiles, 1);
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_stencil_block<T, OP_EXACT, TW><<<grid, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
+            k_stencil_block<T, OP_EXACT, TW><<<grid, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
             return;
         }
     }
-    k_stencil_block<T, OP_SEQ, TW><<<grid, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, b, p);
+    k_stencil_block<T, OP_SEQ, TW><<<grid, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
 }
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
@@ -910,14 +1150,14 @@ static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
 {
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_fused_step<T, OP_EXACT, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+            k_fused_step<T, OP_EXACT, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
             return;
         }
     }
     if constexpr (sizeof(T) == 4)
         k_fused_lean<T, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.units, p);
     else
-        k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+        k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
 }
 
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
@@ -944,18 +1184,66 @@ const void* persistent_kernel(int dtype_f32, int arith, int tw)
 
 int persistent_block_threads() { return kThreads; }
 
+template <int TW>
+static int persistent_bytes_t(int dtype_f32, int arith)
+{
+    if (dtype_f32) return 0;
+    return arith == 1 ? kernel_bytes<double, OP_EXACT, TW>()
+                      : kernel_bytes<double, OP_SEQ, TW>();
+}
+
+int persistent_smem_bytes(int dtype_f32, int arith, int tw)
+{
+    int n = 0;
+    JAC_TW_DISPATCH(tw, (n = persistent_bytes_t<TW>(dtype_f32, arith)))
+    return n;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K* kernel, int bytes)
+{
+    return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <int TW>
+static cudaError_t prepare_tw()
+{
+    cudaError_t e = cudaSuccess;
+#define JAC_ALLOW(K, BYTES) \
+    if (e == cudaSuccess) e = allow_smem(K, BYTES)
+    JAC_ALLOW((k_stencil_block<double, OP_EXACT, TW>), (kernel_bytes<double, OP_EXACT, TW>()));
+    JAC_ALLOW((k_stencil_block<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
+    JAC_ALLOW((k_stencil_block<float, OP_SEQ, TW>), (kernel_bytes<float, OP_SEQ, TW>()));
+    JAC_ALLOW((k_fused_step<double, OP_EXACT, TW>), (kernel_bytes<double, OP_EXACT, TW>()));
+    JAC_ALLOW((k_fused_step<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
+    JAC_ALLOW((k_persistent<double, OP_EXACT, TW, false>), (kernel_bytes<double, OP_EXACT, TW>()));
+    JAC_ALLOW((k_persistent<double, OP_SEQ, TW, false>), (kernel_bytes<double, OP_SEQ, TW>()));
+    JAC_ALLOW((k_residual<double, TW>), (engine_bytes<double, OP_RES, TW, kRingRes>()));
+    JAC_ALLOW((k_residual<float, TW>), (engine_bytes<float, OP_RES, TW, kRingRes>()));
+#undef JAC_ALLOW
+    return e;
+}
+
+cudaError_t prepare_kernels()
+{
+    cudaError_t e = prepare_tw<16>();
+    if (e == cudaSuccess) e = prepare_tw<32>();
+    if (e == cudaSuccess) e = prepare_tw<64>();
+    return e;
+}
+
 template <typename T, int TW>
 static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith, int ctas, cudaStream_t s)
 {
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_persistent<T, OP_EXACT, TW, false><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
+            k_persistent<T, OP_EXACT, TW, false><<<ctas, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
                                                                     q.p0, q.n_iters, q.done, q.work, q.status,
                                                                     q.wait_ns, q.hold_block, q.hold_after);
             return;
         }
     }
-    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, 0, s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? 0 : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
                                                           q.n_iters, q.done, q.work, q.status, q.wait_ns,
                                                           q.hold_block, q.hold_after);
 }
@@ -971,10 +1259,10 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
 cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
 {
     if (dtype_f32)
-        JAC_TW_DISPATCH(a.tile_w, (k_residual<float, TW><<<a.nunits, kThreads, 0, s>>>(
+        JAC_TW_DISPATCH(a.tile_w, (k_residual<float, TW><<<a.nunits, kThreads, engine_bytes<float, OP_RES, TW, kRingRes>(), s>>>(
                                       (const float*)a.pool, a.desc, a.frame, a.units, p, partials)))
     else
-        JAC_TW_DISPATCH(a.tile_w, (k_residual<double, TW><<<a.nunits, kThreads, 0, s>>>(
+        JAC_TW_DISPATCH(a.tile_w, (k_residual<double, TW><<<a.nunits, kThreads, engine_bytes<double, OP_RES, TW, kRingRes>(), s>>>(
                                       (const double*)a.pool, a.desc, a.frame, a.units, p, partials)))
     return cudaGetLastError();
 }

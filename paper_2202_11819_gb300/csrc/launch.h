@@ -36,6 +36,11 @@ int engine_threads();
 bool tile_width_supported(int tw);
 int persistent_block_threads();
 const void* persistent_kernel(int dtype_f32, int arith, int tw);
+// dynamic shared memory of one persistent CTA (for occupancy queries)
+int persistent_smem_bytes(int dtype_f32, int arith, int tw);
+// raises the dynamic shared memory limit of every engine kernel on the
+// current device; once per device, before the first launch or capture
+cudaError_t prepare_kernels();
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
                                  int p, cudaStream_t s);

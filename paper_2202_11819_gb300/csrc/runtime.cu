@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "jacobi3d.h"
@@ -805,6 +806,20 @@ int sync_stream(jac_ctx* h)
 }
 
 // Stream, allocator and the fixed-size device tables (per slot and status).
+// Per-device one-time kernel setup (dynamic shared-memory limits).
+static cudaError_t prepare_device(int dev)
+{
+    static std::mutex mu;
+    static std::vector<char> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((size_t)dev < done.size() && done[dev]) return cudaSuccess;
+    const cudaError_t e = prepare_kernels();
+    if (e != cudaSuccess) return e;
+    if ((size_t)dev >= done.size()) done.resize(dev + 1, 0);
+    done[dev] = 1;
+    return cudaSuccess;
+}
+
 int open_ctx(jac_ctx* h, void* stream)
 {
     h->alloc = g_alloc;
@@ -822,6 +837,7 @@ int open_ctx(jac_ctx* h, void* stream)
         if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
         h->own_stream = true;
     }
+    if ((e = prepare_device(h->device)) != cudaSuccess) return cuda_fail(e, "kernel shared-memory limits");
     const size_t ns = (size_t)std::max(1, h->max_slots);
     int rc;
     if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
@@ -1142,7 +1158,8 @@ int jac_iterate(jac_ctx* h, int64_t n)
             if (h->pctas == 0) {
                 int per_sm = 0, sms = 0;
                 CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith, h->tile_w),
-                                                                 persistent_block_threads(), 0),
+                                                                 persistent_block_threads(),
+                                                                 persistent_smem_bytes(f32, h->arith, h->tile_w)),
                    "occupancy");
                 CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
                 h->pctas = std::max(1, std::min(per_sm * sms, (int)h->hunits.size()));

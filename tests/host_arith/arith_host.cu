@@ -29,3 +29,12 @@ extern "C" int host_frame_laplacian(double c, const double* nb, int eref, double
                ? 1
                : 0;
 }
+
+// 96-bit frame sum of seven values (for checks of the carry chain).
+extern "C" void host_frame_sum7(const double* v, int eref, uint32_t* s)
+{
+    using namespace jac::frame;
+    W96 w[7];
+    for (int i = 0; i < 7; ++i) w[i] = of(v[i], eref);
+    sum7(w[0], w[1], w[2], w[3], w[4], w[5], w[6], s[0], s[1], s[2]);
+}

@@ -125,7 +125,9 @@ def test_grid_frame_mean7_matches_oracle(host_lib):
     for v in mean_cases(rng):
         a = np.ascontiguousarray(v, dtype=np.float64)
         E = max(exp_field(x) for x in a)
-        for extra in (1, 2, 5):
+        # extra >= 20 puts the whole neighbourhood in the low binades of the
+        # frame, where the 96-bit sum has a zero top word
+        for extra in (1, 2, 5, 20, 26, 29):
             eref = max(E, 0) + extra
             total += 1
             if host_lib.host_frame_mean7(a.ctypes.data, eref, ctypes.byref(out)):
@@ -165,3 +167,23 @@ def test_grid_frame_laplacian_matches_oracle(host_lib):
             want = oracle.exact_laplacian(c, a)
             assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (c, nb)
     assert fast > 0.9 * len(cases)
+
+
+def test_frame_sum7_is_the_exact_scaled_sum(host_lib):
+    """The one-chain 96-bit sum equals the exact sum of the values scaled to
+    frame units of 2^(eref - 1106), for values inside the 31-binade window."""
+    host_lib.host_frame_sum7.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    host_lib.host_frame_sum7.restype = None
+    rng = np.random.default_rng(11)
+    out = np.zeros(3, dtype=np.uint32)
+    for _ in range(3000):
+        eref = int(rng.integers(990, 1030))
+        # exponents inside [eref - 31, eref - 1], plus zeros
+        e = rng.integers(eref - 31, eref, size=7)
+        m = 1.0 + rng.random(7)
+        v = np.array([float(np.ldexp(mi, int(ei) - 1023)) for mi, ei in zip(m, e)])
+        v[rng.random(7) < 0.2] = 0.0
+        host_lib.host_frame_sum7(np.ascontiguousarray(v).ctypes.data, eref, out.ctypes.data)
+        got = int(out[0]) | (int(out[1]) << 32) | (int(out[2]) << 64)
+        want = sum(Fraction(float(x)) * Fraction(2) ** (1106 - eref) for x in v)
+        assert want.denominator == 1 and got == want.numerator, (v, eref)
