@@ -505,18 +505,22 @@ JAC_HD inline uint64_t umulhi64(uint64_t a, uint64_t b)
 
 JAC_HD inline W96 of(double v, int eref)
 {
+    // in the frame: sign 0 and exponent field e in [max(eref - 31, 1), eref - 1];
+    // the sign bit makes (hi >> 20) at least 2048, outside every window
     const uint64_t b = dbits(v);
     const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-    const int e = (int)((hi >> 20) & 0x7FF);
-    const int s = e - eref + 31;
-    const bool ok = (hi >> 31) == 0 && e != 0 && (unsigned)s <= 31u;
+    const int lo_e = eref - 31 > 1 ? eref - 31 : 1;
+    const int wn = eref - 1 - lo_e;  // window width - 1 (negative: empty)
+    const uint32_t se = hi >> 20;
+    const bool ok = wn >= 0 && se - (uint32_t)lo_e <= (uint32_t)wn;
     const bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0u;
-    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
-    const int sc = s & 31;
+    const int sc = (int)se - (eref - 31);  // 0 .. 30 when ok
+    const uint32_t mh = ok ? ((hi & 0xFFFFFu) | 0x100000u) : 0u;
+    const uint32_t ml = ok ? lo : 0u;
     W96 w;
-    w.w0 = ok ? (lo << sc) : 0u;
-    w.w1 = ok ? fsl(lo, mh, sc) : 0u;
-    w.w2 = ok ? fsl(mh, 0u, sc) : (zero ? 0u : kMarker);
+    w.w0 = fsl(0u, ml, sc & 31);
+    w.w1 = fsl(ml, mh, sc & 31);
+    w.w2 = fsl(mh, 0u, sc & 31) | ((ok || zero) ? 0u : kMarker);
     w.w3 = 0u;
     return w;
 }
@@ -599,8 +603,8 @@ JAC_HD inline void sum7(const W96& a, const W96& b, const W96& c, const W96& d, 
 //   top bit is bit 63 of N (a sum below 2^64 is first moved up 32 bits; a
 //   nonzero in-frame value is at least 2^52, so S is then zero or has a
 //   nonzero top word); the bits shifted out become a sticky flag.
-//   Q = floor(N / 7) by multiply-high with the magic 2^66/7 and the usual
-//   add-back, Q in [2^60.2, 2^61.2). Q has 61 or 62 bits and is rounded to
+//   Q = floor(N / 7) from a multiply-high by floor(2^64/7), which is exact
+//   or one short, and the remainder against it; Q in [2^60.2, 2^61.2). Q has 61 or 62 bits and is rounded to
 //   53: its last bit lies below the rounding position, so OR-ing the sticky
 //   information (nonzero remainder or dropped bits) into it lets one correctly
 //   rounded integer -> binary64 conversion round the exact quotient.
@@ -619,9 +623,13 @@ JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& 
     const uint64_t Nn = ((uint64_t)fsrc(t1, t2, r) << 32) | fsrc(t0, t1, r);
     const bool st0 = shlc(t0, 32 - r) != 0u;
     const int L = r + (z2 ? 32 : 64);
-    const uint64_t t = umulhi64(Nn, 0x2492492492492493ull);
-    const uint64_t Q = (((Nn - t) >> 1) + t) >> 2;
-    const uint32_t R = (uint32_t)Nn - 7u * (uint32_t)Q;  // the remainder (< 7) from the low words
+    // Qa = floor(Nn * floor(2^64/7) / 2^64) is Q or Q - 1; the remainder
+    // against it, R' in [0, 13], fixes both Q and the true remainder
+    const uint64_t Qa = umulhi64(Nn, 0x2492492492492492ull);
+    const uint32_t Ra = (uint32_t)Nn - 7u * (uint32_t)Qa;
+    const uint32_t fix = Ra >= 7u ? 1u : 0u;
+    const uint64_t Q = Qa + fix;
+    const uint32_t R = Ra - 7u * fix;
     const uint64_t qj = Q | ((R != 0u || st0) ? 1ull : 0ull);
     const uint64_t qb = dbits(u64_to_double_rn(qj));
     const int adj = L - 64 + eref - 1106;

@@ -187,3 +187,19 @@ def test_frame_sum7_is_the_exact_scaled_sum(host_lib):
         got = int(out[0]) | (int(out[1]) << 32) | (int(out[2]) << 64)
         want = sum(Fraction(float(x)) * Fraction(2) ** (1106 - eref) for x in v)
         assert want.denominator == 1 and got == want.numerator, (v, eref)
+
+
+def test_grid_frame_tiny_frames_decline_or_match(host_lib):
+    """Frames whose window reaches the subnormal range (eref below 32), and an
+    empty window (eref 1): every accepted mean is the correctly rounded one."""
+    rng = np.random.default_rng(12)
+    out = ctypes.c_double()
+    for eref in (1, 2, 3, 17, 31, 32, 33):
+        for _ in range(300):
+            e = rng.integers(0, max(eref, 1), size=7)
+            v = np.array([float(np.ldexp(1.0 + rng.random(), int(x) - 1023)) if x > 0
+                          else float(rng.integers(0, 2 ** 20)) * 2.0 ** -1074 for x in e])
+            a = np.ascontiguousarray(v)
+            if host_lib.host_frame_mean7(a.ctypes.data, eref, ctypes.byref(out)):
+                want = oracle.exact_mean7(a)
+                assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (list(v), eref)
