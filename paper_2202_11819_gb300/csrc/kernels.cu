@@ -12,9 +12,11 @@
 //                                 than one thread per cell of all faces),
 //   k_stencil_block               the update of one block from its own ghost
 //                                 layer (unfused flow),
-//   k_fused_step                  unpack + update + pack of every block in one
+//   k_fused_step / k_fused_ring   unpack + update + pack of every block in one
 //                                 launch (strategy C): ghost values are read
-//                                 straight from the neighbouring blocks,
+//                                 straight from the neighbouring blocks
+//                                 (k_fused_ring: binary32, whose update needs
+//                                 no frame conversion),
 //   k_persistent                  all blocks and all iterations in one launch,
 //                                 each tile waiting only for the previous
 //                                 iteration of its own and neighbouring blocks
@@ -26,6 +28,7 @@
 
 #include <cstdint>
 #include <type_traits>
+#include <utility>
 
 #include "arith.cuh"
 #include "jac_common.cuh"
@@ -547,9 +550,9 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     const int64_t plane = d.plane;
     if (tid == 0) slow->n = 0;
 
-    // own stream (kind 1: the plane above, planes z0+1 .. z1-1, the value
-    // above the range held in a register; kind 2: a halo cell inside the
-    // tile, planes z0 .. z1-1)
+    // own stream: the plane above the current one, planes z0+1 .. z1-1 copied
+    // (kind 1: an interior column, whose plane z1 is held in a register; kind
+    // 2: a halo cell inside the tile); the current plane is carried
     const bool k1 = x < bx && y < by;
     const bool k2 = (x == bx && y < by) || (y == by && x < bx);
     const T* osrc = pool;
@@ -569,10 +572,13 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         wzm = frame::of((double)ldv<T, CG>(zlo), eref);
         wc = frame::of((double)ldv<T, CG>(col + z0 * plane), eref);
     } else if (k2) {
+        // a halo cell inside the tile streams like an interior column (its
+        // own plane carried, the plane above copied), without computing
         const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
-        osrc = s.p + z0 * s.stride;
+        osrc = s.p + (z0 + 1) * s.stride;
         ostr = s.stride;
-        olim = z1;
+        olim = z1 - 1;
+        wc = frame::of((double)ldv<T, CG>(s.p + z0 * s.stride), eref);
     }
     const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid);
     const bool hv = hs.er >= 0;
@@ -609,11 +615,11 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         E* const b1 = b0 + kPlane;
         const T v0 = rc[s * kThreads + tid];
         const T v1 = rc[(s + 1) * kThreads + tid];
-        // kind 1: u1, u2 are planes k+1, k+2 (the last one from the register)
-        const E c0 = frame::of((double)(k1 && k + 1 >= z1 ? zhiv : v0), eref);
-        const E c1 = frame::of((double)(k1 && k + 2 >= z1 ? zhiv : v1), eref);
-        b0[own] = k1 ? wc : c0;
-        if (TWO) b1[own] = k1 ? c0 : c1;
+        // planes k+1, k+2 of the own column (plane z1 from the register)
+        const E c0 = frame::of((double)(k + 1 >= z1 ? zhiv : v0), eref);
+        const E c1 = frame::of((double)(k + 2 >= z1 ? zhiv : v1), eref);
+        b0[own] = wc;
+        if (TWO) b1[own] = c0;
         if (halo_warp) {
             b0[hslot] = frame::of((double)re[s * kEr + (tid < kEr ? tid : 0)], eref);
             if (TWO) b1[hslot] = frame::of((double)re[(s + 1) * kEr + (tid < kEr ? tid : 0)], eref);
@@ -657,129 +663,164 @@ __host__ __device__ constexpr int kernel_bytes()
     else return engine_bytes<T, OP, TW, kRing<T>>();
 }
 
-// ---------------------------------------------------------------- lean engine
-// For binary32 (the floating-point rule, cheap arithmetic) the
-// arithmetic is cheap and the kernel must simply keep enough bytes in flight.
-// Each thread owns one column of the tile and walks it along z with no
-// shared memory and no barrier: its own values stream from DRAM DC planes
-// ahead; its four x/y neighbours are read from short streams DN planes ahead,
-// which hit L1 (their lines were requested DC - DN planes earlier by the
-// neighbouring column's own stream); the z neighbours are carried in
-// registers. Neighbours across a block face come from the neighbouring block
-// (or are the Dirichlet constant, stride 0).
+// ------------------------------------------------------- ring engine (SEQ)
+// The floating-point rule needs no conversion, so the prefetch ring itself is
+// the exchange plane: ring slot q holds the whole (TW + 2) x (TY + 2) tile
+// plane q (interior columns, the halo ring, halo cells inside the tile).
+// Every thread copies its stream(s) ahead with cp.async straight into the
+// slot; after a wait and one barrier per batch of kB planes, the cells of the
+// batch read their x/y neighbours from the slot and carry the z neighbours in
+// registers (the value above the unit's last plane is loaded once).
+constexpr int kSeqBatch = 4;
 template <typename T>
-constexpr int kLeanDC = 11;
-constexpr int kLeanDN = 1;
+constexpr int kSeqAhead = sizeof(T) == 4 ? 3 : 1;  // batches in flight beyond the next
+template <typename T>
+constexpr int kSeqRing = (kSeqAhead<T> + 3) * kSeqBatch;  // planes in the ring
 
-template <typename T, bool PULL, bool CG, int TW>
-__device__ __forceinline__ void lean_tile(T* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p,
-                                          int x0, int y0, int z0, int z1)
+template <int TW>
+__host__ __device__ constexpr int seq_plane()
 {
-    constexpr int DC = kLeanDC<T>, DN = kLeanDN;
-    const BlockDesc& d = desc[b];
-    const int tid = threadIdx.x;
-    const int x = x0 + tid % TW, y = y0 + tid / TW;
-    if (x >= d.ext[0] || y >= d.ext[1]) return;
-    const int bz = d.ext[2];
-    const int64_t plane = d.plane;
-    const T* pc = pool + cell_index<T>(d, p, x, y, 0);
-    const int32_t plane32 = (int32_t)plane;
-    const Src<T> s0 = xy_source<T, PULL>(pool, desc, d, p, x - 1, y);
-    const Src<T> s1 = xy_source<T, PULL>(pool, desc, d, p, x + 1, y);
-    const Src<T> s2 = xy_source<T, PULL>(pool, desc, d, p, x, y - 1);
-    const Src<T> s3 = xy_source<T, PULL>(pool, desc, d, p, x, y + 1);
-    // plane strides fit 32 bits (at most (256 + 2) x 512 elements)
-    struct {
-        const T* p;
-        int32_t stride;
-    } sxm{s0.p, (int32_t)s0.stride}, sxp{s1.p, (int32_t)s1.stride}, sym{s2.p, (int32_t)s2.stride},
-        syp{s3.p, (int32_t)s3.stride};
-    const T* zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : pc + z1 * plane;
-    const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : pc + (z0 - 1) * plane;
-    T* out = pool + cell_index<T>(d, p ^ 1, x, y, 0);
-    // Ring slots are fixed registers: the z loop is unrolled by the ring length
-    // R so every slot index is a compile-time constant (moving a register whose
-    // load is still in flight would wait for that load and undo the prefetch).
-    // Own column: plane q sits in slot (q - z0 - 1) % R; neighbours: plane q
-    // in slot (q - z0) % RN, with RN dividing R. Every stream walks with a
-    // running pointer; chunks whose loads all fall inside [z0, z1) run without
-    // range checks.
-    constexpr int R = DC + 1, RN = DN + 1;
-    static_assert(R % RN == 0, "neighbour ring must divide the column ring");
-    T rc[R], rxm[RN], rxp[RN], rym[RN], ryp[RN];
-#pragma unroll
-    for (int i = 0; i < DC; ++i) {
-        const int q = z0 + 1 + i;
-        rc[i] = q < z1 ? ld<T, CG>(pc + q * plane32) : (q == z1 ? ld<T, CG>(zhi) : T(0));
-    }
-    const T* po = pc + (z0 + 1 + DC) * plane32;  // own stream: plane k + 1 + DC
-    const T* pxm = sxm.p + z0 * sxm.stride;       // neighbour streams: plane k + DN
-    const T* pxp = sxp.p + z0 * sxp.stride;
-    const T* pym = sym.p + z0 * sym.stride;
-    const T* pyp = syp.p + z0 * syp.stride;
-#pragma unroll
-    for (int i = 0; i < DN; ++i) {
-        const bool in = z0 + i < z1;
-        rxm[i] = in ? ld<T, CG>(pxm) : T(0);
-        rxp[i] = in ? ld<T, CG>(pxp) : T(0);
-        rym[i] = in ? ld<T, CG>(pym) : T(0);
-        ryp[i] = in ? ld<T, CG>(pyp) : T(0);
-        pxm += sxm.stride;
-        pxp += sxp.stride;
-        pym += sym.stride;
-        pyp += syp.stride;
-    }
-    T zm = ld<T, CG>(zlo);
-    T c = ld<T, CG>(pc + z0 * plane32);
-    T* po_out = out + z0 * plane32;
-    auto step = [&](auto full, int j, int k) {
-        constexpr bool FULL = decltype(full)::value;
-        const int sn = (j + R - 1) % R, sl = (j + DN) % RN, su = j % RN;
-        if (FULL) {
-            rc[sn] = ld<T, CG>(po);
-            rxm[sl] = ld<T, CG>(pxm);
-            rxp[sl] = ld<T, CG>(pxp);
-            rym[sl] = ld<T, CG>(pym);
-            ryp[sl] = ld<T, CG>(pyp);
-        } else {
-            const int q = k + 1 + DC;
-            rc[sn] = q < z1 ? ld<T, CG>(po) : (q == z1 ? ld<T, CG>(zhi) : T(0));
-            if (k + DN < z1) {
-                rxm[sl] = ld<T, CG>(pxm);
-                rxp[sl] = ld<T, CG>(pxp);
-                rym[sl] = ld<T, CG>(pym);
-                ryp[sl] = ld<T, CG>(pyp);
-            }
-        }
-        po += plane32;
-        pxm += sxm.stride;
-        pxp += sxp.stride;
-        pym += sym.stride;
-        pyp += syp.stride;
-        const T zp = rc[j];
-        *po_out = mean7<T, 0>(c, rxm[su], rxp[su], rym[su], ryp[su], zm, zp);
-        po_out += plane32;
-        zm = c;
-        c = zp;
-    };
-    int kb = z0;
-    // full chunks: the last own load of the chunk, plane kb + R + DC, is < z1
-    for (; kb + R + DC < z1; kb += R) {
-#pragma unroll
-        for (int j = 0; j < R; ++j) step(std::true_type{}, j, kb + j);
-    }
-    for (; kb < z1; kb += R) {
-#pragma unroll
-        for (int j = 0; j < R; ++j)
-            if (kb + j < z1) step(std::false_type{}, j, kb + j);
-    }
+    return (kThreads / TW + 2) * (TW + 2) + 1;  // + one slot written by threads without a halo slot
 }
 
 template <typename T, int TW>
-__global__ void __launch_bounds__(kThreads, 2) k_fused_lean(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
+__host__ __device__ constexpr int seq_engine_bytes()
+{
+    return kSeqRing<T> * seq_plane<TW>() * (int)sizeof(T);
+}
+
+template <typename T, bool PULL, bool CG, int TW>
+__device__ void tile_engine_ring(T* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p, int x0,
+                                 int y0, int z0, int z1, unsigned char* smraw)
+{
+    constexpr int kB = kSeqBatch, kP = kSeqAhead<T>, RD = kSeqRing<T>;
+    constexpr int kTX = TW, kSW = TW + 2, kPl = seq_plane<TW>();
+    constexpr uint32_t kPlB = kPl * sizeof(T);
+    T* const ring = (T*)smraw;  // [RD][kPl]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int64_t plane = d.plane;
+
+    // own stream: planes z0 .. z1-1 of the column (kind 1) or of the halo cell
+    // inside the tile (kind 2); q_end = z0 for threads with no stream
+    const bool k1 = x < bx && y < by;
+    const bool k2 = (x == bx && y < by) || (y == by && x < bx);
+    const T* op = pool;
+    int64_t ostr = 0;
+    int oend = z0;
+    T zm = T(0), zhiv = T(0);
+    T* out = pool;
+    if (k1) {
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        op = col + z0 * plane;
+        ostr = plane;
+        oend = z1;
+        zm = ldv<T, CG>(z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane);
+        zhiv = ldv<T, CG>(z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane);
+        out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
+    } else if (k2) {
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
+        op = s.p + z0 * s.stride;
+        ostr = s.stride;
+        oend = z1;
+    }
+    const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid);
+    const bool hv = hs.er >= 0;
+    const T* hp = hs.p;
+    const int64_t hstr = hs.stride;
+    const int hend = hv ? z1 : z0;
+    const int own = (ty + 1) * kSW + tx + 1;
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+    const uint32_t own_s = ring_s + own * sizeof(T);
+    const uint32_t halo_s = ring_s + (hv ? hs.er * kSW + hs.ec : kPl - 1) * sizeof(T);
+
+    // Copy batch m holds planes z0 + m kB .. z0 + m kB + kB - 1 in ring slots
+    // (m kB + i) % RD. Batch j of the update computes planes k0 .. k0+kB-1
+    // (k0 = z0 + j kB) and reads planes k0 .. k0+kB: copy batches up to j + 1
+    // must have landed. It first issues batch j + kP + 1, whose slots last
+    // held planes read two barriers ago. The z loop runs a whole ring turn
+    // (RD / kB batches) per pass, so every slot index is a constant; passes
+    // whose planes and copies all lie inside the range skip the range checks.
+    constexpr int kNB = RD / kB;
+    static_assert(RD % kB == 0, "ring of whole batches");
+    const bool halo_warp = (tid & ~31) < ring_extra<TW>();  // warp-uniform
+    const bool own_on = oend > z0, halo_on = hend > z0;
+    int cq = z0;  // the next plane to copy
+    // copy batch into slots sb * kB .. sb * kB + kB - 1
+    auto copy_batch = [&](auto full_c, auto sb_c) {
+        constexpr bool FULL = decltype(full_c)::value;
+        constexpr int sb = decltype(sb_c)::value;
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const uint32_t so = (uint32_t)((sb * kB + i) * kPlB);
+            cp_async_if<sizeof(T)>(own_s + so, op, FULL ? own_on : cq + i < oend);
+            op += ostr;
+        }
+        if (halo_warp) {
+#pragma unroll
+            for (int i = 0; i < kB; ++i) {
+                const uint32_t so = (uint32_t)((sb * kB + i) * kPlB);
+                cp_async_if<sizeof(T)>(halo_s + so, hp, FULL ? halo_on : cq + i < hend);
+                hp += hstr;
+            }
+        }
+        cq += kB;
+        cp_async_commit();
+    };
+    // prologue: batches 0 .. kP
+    [&]<int... M>(std::integer_sequence<int, M...>) {
+        (copy_batch(std::false_type{}, std::integral_constant<int, M>{}), ...);
+    }(std::make_integer_sequence<int, kP + 1>{});
+
+    const T* const rd = ring + own;  // plane in slot q: rd[q * kPl]
+    T c;
+    cp_async_wait<kP>();
+    __syncthreads();
+    c = rd[0];
+    // one batch: j-th of the pass starting at kb
+    auto batch = [&](auto full_c, auto bi_c, int kb) {
+        constexpr bool FULL = decltype(full_c)::value;
+        constexpr int bi = decltype(bi_c)::value;
+        const int k0 = kb + bi * kB;
+        copy_batch(full_c, std::integral_constant<int, (bi + kP + 1) % kNB>{});
+        cp_async_wait<kP>();
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const int k = k0 + i;
+            if (FULL || k < z1) {
+                const int q = bi * kB + i, qn = (q + 1) % RD;
+                const T* pl = rd + q * kPl;
+                const T zp = (FULL || k + 1 < z1) ? rd[qn * kPl] : zhiv;
+                const T o = mean7<T, 0>(c, pl[-1], pl[1], pl[-kSW], pl[kSW], zm, zp);
+                if (k1) *out = o;
+                out += plane;
+                zm = c;
+                c = zp;
+            }
+        }
+    };
+    auto pass = [&](auto full_c, int kb) {
+        [&]<int... J>(std::integer_sequence<int, J...>) {
+            (batch(full_c, std::integral_constant<int, J>{}, kb), ...);
+        }(std::make_integer_sequence<int, kNB>{});
+    };
+    int kb = z0;
+    // a full pass computes planes kb .. kb+RD-1 (each with a plane above it in
+    // the range) and copies planes up to kb + RD + (kP + 1) kB - 1
+    for (; kb + RD + (kP + 1) * kB <= z1; kb += RD) pass(std::true_type{}, kb);
+    for (; kb < z1; kb += RD) pass(std::false_type{}, kb);
+    cp_async_wait<0>();
+    __syncthreads();  // the ring is free for the next unit
+}
+
+template <typename T, int TW>
+__global__ void __launch_bounds__(kThreads, 3) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
 {
     const TileUnit u = units[blockIdx.x];
-    lean_tile<T, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
+    tile_engine_ring<T, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
 }
 
 template <typename T, int OP, int TW>
@@ -840,8 +881,8 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // overwrites (buffer p^1 held iteration t-1). The seven counters are polled
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
-template <typename T, int OP, int TW, bool LEAN>
-__global__ void __launch_bounds__(kThreads, 2)
+template <typename T, int OP, int TW, bool RING>
+__global__ void __launch_bounds__(kThreads, RING ? 3 : 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
@@ -890,10 +931,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (s_stop) break;
         // take the next unit now; its index is read after this one finishes
         if (tid == 0) s_next = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
-        if constexpr (LEAN) {
-            // plain (L1-cached) loads are safe here: the acquire and the
+        if constexpr (RING) {
+            // L1-allocating copies are safe here: the acquire and the
             // barrier above order them after the neighbours' releases
-            lean_tile<T, true, false, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
+            tile_engine_ring<T, true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1,
+                                                jac_dyn_sm);
         } else {
             if constexpr (OP == OP_EXACT)
                 tile_engine_pair<T, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
@@ -1155,7 +1197,7 @@ static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
         }
     }
     if constexpr (sizeof(T) == 4)
-        k_fused_lean<T, TW><<<a.nunits, kThreads, 0, s>>>((T*)a.pool, a.desc, a.units, p);
+        k_fused_ring<T, TW><<<a.nunits, kThreads, seq_engine_bytes<T, TW>(), s>>>((T*)a.pool, a.desc, a.units, p);
     else
         k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
 }
@@ -1187,7 +1229,7 @@ int persistent_block_threads() { return kThreads; }
 template <int TW>
 static int persistent_bytes_t(int dtype_f32, int arith)
 {
-    if (dtype_f32) return 0;
+    if (dtype_f32) return seq_engine_bytes<float, TW>();
     return arith == 1 ? kernel_bytes<double, OP_EXACT, TW>()
                       : kernel_bytes<double, OP_SEQ, TW>();
 }
@@ -1218,6 +1260,8 @@ static cudaError_t prepare_tw()
     JAC_ALLOW((k_fused_step<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
     JAC_ALLOW((k_persistent<double, OP_EXACT, TW, false>), (kernel_bytes<double, OP_EXACT, TW>()));
     JAC_ALLOW((k_persistent<double, OP_SEQ, TW, false>), (kernel_bytes<double, OP_SEQ, TW>()));
+    JAC_ALLOW((k_fused_ring<float, TW>), (seq_engine_bytes<float, TW>()));
+    JAC_ALLOW((k_persistent<float, OP_SEQ, TW, true>), (seq_engine_bytes<float, TW>()));
     JAC_ALLOW((k_residual<double, TW>), (engine_bytes<double, OP_RES, TW, kRingRes>()));
     JAC_ALLOW((k_residual<float, TW>), (engine_bytes<float, OP_RES, TW, kRingRes>()));
 #undef JAC_ALLOW
@@ -1243,7 +1287,7 @@ static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith
             return;
         }
     }
-    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? 0 : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? seq_engine_bytes<T, TW>() : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
                                                           q.n_iters, q.done, q.work, q.status, q.wait_ns,
                                                           q.hold_block, q.hold_after);
 }
