@@ -32,6 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+MODE_NAMES = {0: "unfused", 1: "fused", 2: "graph", 3: "persistent", 4: "graph_fused"}
 METRIC = "Jacobi3D cell-updates/s"
 UNIT = "cell-updates/s"
 BYTES_PER_UPDATE = {"f64": 16, "f32": 8}  # read + write of one cell at ideal neighbour reuse
@@ -47,12 +48,16 @@ def parse():
     p.add_argument("--block", type=int, nargs=3, default=[64, 64, 64])
     p.add_argument("--iters", type=int, default=1000, help="Jacobi iterations per step")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
-    p.add_argument("--mode", default="persistent")
+    p.add_argument("--mode", default="auto",
+                   help="persistent, fused, graph_fused, graph, unfused, or auto: the autotuner also picks "
+                        "between the persistent and fused forms")
     p.add_argument("--arith", default="exact", choices=["exact", "seq"])
     p.add_argument("--forms", action="store_true", help="also time the unfused / fused / graph forms")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default tile shape (32 wide, whole blocks)")
+    p.add_argument("--tile-w", type=int, default=0, help="fix the tile width (16, 32 or 64; implies --no-autotune)")
+    p.add_argument("--zdepth", type=int, default=0, help="with --tile-w: planes per work unit (0: whole blocks)")
     p.add_argument("--workload", default="grid", choices=["grid", "batch", "f32", "serve"],
                    help="grid: one overdecomposed grid (default); batch: many independent grids in one launch")
     p.add_argument("--instances", type=int, default=256, help="batch workload: number of grids")
@@ -161,26 +166,59 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic(kernel_tag: str):
-    """dram bytes per launch of the timed kernel from the committed ncu
-    summary (profiles/<kernel_tag>.txt, line 'traffic_bytes_per_iteration: N'),
-    or None when no capture of the current kernel exists."""
+def profile_field(kernel_tag: str, key: str):
+    """A 'key: value' line of the committed ncu summary profiles/<kernel_tag>.txt
+    (None when the file or the line is missing)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         for line in f:
-            if line.startswith("traffic_bytes_per_iteration:"):
+            if line.startswith(key + ":"):
                 v = line.split(":", 1)[1].strip()
-                return None if v in ("null", "None", "") else float(v)
+                return None if v in ("null", "None", "") else v
     return None
+
+
+def profile_traffic(kernel_tag: str):
+    """dram bytes per iteration of the timed kernel from the committed ncu
+    summary (line 'traffic_bytes_per_iteration: N'), or None when no capture
+    of the current kernel exists."""
+    v = profile_field(kernel_tag, "traffic_bytes_per_iteration")
+    return None if v is None else float(v)
+
+
+def tune(lib, J, a, modes=("persistent", "fused")):
+    """Tile shape (and, for --mode auto, the form) for context J: a fixed
+    --tile-w, or the library's autotuner run once per candidate form, keeping
+    the fastest. Returns the chosen settings (or None) and leaves J set to them."""
+    J.set_mode(a.mode if a.mode != "auto" else "persistent")
+    if a.tile_w:
+        lib.jac_set_tile(J.h, a.tile_w, a.zdepth)
+        return {"tile_w": a.tile_w, "zdepth": a.zdepth, "fixed": True,
+                "mode": a.mode if a.mode != "auto" else "persistent"}
+    if a.no_autotune:
+        return None
+    cands = modes if a.mode == "auto" else (a.mode,)
+    best = None
+    for m in cands:
+        J.set_mode(m)
+        r = lib.jac_autotune(J.h, 4)
+        r["mode"] = m
+        if best is None or r["ms_per_iter"] < best["ms_per_iter"]:
+            best = r
+    J.set_mode(best["mode"])
+    lib.jac_set_tile(J.h, best["tile_w"], best["zdepth"])
+    if len(cands) > 1:
+        best["modes_tried"] = list(cands)
+    return best
 
 
 def workload_name(a):
     g, b = a.grid, a.block
     nb = [-(-g[i] // b[i]) for i in range(3)]
     return (f"Jacobi3D {g[0]}x{g[1]}x{g[2]} {a.dtype.upper()}, {nb[0]}x{nb[1]}x{nb[2]} blocks of "
-            f"{b[0]}x{b[1]}x{b[2]}, {a.iters} iterations + residual per step, {a.mode} form, "
+            f"{b[0]}x{b[1]}x{b[2]}, {a.iters} iterations + residual per step, "
             f"{'correctly rounded mean' if (a.arith == 'exact' and a.dtype == 'f64') else 'left-to-right sum / 7'}")
 
 
@@ -264,12 +302,11 @@ def run_ours(a, rank, world, local, pg):
     rho = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
 
     with torch.cuda.stream(stream):
-        J = Jacobi3D(g, b, dtype=a.dtype, bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode,
-                     arith=a.arith if a.dtype == "f64" else "seq")
+        J = Jacobi3D(g, b, dtype=a.dtype, bc=synth.DIRICHLET_X0, stream=stream.cuda_stream,
+                     mode="persistent", arith=a.arith if a.dtype == "f64" else "seq")
         J.write_device(dev_u0)
-        tune = None
-        if not a.no_autotune:
-            tune = _lib.jac_autotune(J.h, 4)
+        tuned = tune(_lib, J, a)
+        mode = MODE_NAMES[J.info()["mode"]]
 
         def step():
             J.iterate(a.iters)
@@ -308,10 +345,11 @@ def run_ours(a, rank, world, local, pg):
         mean_launch_s = statistics.mean(iter_ms) / 1e3
         algo_bytes = BYTES_PER_UPDATE[a.dtype] * ncell * a.iters
         achieved = algo_bytes / mean_launch_s / 1e9
-        kernel_tag = f"{a.mode}_{a.dtype}_{a.arith}_{g[0]}"
+        kernel_tag = f"{mode}_{a.dtype}_{a.arith}_{g[0]}"
         traffic = profile_traffic(kernel_tag)
         if traffic is not None:
             traffic = traffic * a.iters  # summaries store bytes per iteration
+        limiter = profile_field(kernel_tag, "limiter")
 
         # ---- end to end through the C ABI with host buffers
         e2e = None
@@ -357,7 +395,7 @@ def run_ours(a, rank, world, local, pg):
                 forms[mode] = {"iters": n, "ms_per_iter": 1e3 * w / n,
                                "cell_updates_per_s": ncell * n / w,
                                "device_ms_per_iter": e0.elapsed_time(e1) / n}
-            J.set_mode(a.mode)
+            J.set_mode(mode)
         J.sync()
         J.close()
 
@@ -383,8 +421,8 @@ def run_ours(a, rank, world, local, pg):
         "dtype": a.dtype,
         "data": "synthetic",
         "config": {"workload": workload_name(a), "grid": list(g), "block": list(b), "iterations_per_step": a.iters,
-                   "mode": a.mode, "arith": a.arith if a.dtype == "f64" else "seq",
-                   "autotune": tune,
+                   "mode": mode, "arith": a.arith if a.dtype == "f64" else "seq",
+                   "autotune": tuned,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (working set %.2f GB vs 129 MB L2)" % (
                        2 * ncell * np.dtype(np_dt).itemsize / 1e9)},
@@ -394,7 +432,7 @@ def run_ours(a, rank, world, local, pg):
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s",
                      "algorithmic_bytes_per_launch": algo_bytes,
-                     "launch_ms_mean": 1e3 * mean_launch_s},
+                     "launch_ms_mean": 1e3 * mean_launch_s, "limiter": limiter},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -429,11 +467,12 @@ def run_batch(a, rank, world, local, pg):
     dev = torch.from_numpy(host).to(f"cuda:{local}")
     bcs = [synth.DIRICHLET_X0] * len(dims)
     with torch.cuda.stream(stream):
-        B = Jacobi3DBatch(dims, a.block, bcs=bcs, stream=stream.cuda_stream, mode=a.mode, arith=a.arith)
+        B = Jacobi3DBatch(dims, a.block, bcs=bcs, stream=stream.cuda_stream, mode="persistent", arith=a.arith)
         from paper_2202_11819_gb300 import _lib
 
         _lib.jac_write_device(B.h, dev.data_ptr(), ncell, _lib.JAC_F64)
-        tune = B.autotune(4)
+        tuned = tune(_lib, B, a)
+        mode = MODE_NAMES[B.info()["mode"]]
         rho = torch.zeros(len(dims), dtype=torch.float64, device=f"cuda:{local}")
 
         def step():
@@ -481,9 +520,9 @@ def run_batch(a, rank, world, local, pg):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"batch of {len(dims)} FP64 grids, each axis from 32..192 step 16 (seed 0), "
                                f"blocks <= {a.block[0]}x{a.block[1]}x{a.block[2]}, {a.batch_iters} iterations "
-                               f"+ per-grid residuals per step, {a.mode} form, autotuned",
+                               f"+ per-grid residuals per step, {mode} form, autotuned",
                    "cells": ncell, "blocks": info["n_blocks"], "units": info["n_units"],
-                   "autotune": tune},
+                   "autotune": tuned},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None},
         "plain_form_cell_updates_per_s": plain,
@@ -514,13 +553,23 @@ def run_f32(a, rank, world, local, pg):
     dev32 = dev64.to(torch.float32)
     n_res = a.f32_iters // a.residual_every
     with torch.cuda.stream(stream):
-        J = Jacobi3D(g, b, dtype="f32", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode)
-        tune = _lib.jac_autotune(J.h, 4) if not a.no_autotune else None
+        J = Jacobi3D(g, b, dtype="f32", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode="persistent")
+        J.write_device(dev32)
+        tuned = tune(_lib, J, a)
+        mode = MODE_NAMES[J.info()["mode"]]
         rho = torch.zeros(max(1, n_res), dtype=torch.float64, device=f"cuda:{local}")
 
-        def step():
+        chunk_ev = []  # CUDA events around each chunk of iterations (the update launches)
+
+        def step(record=False):
             for r in range(n_res):
+                if record:
+                    e = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                    e[0].record(stream)
                 J.iterate(a.residual_every)
+                if record:
+                    e[1].record(stream)
+                    chunk_ev.append(e)
                 _lib.jac_residual_device(J.h, rho[r:r + 1].data_ptr())
             rest = a.f32_iters - n_res * a.residual_every
             if rest:
@@ -537,9 +586,10 @@ def run_f32(a, rank, world, local, pg):
             t0 = time.perf_counter()
             for _ in range(a.steps):
                 J.write_device(dev32)  # every step starts from the same state: the error check below applies to it
-                step()
+                step(record=True)
             stream.synchronize()
             wall = time.perf_counter() - t0
+        chunk_ms = [e[0].elapsed_time(e[1]) for e in chunk_ev]
         J.sync()
         launches = J.info()["kernel_launches"] - launches0
         rhos = rho.cpu().tolist()
@@ -547,7 +597,8 @@ def run_f32(a, rank, world, local, pg):
         J.read_device(out32)
         J.close()
         # binary64 run of the same grid for the error report
-        K = Jacobi3D(g, b, dtype="f64", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=a.mode, arith="exact")
+        K = Jacobi3D(g, b, dtype="f64", bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode="persistent",
+                     arith="exact")
         K.write_device(dev64)
         t1 = time.perf_counter()
         K.iterate(a.f32_iters)
@@ -566,17 +617,30 @@ def run_f32(a, rank, world, local, pg):
     value = world * ncell * a.f32_iters * a.steps / wall
     bound = a.f32_iters * (27.0 / 7.0 + 1.0) * 2.0 ** -24 + 2.0 ** -25
     peak, kind = measured_peaks()
-    achieved = BYTES_PER_UPDATE["f32"] * ncell * a.f32_iters * a.steps / wall / 1e9
+    # the dominant kernel: the update launch (one per iteration in the fused
+    # forms, one per chunk in the persistent form), timed by the chunk events
+    per_launch_iters = 1 if mode in ("fused", "graph_fused", "unfused", "graph") else a.residual_every
+    iter_s = (statistics.mean(chunk_ms) / a.residual_every / 1e3) if chunk_ms else wall / a.f32_iters
+    algo_bytes = BYTES_PER_UPDATE["f32"] * ncell * per_launch_iters
+    achieved = algo_bytes / (iter_s * per_launch_iters) / 1e9
+    traffic = profile_traffic(f"{mode}_f32_seq_{g[0]}")
+    if traffic is not None:
+        traffic = traffic * per_launch_iters
+    limiter = profile_field(f"{mode}_f32_seq_{g[0]}", "limiter")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * wall / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"Jacobi3D {g[0]}x{g[1]}x{g[2]} FP32 storage and arithmetic, blocks of "
                                f"{b[0]}x{b[1]}x{b[2]}, {a.f32_iters} iterations per step with the FP64 residual "
-                               f"every {a.residual_every}, {a.mode} form",
-                   "autotune": tune},
+                               f"every {a.residual_every}, {mode} form",
+                   "autotune": tuned},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "bytes_per_update": 8},
+                     "traffic": traffic, "bytes_per_update": 8, "algorithmic_bytes_per_launch": algo_bytes,
+                     "launch_ms_mean": 1e3 * iter_s * per_launch_iters, "limiter": limiter,
+                     "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)" if kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "step_hbm_frac": BYTES_PER_UPDATE["f32"] * value / 1e9 / peak,
         "error_vs_f64": {"max_abs": max_abs, "rel_l2": rel_l2, "proven_max_abs_bound": bound,
                          "within_bound": max_abs <= bound},
         "f64_same_grid_cell_updates_per_s": ncell * a.f32_iters / t64,

@@ -137,3 +137,27 @@ def test_batch_of_configured_shapes_small():
         B.iterate(3)
         for i in (0, 3):
             assert np.array_equal(B.read(i), oracle.jacobi(grids[i], bc, 3, oracle.RULE_EXACT))
+
+
+@pytest.mark.parametrize("tile_w", [16, 32, 64])
+@pytest.mark.parametrize("zdepth", [0, 16, 7])
+@pytest.mark.parametrize("mode", ["persistent", "fused"])
+def test_f32_tile_shapes_and_z_depths_bit_exact(tile_w, zdepth, mode):
+    """The binary32 ring engine over ragged blocks (tiles overhanging block
+    edges), z ranges shorter than a ring turn (zdepth 7, 16) and whole 64-plane
+    blocks (whole ring turns without range checks), against the binary32
+    oracle."""
+    dims = [(70, 45, 100), (17, 64, 64), (64, 9, 131)]
+    rng = np.random.default_rng(6)
+    bcs = [tuple(float(v) for v in rng.random(6)) for _ in dims]
+    grids = [synth.grid_uniform01(300 + i, *d).astype(np.float32) for i, d in enumerate(dims)]
+    iters = 5
+    with Jacobi3DBatch(dims, (64, 40, 64), dtype="f32", bcs=bcs, mode=mode) as B:
+        B.set_tile(tile_w, zdepth)
+        for i, g in enumerate(grids):
+            _lib.jac_write_instance(B.h, i, g.astype(np.float64))
+        B.iterate(iters)
+        outs = [B.read(i) for i in range(len(dims))]
+    for i, g in enumerate(grids):
+        want = oracle.jacobi_f32(g, bcs[i], iters).astype(np.float64)
+        assert np.array_equal(outs[i], want), f"grid {i}"
