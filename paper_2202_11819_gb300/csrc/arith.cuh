@@ -97,6 +97,19 @@ __device__ __forceinline__ double mean7_seq(double c, double xm, double xp, doub
 // that, and for zero, exact integer division in units of 2^-149. Checked
 // bit for bit against the correctly rounded quotient for every finite
 // binary32 value (tests/test_div7f_exhaustive.py).
+// The common case of div7f (|s| >= 2^-100, s finite), without the branch.
+JAC_HD inline float div7f_fast(float s)
+{
+#if defined(__CUDA_ARCH__)
+    return __fmaf_rn(s, 0x1.24924ap-3f, __fmul_rn(s, -0x1.b6db6ep-28f));
+#else
+    return fmaf(s, 0x1.24924ap-3f, s * -0x1.b6db6ep-28f);
+#endif
+}
+
+// True when div7f_fast(s) may differ from div7f(s).
+JAC_HD inline bool div7f_needs_exact(float s) { return !(fabsf(s) >= 0x1p-100f); }
+
 JAC_HD inline float div7f(float s)
 {
     const float zh = 0x1.24924ap-3f;

@@ -42,6 +42,7 @@ struct BlockDesc {
     double bc[6];     // Dirichlet value per face (used where nbr[f] < 0)
     float bcf[6];     // the same rounded to binary32 (binary32 grids)
     int32_t pad;
+    alignas(8) float bcf2[6][2];  // each binary32 value twice (a constant source for 8-byte pair copies)
 };
 
 // One unit of fused / persistent work: a column tile of one block over the

@@ -529,6 +529,16 @@ __device__ __forceinline__ void cp_async_if(uint32_t dst, const void* src, bool 
         : "memory");
 }
 
+// As cp_async_if, with a compile-time byte offset added to the shared address.
+template <int N, int OFF>
+__device__ __forceinline__ void cp_async_if_off(uint32_t dst, const void* src, bool on)
+{
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q cp.async.ca.shared.global [%0+%4], [%1], %3;\n\t}\n" ::"r"(dst),
+        "l"(src), "r"((int)on), "n"(N), "n"(OFF)
+        : "memory");
+}
+
 template <typename T, bool PULL, bool CG, int RD, int TW>
 __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
                                  const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
@@ -816,11 +826,262 @@ __device__ void tile_engine_ring(T* __restrict__ pool, const BlockDesc* __restri
     __syncthreads();  // the ring is free for the next unit
 }
 
+// ------------------------------------------- two-column ring engine (binary32)
+// The ring engine with each thread owning an x-adjacent pair of columns:
+// 8-byte copies and loads for the pair, 4-byte loads for its two outer x
+// neighbours, so a cell costs half the shared-memory instructions. A tile is
+// TW x (1024 / TW) cells. Plane rows are laid out [pad, left halo, TW
+// interior, right halo, pad] so every pair sits on an 8-byte boundary. Used
+// when the block's x extent is even (pairs never straddle the block edge).
+constexpr int kR2Batch = 4, kR2Ahead = 2;
+constexpr int kR2Ring = (kR2Ahead + 3) * kR2Batch;
+
+template <int TW>
+__host__ __device__ constexpr int ring2_rows()
+{
+    return 2 * kThreads / TW;
+}
+
+template <int TW>
+__host__ __device__ constexpr int ring2_plane()
+{
+    return (ring2_rows<TW>() + 2) * (TW + 4) + 2;  // + one pair written by threads without a halo slot
+}
+
+template <int TW>
+__host__ __device__ constexpr int ring2_bytes()
+{
+    return kR2Ring * ring2_plane<TW>() * (int)sizeof(float);
+}
+
+// Where a pair of x-adjacent cells (x, x+1) lives along z (x even, both in
+// the block or both in one neighbouring block); a Dirichlet constant is read
+// from its duplicated form.
+__device__ __forceinline__ Src<float> pair_source(const float* pool, const BlockDesc* desc, const BlockDesc& d, int p,
+                                                  int x, int y)
+{
+    Src<float> s = xy_source<float, true>(pool, desc, d, p, x, y);
+    if (s.stride == 0) s.p = d.bcf2[s.p - d.bcf];
+    return s;
+}
+
+__device__ __forceinline__ float2 ld2(const float* p) { return *(const float2*)p; }
+__device__ __forceinline__ float2 ldcg2(const float* p) { return __ldcg((const float2*)p); }
+
+template <bool CG, int TW>
+__device__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p, int x0,
+                                  int y0, int z0, int z1, unsigned char* smraw)
+{
+    using T = float;
+    constexpr int kB = kR2Batch, kP = kR2Ahead, RD = kR2Ring, kNB = RD / kB;
+    constexpr int kTPR = TW / 2, kTY = ring2_rows<TW>(), kSW = TW + 4, kPl = ring2_plane<TW>();
+    constexpr uint32_t kPlB = kPl * sizeof(T);
+    static_assert(RD % kB == 0, "ring of whole batches");
+    T* const ring = (T*)smraw;  // [RD][kPl]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int tid = threadIdx.x, tx = tid % kTPR, ty = tid / kTPR;
+    const int x = x0 + 2 * tx, y = y0 + ty;  // the pair (x, y), (x + 1, y)
+    const int64_t plane = d.plane;
+    auto ldp = [&](const T* q) { return CG ? ldcg2(q) : ld2(q); };
+
+    // own stream: an interior pair (k1); a pair of the y-halo row inside the
+    // tile (k2p, 8-byte copies); the x-halo column inside the tile (k2s, the
+    // pair's first cell, 4-byte copies)
+    const bool k1 = x < bx && y < by;
+    const bool k2p = y == by && x < bx;
+    const bool k2s = x == bx && y < by;
+    const T* op = pool;
+    int64_t ostr = 0;
+    float2 zm = make_float2(0.f, 0.f), zhiv = zm;
+    T* out = pool;
+    if (k1) {
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        op = col + z0 * plane;
+        ostr = plane;
+        out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
+        if (z0 > 0) zm = ldp(col + (z0 - 1) * plane);
+        else if (d.nbr[4] < 0) zm = make_float2(d.bcf[4], d.bcf[4]);
+        else {
+            const BlockDesc& n = desc[d.nbr[4]];
+            zm = ldp(pool + cell_index<T>(n, p, x, y, n.ext[2] - 1));
+        }
+        if (z1 < bz) zhiv = ldp(col + z1 * plane);
+        else if (d.nbr[5] < 0) zhiv = make_float2(d.bcf[5], d.bcf[5]);
+        else zhiv = ldp(pool + cell_index<T>(desc[d.nbr[5]], p, x, y, 0));
+    } else if (k2p) {
+        const Src<T> s = pair_source(pool, desc, d, p, x, y);
+        op = s.p + z0 * s.stride;
+        ostr = s.stride;
+    } else if (k2s) {
+        const Src<T> s = xy_source<T, true>(pool, desc, d, p, x, y);
+        op = s.p + z0 * s.stride;
+        ostr = s.stride;
+    }
+    const bool own8 = k1 || k2p, own4 = k2s;
+    const int own = (ty + 1) * kSW + 2 * tx + 2;
+
+    // halo-ring slots: top and bottom rows as pairs (8 bytes), left and right
+    // columns as single cells (4 bytes); threads without one use the dummy pair
+    bool h8 = false, h4 = false;
+    int hslot = kPl - 2;
+    const T* hp = pool;
+    int64_t hstr = 0;
+    if (tid < 2 * kTPR + 2 * kTY) {
+        int hx, hy, slot;
+        bool pair, valid;
+        if (tid < kTPR) {
+            hx = x0 + 2 * tid;
+            hy = y0 - 1;
+            slot = 2 * tid + 2;
+            pair = true;
+            valid = hx < bx;
+        } else if (tid < 2 * kTPR) {
+            const int c = tid - kTPR;
+            hx = x0 + 2 * c;
+            hy = y0 + kTY;
+            slot = (kTY + 1) * kSW + 2 * c + 2;
+            pair = true;
+            valid = hx < bx && hy <= by;
+        } else if (tid < 2 * kTPR + kTY) {
+            const int r = tid - 2 * kTPR;
+            hx = x0 - 1;
+            hy = y0 + r;
+            slot = (r + 1) * kSW + 1;
+            pair = false;
+            valid = hy < by;
+        } else {
+            const int r = tid - 2 * kTPR - kTY;
+            hx = x0 + TW;
+            hy = y0 + r;
+            slot = (r + 1) * kSW + TW + 2;
+            pair = false;
+            valid = hy < by && hx <= bx;
+        }
+        if (valid) {
+            const Src<T> hs = pair ? pair_source(pool, desc, d, p, hx, hy) : xy_source<T, true>(pool, desc, d, p, hx, hy);
+            hp = hs.p + z0 * hs.stride;
+            hstr = hs.stride;
+            hslot = slot;
+            h8 = pair;
+            h4 = !pair;
+        }
+    }
+    const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+    const uint32_t own_s = ring_s + own * sizeof(T);
+    const uint32_t halo_s = ring_s + hslot * sizeof(T);
+    const bool halo_warp = (tid & ~31) < 2 * kTPR + 2 * kTY;  // warp-uniform
+
+    int cq = z0;  // the next plane to copy
+    // copy batch into ring slots sb .. sb + kB - 1 (sb a multiple of kB)
+    auto copy_batch = [&](auto full_c, int sb) {
+        constexpr bool FULL = decltype(full_c)::value;
+        const uint32_t so = (uint32_t)sb * kPlB;
+        const uint32_t od = own_s + so, hd = halo_s + so;
+        [&]<int... I>(std::integer_sequence<int, I...>) {
+            ((cp_async_if_off<8, I * (int)kPlB>(od, op + I * ostr, own8 && (FULL || cq + I < z1)),
+              cp_async_if_off<4, I * (int)kPlB>(od, op + I * ostr, own4 && (FULL || cq + I < z1))),
+             ...);
+        }(std::make_integer_sequence<int, kB>{});
+        op += kB * ostr;
+        if (halo_warp) {
+            [&]<int... I>(std::integer_sequence<int, I...>) {
+                ((cp_async_if_off<8, I * (int)kPlB>(hd, hp + I * hstr, h8 && (FULL || cq + I < z1)),
+                  cp_async_if_off<4, I * (int)kPlB>(hd, hp + I * hstr, h4 && (FULL || cq + I < z1))),
+                 ...);
+            }(std::make_integer_sequence<int, kB>{});
+            hp += kB * hstr;
+        }
+        cq += kB;
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int m = 0; m <= kP; ++m) copy_batch(std::false_type{}, m * kB);
+
+    const T* const rd = ring + own;  // the pair of the plane in slot q: rd[q * kPl]
+    cp_async_wait<kP>();
+    __syncthreads();
+    float2 c = ld2(rd);
+    // Batch j computes planes k0 .. k0+kB-1 (slots q0 ..) and reads plane
+    // k0+kB too; it first issues copy batch j + kP + 1 into slots sb ..
+    int q0 = 0, sb = (kP + 1) * kB;
+    auto batch = [&](auto full_c, int k0) {
+        constexpr bool FULL = decltype(full_c)::value;
+        copy_batch(full_c, sb);
+        cp_async_wait<kP>();
+        __syncthreads();
+        const T* const p0 = rd + q0 * kPl;
+        const int qe = q0 + kB == RD ? 0 : q0 + kB;  // slot of plane k0 + kB
+#pragma unroll
+        for (int i = 0; i < kB; ++i) {
+            const int k = k0 + i;
+            if (FULL || k < z1) {
+                const T* pl = p0 + i * kPl;
+                const T* pn = i + 1 < kB ? pl + kPl : rd + qe * kPl;
+                const float2 zp = (FULL || k + 1 < z1) ? ld2(pn) : zhiv;
+                const float xm0 = pl[-1], xp1 = pl[2];
+                const float2 ym = ld2(pl - kSW), yp = ld2(pl + kSW);
+                float s0 = __fadd_rn(c.x, xm0);
+                s0 = __fadd_rn(s0, c.y);
+                s0 = __fadd_rn(s0, ym.x);
+                s0 = __fadd_rn(s0, yp.x);
+                s0 = __fadd_rn(s0, zm.x);
+                s0 = __fadd_rn(s0, zp.x);
+                float s1 = __fadd_rn(c.y, c.x);
+                s1 = __fadd_rn(s1, xp1);
+                s1 = __fadd_rn(s1, ym.y);
+                s1 = __fadd_rn(s1, yp.y);
+                s1 = __fadd_rn(s1, zm.y);
+                s1 = __fadd_rn(s1, zp.y);
+                float2 o = make_float2(div7f_fast(s0), div7f_fast(s1));
+                // the exact small-value path, for the warp only when a lane needs it
+                if (__any_sync(0xffffffffu, k1 && (div7f_needs_exact(s0) || div7f_needs_exact(s1)))) {
+                    o.x = div7f(s0);
+                    o.y = div7f(s1);
+                }
+                if (k1) *(float2*)out = o;
+                out += plane;
+                zm = c;
+                c = zp;
+            }
+        }
+        q0 = qe;
+        sb = sb + kB == RD ? 0 : sb + kB;
+    };
+    int k0 = z0;
+    // a FULL batch: its planes, the plane above them and its copies (up to
+    // plane k0 + (kP + 2) kB - 1) all lie inside the range
+    for (; k0 + (kP + 2) * kB <= z1; k0 += kB) batch(std::true_type{}, k0);
+    for (; k0 < z1; k0 += kB) batch(std::false_type{}, k0);
+    cp_async_wait<0>();
+    __syncthreads();  // the ring is free for the next unit
+}
+
+// A binary32 unit (TW x 1024/TW cells): the two-column engine when the
+// block's x extent is even, else the scalar ring engine on its two halves.
+template <bool CG, int TW>
+__device__ __forceinline__ void f32_unit(float* pool, const BlockDesc* desc, int b, int p, int x0, int y0, int z0,
+                                         int z1)
+{
+    if ((desc[b].ext[0] & 1) == 0) {
+        tile_engine_ring2<CG, TW>(pool, desc, b, p, x0, y0, z0, z1, jac_dyn_sm);
+    } else {
+        tile_engine_ring<float, true, CG, TW>(pool, desc, b, p, x0, y0, z0, z1, jac_dyn_sm);
+        tile_engine_ring<float, true, CG, TW>(pool, desc, b, p, x0, y0 + kThreads / TW, z0, z1, jac_dyn_sm);
+    }
+}
+
+template <int TW>
+__host__ __device__ constexpr int f32_unit_bytes()
+{
+    return ring2_bytes<TW>() > seq_engine_bytes<float, TW>() ? ring2_bytes<TW>() : seq_engine_bytes<float, TW>();
+}
+
 template <typename T, int TW>
-__global__ void __launch_bounds__(kThreads, 3) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
+__global__ void __launch_bounds__(kThreads, 2) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
 {
     const TileUnit u = units[blockIdx.x];
-    tile_engine_ring<T, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
+    f32_unit<false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
 }
 
 template <typename T, int OP, int TW>
@@ -882,7 +1143,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
 template <typename T, int OP, int TW, bool RING>
-__global__ void __launch_bounds__(kThreads, RING ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
@@ -934,8 +1195,7 @@ __global__ void __launch_bounds__(kThreads, RING ? 3 : 2)
         if constexpr (RING) {
             // L1-allocating copies are safe here: the acquire and the
             // barrier above order them after the neighbours' releases
-            tile_engine_ring<T, true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1,
-                                                jac_dyn_sm);
+            f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
         } else {
             if constexpr (OP == OP_EXACT)
                 tile_engine_pair<T, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
@@ -962,8 +1222,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
     __shared__ SlowList slow;
     __shared__ double red[kThreads];
     const TileUnit u = units[blockIdx.x];
-    const double acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
-                                                                         p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+    double acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                   u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+    if constexpr (sizeof(T) == 4) {
+        // a binary32 unit is two engine tiles tall
+        __syncthreads();
+        acc += tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                 u.x0, u.y0 + kThreads / TW, u.z0, u.z1, jac_dyn_sm,
+                                                                 &slow);
+    }
     const int tid = threadIdx.x;
     red[tid] = acc;
     __syncthreads();
@@ -1143,7 +1410,7 @@ __global__ void k_init_ghosts(T* pool, const BlockDesc* desc)
 
 // ---------------------------------------------------------------- launchers
 
-int tile_rows(int tw) { return kThreads / tw; }
+int tile_rows(int tw, bool f32) { return (f32 ? 2 : 1) * kThreads / tw; }
 int engine_threads() { return kThreads; }
 bool tile_width_supported(int tw) { return tw == 16 || tw == 32 || tw == 64; }
 
@@ -1197,7 +1464,7 @@ static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
         }
     }
     if constexpr (sizeof(T) == 4)
-        k_fused_ring<T, TW><<<a.nunits, kThreads, seq_engine_bytes<T, TW>(), s>>>((T*)a.pool, a.desc, a.units, p);
+        k_fused_ring<T, TW><<<a.nunits, kThreads, f32_unit_bytes<TW>(), s>>>((T*)a.pool, a.desc, a.units, p);
     else
         k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
 }
@@ -1229,7 +1496,7 @@ int persistent_block_threads() { return kThreads; }
 template <int TW>
 static int persistent_bytes_t(int dtype_f32, int arith)
 {
-    if (dtype_f32) return seq_engine_bytes<float, TW>();
+    if (dtype_f32) return f32_unit_bytes<TW>();
     return arith == 1 ? kernel_bytes<double, OP_EXACT, TW>()
                       : kernel_bytes<double, OP_SEQ, TW>();
 }
@@ -1260,8 +1527,8 @@ static cudaError_t prepare_tw()
     JAC_ALLOW((k_fused_step<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
     JAC_ALLOW((k_persistent<double, OP_EXACT, TW, false>), (kernel_bytes<double, OP_EXACT, TW>()));
     JAC_ALLOW((k_persistent<double, OP_SEQ, TW, false>), (kernel_bytes<double, OP_SEQ, TW>()));
-    JAC_ALLOW((k_fused_ring<float, TW>), (seq_engine_bytes<float, TW>()));
-    JAC_ALLOW((k_persistent<float, OP_SEQ, TW, true>), (seq_engine_bytes<float, TW>()));
+    JAC_ALLOW((k_fused_ring<float, TW>), (f32_unit_bytes<TW>()));
+    JAC_ALLOW((k_persistent<float, OP_SEQ, TW, true>), (f32_unit_bytes<TW>()));
     JAC_ALLOW((k_residual<double, TW>), (engine_bytes<double, OP_RES, TW, kRingRes>()));
     JAC_ALLOW((k_residual<float, TW>), (engine_bytes<float, OP_RES, TW, kRingRes>()));
 #undef JAC_ALLOW
@@ -1287,7 +1554,7 @@ static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith
             return;
         }
     }
-    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? seq_engine_bytes<T, TW>() : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
+    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? f32_unit_bytes<TW>() : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
                                                           q.n_iters, q.done, q.work, q.status, q.wait_ns,
                                                           q.hold_block, q.hold_after);
 }

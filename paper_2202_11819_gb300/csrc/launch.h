@@ -31,7 +31,8 @@ struct PersistentArgs {
     int64_t hold_after;
 };
 
-int tile_rows(int tw);
+// rows of a work unit's tile: 512 / tw (binary64), 1024 / tw (binary32: two columns per thread)
+int tile_rows(int tw, bool f32);
 int engine_threads();
 bool tile_width_supported(int tw);
 int persistent_block_threads();

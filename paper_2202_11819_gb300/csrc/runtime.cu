@@ -328,7 +328,7 @@ void exponent_field_max(const double* bc, int dtype, int32_t& e)
 // per-grid unit ranges.
 int build_units(jac_ctx* h)
 {
-    const int TW = h->tile_w, TH = tile_rows(h->tile_w);
+    const int TW = h->tile_w, TH = tile_rows(h->tile_w, h->dtype == JAC_F32);
     const int64_t nblocks = (int64_t)h->hdesc.size();
     h->ntx.resize(nblocks);
     h->nty.resize(nblocks);
@@ -422,6 +422,7 @@ int64_t instance_geometry(const jac_ctx* h, Instance& I)
                     else d.nbr[f] = (int32_t)(q[0] + (int64_t)I.nb[0] * (q[1] + (int64_t)I.nb[1] * q[2]));
                     d.bc[f] = I.bc[f];
                     d.bcf[f] = (float)I.bc[f];
+                    d.bcf2[f][0] = d.bcf2[f][1] = d.bcf[f];
                 }
                 d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
                 d.plane = (int64_t)d.pitch * (d.ext[1] + 2);
