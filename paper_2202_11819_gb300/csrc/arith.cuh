@@ -609,7 +609,7 @@ JAC_HD inline void sum7(const W96& a, const W96& b, const W96& c, const W96& d, 
 #endif
 }
 
-// RN((c + xm + xp + ym + yp + zm + zp) / 7) from frame values, without
+// RN(S / 7) for the frame sum S = s2:s1:s0 of seven values, without
 // branches. Returns false when the exact per-cell path must be taken (a
 // marker, or a subnormal result).
 //   S (96 bits, below 2^87 unless a marker is present) is normalised so its
@@ -617,17 +617,15 @@ JAC_HD inline void sum7(const W96& a, const W96& b, const W96& c, const W96& d, 
 //   nonzero in-frame value is at least 2^52, so S is then zero or has a
 //   nonzero top word); the bits shifted out become a sticky flag.
 //   Q = floor(N / 7) from a multiply-high by floor(2^64/7), which is exact
-//   or one short, and the remainder against it; Q in [2^60.2, 2^61.2). Q has 61 or 62 bits and is rounded to
-//   53: its last bit lies below the rounding position, so OR-ing the sticky
+//   or one short, and the remainder against it; Q in [2^60.2, 2^61.2). Q
+//   has 61 or 62 bits and is rounded to 53: its last bit lies below the
+//   rounding position, so OR-ing the sticky
 //   information (nonzero remainder or dropped bits) into it lets one correctly
 //   rounded integer -> binary64 conversion round the exact quotient.
 //   S/7 = (Q + fraction) * 2^(L-64) units of 2^(eref-1106): that scale is
 //   added to the exponent field of the converted value.
-JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& ym, const W96& yp, const W96& zm,
-                         const W96& zp, int eref, double& out)
+JAC_HD inline bool mean7_of_sum(uint32_t s0, uint32_t s1, uint32_t s2, int eref, double& out)
 {
-    uint32_t s0, s1, s2;
-    sum7(c, xm, xp, ym, yp, zm, zp, s0, s1, s2);
     const bool marker = s2 >= kMarker;
     const bool z2 = s2 == 0u;
     const uint32_t t2 = z2 ? s1 : s2, t1 = z2 ? s0 : s1, t0 = z2 ? 0u : s0;
@@ -649,6 +647,39 @@ JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& 
     const int biased = (int)(qb >> 52) + adj;
     out = zero ? 0.0 : bitsd(qb + ((uint64_t)(int64_t)adj << 52));
     return !marker && (zero || biased >= 1);
+}
+
+// mean7 on frame values: the sum, then mean7_of_sum.
+JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& ym, const W96& yp, const W96& zm,
+                         const W96& zp, int eref, double& out)
+{
+    uint32_t s0, s1, s2;
+    sum7(c, xm, xp, ym, yp, zm, zp, s0, s1, s2);
+    return mean7_of_sum(s0, s1, s2, eref, out);
+}
+
+// The mean from a sum in the top binades of the frame: 2^80 <= S < 2^93
+// (top word in [2^16, kMarker)), for eref >= 7. Then N = S >> 23 is at
+// least 2^57 and Q = floor(N / 7) at least 2^54, so Q has two bits or more
+// below the binary64 rounding position: one correctly rounded conversion of
+// Q with the sticky bit (bits of S below 2^23, or a remainder) jammed into
+// its last bit rounds the exact mean. The result's exponent field is at
+// least eref - 6 >= 1 (a normal number) and S is not zero, so no per-cell
+// checks remain. The scale 2^(23 + eref - 1106) is the constant scale_hi =
+// (uint32_t)(eref - 1083) << 20 added to the high word of the conversion.
+JAC_HD inline bool sum_in_top(uint32_t s2) { return s2 - 65536u < kMarker - 65536u; }
+
+JAC_HD inline double mean7_top(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t scale_hi)
+{
+    const uint64_t N = ((uint64_t)fsr(s1, s2, 23) << 32) | fsr(s0, s1, 23);
+    const bool st0 = (s0 & 0x7FFFFFu) != 0u;
+    const uint64_t Qa = umulhi64(N, 0x2492492492492492ull);
+    const uint32_t Ra = (uint32_t)N - 7u * (uint32_t)Qa;
+    const uint32_t fix = Ra >= 7u ? 1u : 0u;
+    const uint64_t Q = Qa + fix;
+    const uint32_t R = Ra - 7u * fix;
+    const uint64_t qj = Q | ((R != 0u || st0) ? 1ull : 0ull);
+    return bitsd(dbits(u64_to_double_rn(qj)) + ((uint64_t)scale_hi << 32));
 }
 
 // RN(xm + xp + ym + yp + zm + zp - 6c) from frame values. Returns false for

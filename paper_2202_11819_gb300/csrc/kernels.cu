@@ -555,6 +555,8 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     const int eref = frame_e[d.inst] + 1;
+    const bool top_ok = eref >= 7;                          // frame::mean7_top applies
+    const uint32_t scale_hi = (uint32_t)(eref - 1083) << 20;  // its scale 2^(23 + eref - 1106)
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const int x = x0 + tx, y = y0 + ty;
     const int64_t plane = d.plane;
@@ -636,9 +638,20 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         }
         __syncthreads();
         double o0, o1 = 0.0;
-        bool ok0 = frame::mean7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, eref, o0);
-        bool ok1 = true;
-        if (TWO) ok1 = frame::mean7(c0, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], wc, c1, eref, o1);
+        bool ok0 = true, ok1 = true;
+        uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 65536u;
+        frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
+        if (TWO) frame::sum7(c0, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], wc, c1, e0, e1, e2);
+        // the fixed-shift mean when every computing lane's sums lie in the
+        // top binades of the frame (nearly always), else the general one
+        const bool top = top_ok && frame::sum_in_top(a2) && frame::sum_in_top(e2);
+        if (__all_sync(0xffffffffu, top || !k1)) {
+            o0 = frame::mean7_top(a0, a1, a2, scale_hi);
+            if (TWO) o1 = frame::mean7_top(e0, e1, e2, scale_hi);
+        } else {
+            ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
+            if (TWO) ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
+        }
         if (k1 && ok0) out[0] = (T)o0;
         if (TWO && k1 && ok1) out[plane] = (T)o1;
         if (k1 && !(ok0 && ok1)) {

@@ -38,3 +38,17 @@ extern "C" void host_frame_sum7(const double* v, int eref, uint32_t* s)
     for (int i = 0; i < 7; ++i) w[i] = of(v[i], eref);
     sum7(w[0], w[1], w[2], w[3], w[4], w[5], w[6], s[0], s[1], s[2]);
 }
+
+// The top-binade fast path of the mean: 1 and the mean when the frame sum of
+// the seven values qualifies (sum_in_top, eref >= 7), else 0.
+extern "C" int host_frame_mean7_top(const double* v, int eref, double* out)
+{
+    using namespace jac::frame;
+    W96 w[7];
+    for (int i = 0; i < 7; ++i) w[i] = of(v[i], eref);
+    uint32_t s0, s1, s2;
+    sum7(w[0], w[1], w[2], w[3], w[4], w[5], w[6], s0, s1, s2);
+    if (eref < 7 || !sum_in_top(s2)) return 0;
+    *out = mean7_top(s0, s1, s2, (uint32_t)(eref - 1083) << 20);
+    return 1;
+}

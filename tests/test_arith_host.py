@@ -203,3 +203,88 @@ def test_grid_frame_tiny_frames_decline_or_match(host_lib):
             if host_lib.host_frame_mean7(a.ctypes.data, eref, ctypes.byref(out)):
                 want = oracle.exact_mean7(a)
                 assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (list(v), eref)
+
+
+def test_grid_frame_mean7_top_binades_fast_path(host_lib):
+    """The fixed-shift mean for sums in the top binades of the frame equals
+    the correctly rounded mean, and covers typical data."""
+    host_lib.host_frame_mean7_top.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    host_lib.host_frame_mean7_top.restype = ctypes.c_int
+    rng = np.random.default_rng(13)
+    out = ctypes.c_double()
+    hits = total = 0
+    for v in mean_cases(rng):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        E = max(exp_field(x) for x in a)
+        for extra in (1, 2, 5, 8, 20):
+            eref = max(E, 0) + extra
+            total += 1
+            if host_lib.host_frame_mean7_top(a.ctypes.data, eref, ctypes.byref(out)):
+                hits += 1
+                want = oracle.exact_mean7(a)
+                assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (v, eref)
+    # ties and near-ties at the rounding point with large sums
+    for _ in range(3000):
+        v = 0.5 + rng.integers(0, 2 ** 20, size=7) * 2.0 ** -53
+        a = np.ascontiguousarray(v)
+        if host_lib.host_frame_mean7_top(a.ctypes.data, 1024, ctypes.byref(out)):
+            hits += 1
+            assert out.value == oracle.exact_mean7(a)
+    ok = 0
+    for _ in range(3000):
+        a = np.ascontiguousarray(rng.random(7))
+        ok += host_lib.host_frame_mean7_top(a.ctypes.data, 1024, ctypes.byref(out))
+    assert ok > 2900
+    assert hits > total // 4
+
+
+
+def tie_cases(rng, n):
+    """Triples of seven doubles around a binary64 midpoint t in [0.5, 1):
+    the exact mean is t (a tie), or t plus or minus 2^-70 / 7, where the bits
+    that decide the rounding lie far below the 53rd and below the top 64 bits
+    of the frame sum. Values: five in [0.5, 1), one in [0.25, 0.5) and
+    w = 2^-20 (+- 2^-70)."""
+    out = []
+    w = Fraction(1, 2 ** 20)
+    eps = Fraction(1, 2 ** 70)
+    while len(out) < 3 * n:
+        t = Fraction(2 * int(rng.integers(2 ** 52, 2 ** 53)) + 1, 2 ** 54)  # odd multiple of 2^-54 in [0.5, 1)
+        target = 7 * t - w
+        v6 = Fraction(int(rng.integers(2 ** 52, 2 ** 53)), 2 ** 54)
+        if ((target - v6) * 2 ** 53).denominator != 1:
+            v6 += Fraction(1, 2 ** 54)
+        rest = target - v6
+        vs = [Fraction(int(rng.integers(2 ** 52, 2 ** 53)), 2 ** 53) for _ in range(4)]
+        last = rest - sum(vs)
+        if not (Fraction(1, 2) <= last < 1):
+            continue
+        base = [float(x) for x in vs + [last, v6]]
+        for d in (0, 1, -1):
+            vals = base + [float(w + d * eps)]
+            assert sum(Fraction(x) for x in vals) == 7 * t + d * eps
+            out.append(vals)
+    return out
+
+
+def test_grid_frame_mean7_ties_and_sticky_near_ties(host_lib):
+    """Exact binary64 ties of the mean and near-ties decided only by bits far
+    below the rounding position: both frame paths against the oracle."""
+    host_lib.host_frame_mean7_top.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    host_lib.host_frame_mean7_top.restype = ctypes.c_int
+    rng = np.random.default_rng(14)
+    out = ctypes.c_double()
+    n_top = n_gen = 0
+    for vals in tie_cases(rng, 400):
+        a = np.ascontiguousarray(vals, dtype=np.float64)
+        want = oracle.exact_mean7(a)
+        exact = sum(Fraction(float(x)) for x in a) / 7
+        assert want == float(exact)  # the oracle's rounding of the exact mean
+        assert (exact * 2 ** 53).denominator != 1  # not representable: a tie or a near-tie
+        if host_lib.host_frame_mean7_top(a.ctypes.data, 1024, ctypes.byref(out)):
+            n_top += 1
+            assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), vals
+        if host_lib.host_frame_mean7(a.ctypes.data, 1024, ctypes.byref(out)):
+            n_gen += 1
+            assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), vals
+    assert n_top == n_gen == 1200
