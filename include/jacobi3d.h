@@ -113,6 +113,10 @@ typedef struct {
     int32_t trial_tile_w[16];
     int32_t trial_zdepth[16];
     double trial_ms_per_iter[16];
+    int32_t n_classes;           /* block-width classes refined (0: one width for all blocks) */
+    int32_t class_block_x[16];   /* a class: blocks of this x extent ...                      */
+    int32_t class_tile_w[16];    /* ... run with this tile width                              */
+    double ms_per_iter_classes;  /* ms per iteration after the per-class refinement           */
 } jac_tune_t;
 
 /* ------------------------------------------------------------------ */
@@ -247,15 +251,25 @@ int jac_write_instance_device(jac_ctx *h, int32_t i, const void *dev, size_t n_c
 int jac_read_instance(jac_ctx *h, int32_t i, double *host, size_t n_cells);
 int jac_read_instance_device(jac_ctx *h, int32_t i, void *dev, size_t n_cells, int32_t dtype);
 
-/* Tile shape of the update engine: 512 threads as tile_w x (512/tile_w)
- * columns (tile_w 16, 32 or 64), each work unit covering zdepth planes of a
- * block (0: all of them). Results do not depend on it. Synchronises. */
+/* Tile shape of the update engine: 512 threads over tile_w x (512/tile_w)
+ * columns (binary64) or tile_w x (1024/tile_w) columns (binary32, two per
+ * thread), tile_w 16, 32 or 64, each work unit covering zdepth planes of a
+ * block (0: all of them). Clears the per-class widths. Results do not depend
+ * on it. Synchronises. */
 int jac_set_tile(jac_ctx *h, int32_t tile_w, int32_t zdepth);
 
+/* Tile width for the blocks whose x extent is block_x (a block-width class),
+ * overriding jac_set_tile's width for them; tile_w 0 removes the override.
+ * Results do not depend on it. Synchronises. */
+int jac_set_tile_class(jac_ctx *h, int32_t block_x, int32_t tile_w);
+
 /* Autotuner: time trial_iters iterations of the current mode for every tile
- * width and z depth, keep the fastest (reported in *result, may be NULL),
- * and restore the grid and iteration count exactly as they were. Needs
- * temporary device memory for one copy of the block storage. Synchronises. */
+ * width and z depth and keep the fastest; when the blocks come in several x
+ * extents, then try the other widths class by class (largest classes first,
+ * at most 16) and keep each change that makes the whole launch faster.
+ * Reports the choice in *result (may be NULL) and restores the grid and
+ * iteration count exactly as they were. Needs temporary device memory for
+ * one copy of the block storage. Synchronises. */
 int jac_autotune(jac_ctx *h, int32_t trial_iters, jac_tune_t *result);
 
 /* Wait for the context's stream and report a device-side wait timeout

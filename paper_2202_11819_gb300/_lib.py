@@ -78,6 +78,10 @@ class jac_tune_t(ctypes.Structure):
         ("trial_tile_w", ctypes.c_int32 * 16),
         ("trial_zdepth", ctypes.c_int32 * 16),
         ("trial_ms_per_iter", ctypes.c_double * 16),
+        ("n_classes", ctypes.c_int32),
+        ("class_block_x", ctypes.c_int32 * 16),
+        ("class_tile_w", ctypes.c_int32 * 16),
+        ("ms_per_iter_classes", ctypes.c_double),
     ]
 
 
@@ -145,6 +149,7 @@ _SIGS = {
     "jac_residual_instances": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "jac_residual_instances_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "jac_set_tile": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "jac_set_tile_class": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "jac_autotune": ([ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(jac_tune_t)], ctypes.c_int),
     "jac_storage_bytes": ([ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                            ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -367,12 +372,21 @@ def jac_set_tile(h, tile_w: int, zdepth: int) -> None:
     _check(load().jac_set_tile(h, int(tile_w), int(zdepth)), "jac_set_tile")
 
 
+def jac_set_tile_class(h, block_x: int, tile_w: int) -> None:
+    _check(load().jac_set_tile_class(h, int(block_x), int(tile_w)), "jac_set_tile_class")
+
+
 def jac_autotune(h, trial_iters: int) -> dict:
     r = jac_tune_t()
     _check(load().jac_autotune(h, int(trial_iters), ctypes.byref(r)), "jac_autotune")
     n = min(r.n_trials, 16)
-    return {"tile_w": r.tile_w, "zdepth": r.zdepth, "ms_per_iter": r.ms_per_iter,
-            "trials": [(r.trial_tile_w[i], r.trial_zdepth[i], r.trial_ms_per_iter[i]) for i in range(n)]}
+    out = {"tile_w": r.tile_w, "zdepth": r.zdepth, "ms_per_iter": r.ms_per_iter,
+           "trials": [(r.trial_tile_w[i], r.trial_zdepth[i], r.trial_ms_per_iter[i]) for i in range(n)],
+           "n_trials": r.n_trials}
+    if r.n_classes:
+        out["classes"] = [(r.class_block_x[i], r.class_tile_w[i]) for i in range(min(r.n_classes, 16))]
+        out["ms_per_iter_classes"] = r.ms_per_iter_classes
+    return out
 
 
 def _i64x3(dims):

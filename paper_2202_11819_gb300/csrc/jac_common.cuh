@@ -46,11 +46,13 @@ struct BlockDesc {
 };
 
 // One unit of fused / persistent work: a column tile of one block over the
-// planes z0 .. z1-1.
+// planes z0 .. z1-1, tw columns wide.
 struct TileUnit {
     int32_t block;
     int16_t x0, y0;
     int16_t z0, z1;
+    int16_t tw;   // tile width: 16, 32 or 64 columns
+    int16_t pad;
 };
 
 // Error word values written by kernels (read back by the host at syncs).

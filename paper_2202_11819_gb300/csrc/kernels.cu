@@ -1090,11 +1090,24 @@ __host__ __device__ constexpr int f32_unit_bytes()
     return ring2_bytes<TW>() > seq_engine_bytes<float, TW>() ? ring2_bytes<TW>() : seq_engine_bytes<float, TW>();
 }
 
-template <typename T, int TW>
+// Work units carry their tile width (16, 32 or 64, chosen per block-width
+// class by the autotuner): the unit kernels dispatch on it.
+template <typename F>
+__device__ __forceinline__ void with_tw(int tw, F&& f)
+{
+    if (tw == 16) f(std::integral_constant<int, 16>{});
+    else if (tw == 64) f(std::integral_constant<int, 64>{});
+    else f(std::integral_constant<int, 32>{});
+}
+
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
 {
     const TileUnit u = units[blockIdx.x];
-    f32_unit<false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
+    with_tw(u.tw, [&](auto tw_c) {
+        constexpr int TW = decltype(tw_c)::value;
+        f32_unit<false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
+    });
 }
 
 template <typename T, int OP, int TW>
@@ -1112,18 +1125,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_stencil_block(T* pool, const Bl
                                                        &slow);
 }
 
-template <typename T, int OP, int TW>
+template <typename T, int OP>
 __global__ void __launch_bounds__(kThreads, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p)
 {
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
-    if constexpr (OP == OP_EXACT)
-        tile_engine_pair<T, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
-                                                       jac_dyn_sm, &slow);
-    else
-        tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
-                                                      jac_dyn_sm, &slow);
+    with_tw(u.tw, [&](auto tw_c) {
+        constexpr int TW = decltype(tw_c)::value;
+        if constexpr (OP == OP_EXACT)
+            tile_engine_pair<T, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                           jac_dyn_sm, &slow);
+        else
+            tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                          jac_dyn_sm, &slow);
+    });
 }
 
 __device__ __forceinline__ uint64_t global_ns()
@@ -1155,7 +1171,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // overwrites (buffer p^1 held iteration t-1). The seven counters are polled
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
-template <typename T, int OP, int TW, bool RING>
+template <typename T, int OP, bool RING>
 __global__ void __launch_bounds__(kThreads, 2)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
@@ -1205,18 +1221,20 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (s_stop) break;
         // take the next unit now; its index is read after this one finishes
         if (tid == 0) s_next = ld_volatile(&st->abort) ? total : (long long)atomicAdd(work, 1ull);
-        if constexpr (RING) {
-            // L1-allocating copies are safe here: the acquire and the
-            // barrier above order them after the neighbours' releases
-            f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
-        } else {
-            if constexpr (OP == OP_EXACT)
+        with_tw(u.tw, [&](auto tw_c) {
+            constexpr int TW = decltype(tw_c)::value;
+            if constexpr (RING) {
+                // L1-allocating copies are safe here: the acquire and the
+                // barrier above order them after the neighbours' releases
+                f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
+            } else if constexpr (OP == OP_EXACT) {
                 tile_engine_pair<T, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
                                                               u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
-            else
+            } else {
                 tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
                                                              u.z0, u.z1, jac_dyn_sm, &slow);
-        }
+            }
+        });
         __syncthreads();
         if (tid == 0 && !(u.block == hold_block && t >= hold_after)) {
             __threadfence();
@@ -1227,7 +1245,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 // Residual: per CTA the sum over its tile of L^2 (L the exact Laplacian term
 // rounded once), in a fixed order (per thread over k, then a fixed tree).
-template <typename T, int TW>
+template <typename T>
 __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const BlockDesc* desc,
                                                           const int32_t* frame_e, const TileUnit* units, int p,
                                                           double* partials)
@@ -1235,15 +1253,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
     __shared__ SlowList slow;
     __shared__ double red[kThreads];
     const TileUnit u = units[blockIdx.x];
-    double acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                   u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
-    if constexpr (sizeof(T) == 4) {
-        // a binary32 unit is two engine tiles tall
-        __syncthreads();
-        acc += tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                 u.x0, u.y0 + kThreads / TW, u.z0, u.z1, jac_dyn_sm,
-                                                                 &slow);
-    }
+    double acc = 0.0;
+    with_tw(u.tw, [&](auto tw_c) {
+        constexpr int TW = decltype(tw_c)::value;
+        acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+        if constexpr (sizeof(T) == 4) {
+            // a binary32 unit is two engine tiles tall
+            __syncthreads();
+            acc += tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
+                                                                     p, u.x0, u.y0 + kThreads / TW, u.z0, u.z1,
+                                                                     jac_dyn_sm, &slow);
+        }
+    });
     const int tid = threadIdx.x;
     red[tid] = acc;
     __syncthreads();
@@ -1467,58 +1489,54 @@ cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, 
     return cudaGetLastError();
 }
 
-template <typename T, int TW>
-static void fused_step_t(const LaunchArgs& a, int arith, int p, cudaStream_t s)
+// Dynamic shared memory of the unit kernels: the largest over the three tile
+// widths (units of one launch may use different widths).
+template <typename T, int OP>
+static constexpr int unit_bytes()
 {
-    if constexpr (sizeof(T) == 8) {
-        if (arith == 1) {
-            k_fused_step<T, OP_EXACT, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
-            return;
-        }
+    if constexpr (sizeof(T) == 4 && OP == OP_SEQ) {
+        constexpr int a = f32_unit_bytes<16>(), b = f32_unit_bytes<32>(), c = f32_unit_bytes<64>();
+        return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    } else {
+        constexpr int a = kernel_bytes<T, OP, 16>(), b = kernel_bytes<T, OP, 32>(), c = kernel_bytes<T, OP, 64>();
+        return a > b ? (a > c ? a : c) : (b > c ? b : c);
     }
-    if constexpr (sizeof(T) == 4)
-        k_fused_ring<T, TW><<<a.nunits, kThreads, f32_unit_bytes<TW>(), s>>>((T*)a.pool, a.desc, a.units, p);
-    else
-        k_fused_step<T, OP_SEQ, TW><<<a.nunits, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, p);
+}
+
+template <typename T>
+static constexpr int residual_bytes()
+{
+    constexpr int a = engine_bytes<T, OP_RES, 16, kRingRes>(), b = engine_bytes<T, OP_RES, 32, kRingRes>(),
+                  c = engine_bytes<T, OP_RES, 64, kRingRes>();
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
 {
-    if (dtype_f32) JAC_TW_DISPATCH(a.tile_w, (fused_step_t<float, TW>(a, arith, p, s)))
-    else JAC_TW_DISPATCH(a.tile_w, (fused_step_t<double, TW>(a, arith, p, s)))
+    if (dtype_f32)
+        k_fused_ring<float><<<a.nunits, kThreads, unit_bytes<float, OP_SEQ>(), s>>>((float*)a.pool, a.desc, a.units, p);
+    else if (arith == 1)
+        k_fused_step<double, OP_EXACT><<<a.nunits, kThreads, unit_bytes<double, OP_EXACT>(), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, p);
+    else
+        k_fused_step<double, OP_SEQ><<<a.nunits, kThreads, unit_bytes<double, OP_SEQ>(), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, p);
     return cudaGetLastError();
 }
 
-template <int TW>
-static const void* persistent_fn(int dtype_f32, int arith)
+const void* persistent_kernel(int dtype_f32, int arith)
 {
-    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, TW, true>;
-    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, TW, false>
-                      : (const void*)k_persistent<double, OP_SEQ, TW, false>;
-}
-
-const void* persistent_kernel(int dtype_f32, int arith, int tw)
-{
-    const void* f = nullptr;
-    JAC_TW_DISPATCH(tw, (f = persistent_fn<TW>(dtype_f32, arith)))
-    return f;
+    if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, true>;
+    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, false>
+                      : (const void*)k_persistent<double, OP_SEQ, false>;
 }
 
 int persistent_block_threads() { return kThreads; }
 
-template <int TW>
-static int persistent_bytes_t(int dtype_f32, int arith)
+int persistent_smem_bytes(int dtype_f32, int arith)
 {
-    if (dtype_f32) return f32_unit_bytes<TW>();
-    return arith == 1 ? kernel_bytes<double, OP_EXACT, TW>()
-                      : kernel_bytes<double, OP_SEQ, TW>();
-}
-
-int persistent_smem_bytes(int dtype_f32, int arith, int tw)
-{
-    int n = 0;
-    JAC_TW_DISPATCH(tw, (n = persistent_bytes_t<TW>(dtype_f32, arith)))
-    return n;
+    if (dtype_f32) return unit_bytes<float, OP_SEQ>();
+    return arith == 1 ? unit_bytes<double, OP_EXACT>() : unit_bytes<double, OP_SEQ>();
 }
 
 template <typename K>
@@ -1536,14 +1554,6 @@ static cudaError_t prepare_tw()
     JAC_ALLOW((k_stencil_block<double, OP_EXACT, TW>), (kernel_bytes<double, OP_EXACT, TW>()));
     JAC_ALLOW((k_stencil_block<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
     JAC_ALLOW((k_stencil_block<float, OP_SEQ, TW>), (kernel_bytes<float, OP_SEQ, TW>()));
-    JAC_ALLOW((k_fused_step<double, OP_EXACT, TW>), (kernel_bytes<double, OP_EXACT, TW>()));
-    JAC_ALLOW((k_fused_step<double, OP_SEQ, TW>), (kernel_bytes<double, OP_SEQ, TW>()));
-    JAC_ALLOW((k_persistent<double, OP_EXACT, TW, false>), (kernel_bytes<double, OP_EXACT, TW>()));
-    JAC_ALLOW((k_persistent<double, OP_SEQ, TW, false>), (kernel_bytes<double, OP_SEQ, TW>()));
-    JAC_ALLOW((k_fused_ring<float, TW>), (f32_unit_bytes<TW>()));
-    JAC_ALLOW((k_persistent<float, OP_SEQ, TW, true>), (f32_unit_bytes<TW>()));
-    JAC_ALLOW((k_residual<double, TW>), (engine_bytes<double, OP_RES, TW, kRingRes>()));
-    JAC_ALLOW((k_residual<float, TW>), (engine_bytes<float, OP_RES, TW, kRingRes>()));
 #undef JAC_ALLOW
     return e;
 }
@@ -1553,41 +1563,46 @@ cudaError_t prepare_kernels()
     cudaError_t e = prepare_tw<16>();
     if (e == cudaSuccess) e = prepare_tw<32>();
     if (e == cudaSuccess) e = prepare_tw<64>();
+#define JAC_ALLOW(K, BYTES) \
+    if (e == cudaSuccess) e = allow_smem(K, BYTES)
+    JAC_ALLOW((k_fused_step<double, OP_EXACT>), (unit_bytes<double, OP_EXACT>()));
+    JAC_ALLOW((k_fused_step<double, OP_SEQ>), (unit_bytes<double, OP_SEQ>()));
+    JAC_ALLOW((k_fused_ring<float>), (unit_bytes<float, OP_SEQ>()));
+    JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes<double, OP_EXACT>()));
+    JAC_ALLOW((k_persistent<double, OP_SEQ, false>), (unit_bytes<double, OP_SEQ>()));
+    JAC_ALLOW((k_persistent<float, OP_SEQ, true>), (unit_bytes<float, OP_SEQ>()));
+    JAC_ALLOW((k_residual<double>), (residual_bytes<double>()));
+    JAC_ALLOW((k_residual<float>), (residual_bytes<float>()));
+#undef JAC_ALLOW
     return e;
-}
-
-template <typename T, int TW>
-static void persistent_t(const LaunchArgs& a, const PersistentArgs& q, int arith, int ctas, cudaStream_t s)
-{
-    if constexpr (sizeof(T) == 8) {
-        if (arith == 1) {
-            k_persistent<T, OP_EXACT, TW, false><<<ctas, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits,
-                                                                    q.p0, q.n_iters, q.done, q.work, q.status,
-                                                                    q.wait_ns, q.hold_block, q.hold_after);
-            return;
-        }
-    }
-    k_persistent<T, OP_SEQ, TW, sizeof(T) == 4><<<ctas, kThreads, sizeof(T) == 4 ? f32_unit_bytes<TW>() : kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0,
-                                                          q.n_iters, q.done, q.work, q.status, q.wait_ns,
-                                                          q.hold_block, q.hold_after);
 }
 
 cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int dtype_f32, int arith, int ctas,
                               cudaStream_t s)
 {
-    if (dtype_f32) JAC_TW_DISPATCH(a.tile_w, (persistent_t<float, TW>(a, q, arith, ctas, s)))
-    else JAC_TW_DISPATCH(a.tile_w, (persistent_t<double, TW>(a, q, arith, ctas, s)))
+    if (dtype_f32)
+        k_persistent<float, OP_SEQ, true><<<ctas, kThreads, unit_bytes<float, OP_SEQ>(), s>>>(
+            (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
+            q.hold_block, q.hold_after);
+    else if (arith == 1)
+        k_persistent<double, OP_EXACT, false><<<ctas, kThreads, unit_bytes<double, OP_EXACT>(), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
+            q.hold_block, q.hold_after);
+    else
+        k_persistent<double, OP_SEQ, false><<<ctas, kThreads, unit_bytes<double, OP_SEQ>(), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
+            q.hold_block, q.hold_after);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
 {
     if (dtype_f32)
-        JAC_TW_DISPATCH(a.tile_w, (k_residual<float, TW><<<a.nunits, kThreads, engine_bytes<float, OP_RES, TW, kRingRes>(), s>>>(
-                                      (const float*)a.pool, a.desc, a.frame, a.units, p, partials)))
+        k_residual<float><<<a.nunits, kThreads, residual_bytes<float>(), s>>>((const float*)a.pool, a.desc, a.frame,
+                                                                             a.units, p, partials);
     else
-        JAC_TW_DISPATCH(a.tile_w, (k_residual<double, TW><<<a.nunits, kThreads, engine_bytes<double, OP_RES, TW, kRingRes>(), s>>>(
-                                      (const double*)a.pool, a.desc, a.frame, a.units, p, partials)))
+        k_residual<double><<<a.nunits, kThreads, residual_bytes<double>(), s>>>((const double*)a.pool, a.desc,
+                                                                               a.frame, a.units, p, partials);
     return cudaGetLastError();
 }
 

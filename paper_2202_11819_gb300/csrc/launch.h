@@ -36,9 +36,9 @@ int tile_rows(int tw, bool f32);
 int engine_threads();
 bool tile_width_supported(int tw);
 int persistent_block_threads();
-const void* persistent_kernel(int dtype_f32, int arith, int tw);
+const void* persistent_kernel(int dtype_f32, int arith);
 // dynamic shared memory of one persistent CTA (for occupancy queries)
-int persistent_smem_bytes(int dtype_f32, int arith, int tw);
+int persistent_smem_bytes(int dtype_f32, int arith);
 // raises the dynamic shared memory limit of every engine kernel on the
 // current device; once per device, before the first launch or capture
 cudaError_t prepare_kernels();

@@ -163,6 +163,8 @@ struct jac_ctx {
     size_t done_cap = 0;
     int tile_w = 32;              // tile width of the update engine
     int zdepth = 0;               // planes per work unit (0: the whole block)
+    // per block-width class (block x extent) tile widths overriding tile_w
+    std::vector<std::pair<int32_t, int32_t>> class_tw;
     int dtype = JAC_F64;
     int esize = 8;
     int mode = JAC_MODE_PERSISTENT;
@@ -326,9 +328,17 @@ void exponent_field_max(const double* bc, int dtype, int32_t& e)
 // tiles times its z chunks, blocks in table order, so each grid's units are
 // contiguous. Uploads the tile table, the per-block unit counts and the
 // per-grid unit ranges.
+// The tile width for blocks of x extent bx: the class override, else the
+// context's width.
+int class_tile_width(const jac_ctx* h, int32_t bx)
+{
+    for (const auto& c : h->class_tw)
+        if (c.first == bx) return c.second;
+    return h->tile_w;
+}
+
 int build_units(jac_ctx* h)
 {
-    const int TW = h->tile_w, TH = tile_rows(h->tile_w, h->dtype == JAC_F32);
     const int64_t nblocks = (int64_t)h->hdesc.size();
     h->ntx.resize(nblocks);
     h->nty.resize(nblocks);
@@ -342,6 +352,7 @@ int build_units(jac_ctx* h)
         slot.push_back((int32_t)ii);
         for (int32_t b = I.b0; b < I.b1; ++b) {
             BlockDesc& d = h->hdesc[b];
+            const int TW = class_tile_width(h, d.ext[0]), TH = tile_rows(TW, h->dtype == JAC_F32);
             h->ntx[b] = (d.ext[0] + TW - 1) / TW;
             h->nty[b] = (d.ext[1] + TH - 1) / TH;
             const int zd = h->zdepth > 0 ? h->zdepth : d.ext[2];
@@ -356,6 +367,8 @@ int build_units(jac_ctx* h)
                         u.y0 = (int16_t)(ty * TH);
                         u.z0 = (int16_t)(zc * zd);
                         u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
+                        u.tw = (int16_t)TW;
+                        u.pad = 0;
                         h->hunits.push_back(u);
                     }
         }
@@ -1158,9 +1171,9 @@ int jac_iterate(jac_ctx* h, int64_t n)
         case JAC_MODE_PERSISTENT: {
             if (h->pctas == 0) {
                 int per_sm = 0, sms = 0;
-                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith, h->tile_w),
+                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
                                                                  persistent_block_threads(),
-                                                                 persistent_smem_bytes(f32, h->arith, h->tile_w)),
+                                                                 persistent_smem_bytes(f32, h->arith)),
                    "occupancy");
                 CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
                 h->pctas = std::max(1, std::min(per_sm * sms, (int)h->hunits.size()));
@@ -1330,16 +1343,40 @@ int jac_set_tile(jac_ctx* h, int32_t tile_w, int32_t zdepth)
     if (rc) return rc;
     if (!tile_width_supported(tile_w)) return fail(JAC_EINVAL, "tile width must be 16, 32 or 64");
     if (zdepth < 0 || zdepth > 256) return fail(JAC_EINVAL, "z depth must be in [0, 256]");
-    if (tile_w == h->tile_w && zdepth == h->zdepth) return JAC_OK;
+    if (tile_w == h->tile_w && zdepth == h->zdepth && h->class_tw.empty()) return JAC_OK;
     CU(cudaStreamSynchronize(h->stream), "tile sync");
     h->tile_w = tile_w;
     h->zdepth = zdepth;
+    h->class_tw.clear();
+    destroy_graphs(h);
+    return build_units(h);
+}
+
+int jac_set_tile_class(jac_ctx* h, int32_t block_x, int32_t tile_w)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (block_x < 1) return fail(JAC_EINVAL, "block x extent must be >= 1");
+    if (tile_w != 0 && !tile_width_supported(tile_w)) return fail(JAC_EINVAL, "tile width must be 0, 16, 32 or 64");
+    CU(cudaStreamSynchronize(h->stream), "tile sync");
+    auto it = std::find_if(h->class_tw.begin(), h->class_tw.end(),
+                           [&](const std::pair<int32_t, int32_t>& c) { return c.first == block_x; });
+    if (tile_w == 0) {
+        if (it != h->class_tw.end()) h->class_tw.erase(it);
+    } else if (it != h->class_tw.end()) {
+        it->second = tile_w;
+    } else {
+        h->class_tw.emplace_back(block_x, tile_w);
+    }
     destroy_graphs(h);
     return build_units(h);
 }
 
 // Time every (tile width, z depth) pair for the current mode on the context
-// itself, keep the fastest, and put the grid back as it was.
+// itself and keep the fastest; then, when the blocks come in several x
+// extents (block-width classes), refine the width class by class (largest
+// classes first), keeping a change only when the whole launch gets faster.
+// The grid and iteration count are put back as they were.
 int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
 {
     int rc = check_ready(h);
@@ -1365,19 +1402,25 @@ int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0), "event");
     CU(cudaEventCreate(&e1), "event");
+    auto time_it = [&](double* per) -> int {
+        int r;
+        if ((r = jac_iterate(h, 1))) return r;  // builds graphs / streams outside the timing
+        cudaEventRecord(e0, h->stream);
+        if ((r = jac_iterate(h, trial_iters))) return r;
+        cudaEventRecord(e1, h->stream);
+        if ((r = read_status(h))) return r;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        *per = (double)ms / trial_iters;
+        return JAC_OK;
+    };
     for (int wi = 0; wi < 3 && !rc; ++wi)
         for (int di = 0; di < 4 && !rc; ++di) {
             const int zd = depths[di];
             if (zd != 0 && zd >= max_bz) continue;
             if ((rc = jac_set_tile(h, widths[wi], zd))) break;
-            if ((rc = jac_iterate(h, 1))) break;  // builds graphs / streams outside the timing
-            cudaEventRecord(e0, h->stream);
-            if ((rc = jac_iterate(h, trial_iters))) break;
-            cudaEventRecord(e1, h->stream);
-            if ((rc = read_status(h))) break;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            const double per = (double)ms / trial_iters;
+            double per = 0.0;
+            if ((rc = time_it(&per))) break;
             if (best.n_trials < 16) {
                 best.trial_tile_w[best.n_trials] = widths[wi];
                 best.trial_zdepth[best.n_trials] = zd;
@@ -1390,9 +1433,44 @@ int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
                 best.zdepth = zd;
             }
         }
+    if (!rc && best.tile_w) rc = jac_set_tile(h, best.tile_w, best.zdepth);
+    best.ms_per_iter_classes = best.ms_per_iter;
+    // block-width classes, largest (most cells) first
+    std::vector<std::pair<int64_t, int32_t>> cls;  // (cells, bx)
+    for (const BlockDesc& d : h->hdesc) {
+        const int64_t cells = (int64_t)d.ext[0] * d.ext[1] * d.ext[2];
+        auto it = std::find_if(cls.begin(), cls.end(),
+                               [&](const std::pair<int64_t, int32_t>& c) { return c.second == d.ext[0]; });
+        if (it == cls.end()) cls.emplace_back(cells, d.ext[0]);
+        else it->first += cells;
+    }
+    std::sort(cls.begin(), cls.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    if (!rc && cls.size() > 1) {
+        double base = 0.0;
+        rc = time_it(&base);
+        for (size_t c = 0; c < cls.size() && c < 16 && !rc; ++c) {
+            const int32_t bx = cls[c].second;
+            int32_t keep = best.tile_w;
+            for (int wi = 0; wi < 3 && !rc; ++wi) {
+                if (widths[wi] == best.tile_w) continue;
+                if ((rc = jac_set_tile_class(h, bx, widths[wi]))) break;
+                double per = 0.0;
+                if ((rc = time_it(&per))) break;
+                best.n_trials += 1;
+                if (per < base) {
+                    base = per;
+                    keep = widths[wi];
+                }
+            }
+            if (!rc) rc = jac_set_tile_class(h, bx, keep == best.tile_w ? 0 : keep);
+            best.class_block_x[best.n_classes] = bx;
+            best.class_tile_w[best.n_classes] = keep;
+            best.n_classes += 1;
+        }
+        best.ms_per_iter_classes = base;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (!rc && best.tile_w) rc = jac_set_tile(h, best.tile_w, best.zdepth);
     cudaMemcpyAsync(h->pool, snap, bytes, cudaMemcpyDeviceToDevice, h->stream);
     cudaFreeAsync(snap, h->stream);
     h->parity = parity0;

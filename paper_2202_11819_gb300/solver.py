@@ -201,6 +201,9 @@ class Jacobi3DBatch:
     def set_tile(self, tile_w, zdepth):
         _lib.jac_set_tile(self.h, tile_w, zdepth)
 
+    def set_tile_class(self, block_x, tile_w):
+        _lib.jac_set_tile_class(self.h, block_x, tile_w)
+
     def autotune(self, trial_iters=4):
         return _lib.jac_autotune(self.h, trial_iters)
 

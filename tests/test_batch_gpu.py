@@ -161,3 +161,54 @@ def test_f32_tile_shapes_and_z_depths_bit_exact(tile_w, zdepth, mode):
     for i, g in enumerate(grids):
         want = oracle.jacobi_f32(g, bcs[i], iters).astype(np.float64)
         assert np.array_equal(outs[i], want), f"grid {i}"
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("mode", ["persistent", "fused"])
+def test_per_class_tile_widths_bit_exact(dtype, mode):
+    """Blocks of different x extents (35, 40, 50) run with different tile
+    widths in one launch; results stay those of the oracle."""
+    dims = [(70, 45, 50), (40, 64, 30), (100, 33, 41)]
+    rng = np.random.default_rng(21)
+    bcs = [tuple(float(v) for v in rng.random(6)) for _ in dims]
+    grids = [synth.grid_uniform01(400 + i, *d) for i, d in enumerate(dims)]
+    if dtype == "f32":
+        grids = [g.astype(np.float32).astype(np.float64) for g in grids]
+    iters = 5
+    with Jacobi3DBatch(dims, (64, 40, 64), dtype=dtype, bcs=bcs, mode=mode) as B:
+        B.set_tile(32, 0)
+        B.set_tile_class(35, 16)
+        B.set_tile_class(50, 64)
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        B.iterate(iters)
+        outs = [B.read(i) for i in range(len(dims))]
+        rhos = B.residuals()
+    for i, g in enumerate(grids):
+        if dtype == "f32":
+            want = oracle.jacobi_f32(g.astype(np.float32), bcs[i], iters).astype(np.float64)
+            assert np.array_equal(outs[i], want), f"grid {i}"
+            # a binary32 grid's boundary values are stored in binary32
+            r = oracle.residual(want, tuple(float(np.float32(v)) for v in bcs[i]))
+        else:
+            want = oracle.jacobi(g, bcs[i], iters, oracle.RULE_EXACT)
+            assert np.array_equal(outs[i], want), f"grid {i}"
+            r = oracle.residual(want, bcs[i])
+        assert abs(rhos[i] - r) <= 1e-12 * r
+
+
+def test_autotune_refines_block_width_classes():
+    dims = synth.batch_instance_dims(12, seed=3)
+    grids = [synth.grid_uniform01(i, *d) for i, d in enumerate(dims)]
+    bc = synth.DIRICHLET_X0
+    with Jacobi3DBatch(dims, (64, 64, 64), bcs=[bc] * len(dims), mode="persistent") as B:
+        for i, g in enumerate(grids):
+            B.write(i, g)
+        res = B.autotune(2)
+        widths = {d[0] if d[0] <= 64 else -(-d[0] // -(-d[0] // 64)) for d in dims}
+        if len(widths) > 1:
+            assert res.get("classes"), res
+            assert all(tw in (16, 32, 64) for _, tw in res["classes"])
+        B.iterate(3)
+        for i in (0, 5, 11):
+            assert np.array_equal(B.read(i), oracle.jacobi(grids[i], bc, 3, oracle.RULE_EXACT))
