@@ -76,6 +76,44 @@ JAC_HD inline int clz32(uint32_t x)  // 32 for x == 0
 
 JAC_HD inline int imax(int a, int b) { return a > b ? a : b; }
 
+JAC_HD inline uint64_t mulhi_u64(uint64_t a, uint64_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// RN(s / 7) for a binary64 s whose exponent field e is in [4, 2046] (so s
+// and the quotient are normal), in integer arithmetic plus one integer ->
+// binary64 conversion. N = significand << 11 lies in [2^63, 2^64); Qa, the
+// high word of N * floor(2^64/7), is floor(N/7) or one less, and has 61 or 62
+// bits, so converting it rounds away its d = 8 or 9 low bits. That rounding
+// equals the rounding of the exact quotient N/7: the two could differ only
+// if a rounding midpoint lay in [Qa, N/7], i.e. if floor(N/7) had its d low
+// bits equal to 2^(d-1). As N is a multiple of 2^11, 7 floor(N/7) + r = N
+// (r < 7) forces floor(N/7) mod 2^d to be 0 modulo 2^(d-1) only together
+// with r = 128 (d = 8) or r = 256 (d = 9), which cannot be; and Qa one less
+// happens only for r <= 1 and steps over no midpoint either. The exponent is
+// then rescaled by e - 1086 and the sign copied. Returns false (out unset)
+// outside that range: zero, subnormals, infinities and NaN. Checked against
+// correctly rounded division on the host (tests/test_arith_host.py).
+JAC_HD inline bool div7d(double s, double& out)
+{
+    const uint64_t b = dbits(s);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+    const uint64_t N = (((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11);
+    const uint64_t Qa = mulhi_u64(N, 0x2492492492492492ull);
+#if defined(__CUDA_ARCH__)
+    const uint64_t qb = dbits(__ull2double_rn(Qa));
+#else
+    const uint64_t qb = dbits((double)(int64_t)Qa);
+#endif
+    out = bitsd((qb + ((uint64_t)((int64_t)e - 1086) << 52)) | (b & 0x8000000000000000ull));
+    return e >= 4u && e <= 2046u;
+}
+
 __device__ __forceinline__ double mean7_seq(double c, double xm, double xp, double ym, double yp,
                                             double zm, double zp)
 {
@@ -85,7 +123,9 @@ __device__ __forceinline__ double mean7_seq(double c, double xm, double xp, doub
     s = __dadd_rn(s, yp);
     s = __dadd_rn(s, zm);
     s = __dadd_rn(s, zp);
-    return __ddiv_rn(s, 7.0);
+    double q;
+    if (!div7d(s, q)) q = __ddiv_rn(s, 7.0);
+    return q;
 }
 
 // RN(s / 7) in binary32 without a division routine (so without the call its

@@ -52,3 +52,10 @@ extern "C" int host_frame_mean7_top(const double* v, int eref, double* out)
     *out = mean7_top(s0, s1, s2, (uint32_t)(eref - 1083) << 20);
     return 1;
 }
+
+// The binary64 division by 7 of the sequential rule: 1 and RN(s / 7) when
+// its integer path applies, else 0.
+extern "C" int host_div7d(double s, double* out)
+{
+    return jac::div7d(s, *out) ? 1 : 0;
+}

@@ -288,3 +288,29 @@ def test_grid_frame_mean7_ties_and_sticky_near_ties(host_lib):
             n_gen += 1
             assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), vals
     assert n_top == n_gen == 1200
+
+
+def test_div7d_matches_correctly_rounded_division(host_lib):
+    """The integer division by 7 of the sequential rule equals IEEE division
+    (correctly rounded) wherever it applies: random significands over every
+    exponent, both signs, the ends of its range, and exact multiples of 7."""
+    host_lib.host_div7d.argtypes = [ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    host_lib.host_div7d.restype = ctypes.c_int
+    rng = np.random.default_rng(15)
+    out = ctypes.c_double()
+    bits = rng.integers(0, 2 ** 63, size=200000, dtype=np.uint64) | (
+        rng.integers(0, 2, size=200000, dtype=np.uint64) << np.uint64(63))
+    vals = list(bits.view(np.float64))
+    vals += [7.0, 3.5, 1.0, 2.0 ** -1018, 2.0 ** -1019, 2.0 ** -1020, 1.7976931348623157e308, 7.0 * 2.0 ** 1000,
+             -7.0, 0.0, -0.0, 5e-324, float("inf"), float("nan")]
+    vals += [float(7 * k) * 2.0 ** int(e) for k, e in zip(rng.integers(1, 2 ** 50, 2000), rng.integers(-900, 900, 2000))]
+    applied = 0
+    for v in vals:
+        if host_lib.host_div7d(float(v), ctypes.byref(out)):
+            applied += 1
+            want = np.float64(v) / np.float64(7.0)
+            assert np.float64(out.value).tobytes() == want.tobytes(), v
+        else:
+            e = (np.float64(v).view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)
+            assert e < 4 or e == 2047, v
+    assert applied > 190000
