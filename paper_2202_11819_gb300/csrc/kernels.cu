@@ -26,6 +26,7 @@
 //   k_scatter / k_gather          dense x-fastest arrays <-> block storage.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 #include <utility>
@@ -1489,37 +1490,53 @@ cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, 
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of the unit kernels: the largest over the three tile
-// widths (units of one launch may use different widths).
-template <typename T, int OP>
-static constexpr int unit_bytes()
+// Dynamic shared memory of the unit kernels: the largest over the tile widths
+// the units use (units of one launch may use different widths). Only what
+// those widths need is requested, so the rest of the SM stays L1 cache.
+template <typename T, int OP, int TW>
+static constexpr int unit_bytes_tw()
 {
-    if constexpr (sizeof(T) == 4 && OP == OP_SEQ) {
-        constexpr int a = f32_unit_bytes<16>(), b = f32_unit_bytes<32>(), c = f32_unit_bytes<64>();
-        return a > b ? (a > c ? a : c) : (b > c ? b : c);
-    } else {
-        constexpr int a = kernel_bytes<T, OP, 16>(), b = kernel_bytes<T, OP, 32>(), c = kernel_bytes<T, OP, 64>();
-        return a > b ? (a > c ? a : c) : (b > c ? b : c);
-    }
+    if constexpr (sizeof(T) == 4 && OP == OP_SEQ) return f32_unit_bytes<TW>();
+    else return kernel_bytes<T, OP, TW>();
+}
+
+template <typename T, int OP>
+static int unit_bytes(int tw_mask)
+{
+    if (tw_mask == 0) tw_mask = 7;  // no units yet
+    int n = 0;
+    if (tw_mask & 1) n = std::max(n, unit_bytes_tw<T, OP, 16>());
+    if (tw_mask & 2) n = std::max(n, unit_bytes_tw<T, OP, 32>());
+    if (tw_mask & 4) n = std::max(n, unit_bytes_tw<T, OP, 64>());
+    return n;
+}
+
+template <typename T, int OP>
+static int unit_bytes_max()
+{
+    return unit_bytes<T, OP>(7);
 }
 
 template <typename T>
-static constexpr int residual_bytes()
+static int residual_bytes(int tw_mask)
 {
-    constexpr int a = engine_bytes<T, OP_RES, 16, kRingRes>(), b = engine_bytes<T, OP_RES, 32, kRingRes>(),
-                  c = engine_bytes<T, OP_RES, 64, kRingRes>();
-    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    if (tw_mask == 0) tw_mask = 7;
+    int n = 0;
+    if (tw_mask & 1) n = std::max(n, engine_bytes<T, OP_RES, 16, kRingRes>());
+    if (tw_mask & 2) n = std::max(n, engine_bytes<T, OP_RES, 32, kRingRes>());
+    if (tw_mask & 4) n = std::max(n, engine_bytes<T, OP_RES, 64, kRingRes>());
+    return n;
 }
 
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
 {
     if (dtype_f32)
-        k_fused_ring<float><<<a.nunits, kThreads, unit_bytes<float, OP_SEQ>(), s>>>((float*)a.pool, a.desc, a.units, p);
+        k_fused_ring<float><<<a.nunits, kThreads, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
-        k_fused_step<double, OP_EXACT><<<a.nunits, kThreads, unit_bytes<double, OP_EXACT>(), s>>>(
+        k_fused_step<double, OP_EXACT><<<a.nunits, kThreads, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p);
     else
-        k_fused_step<double, OP_SEQ><<<a.nunits, kThreads, unit_bytes<double, OP_SEQ>(), s>>>(
+        k_fused_step<double, OP_SEQ><<<a.nunits, kThreads, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p);
     return cudaGetLastError();
 }
@@ -1533,10 +1550,10 @@ const void* persistent_kernel(int dtype_f32, int arith)
 
 int persistent_block_threads() { return kThreads; }
 
-int persistent_smem_bytes(int dtype_f32, int arith)
+int persistent_smem_bytes(int dtype_f32, int arith, int tw_mask)
 {
-    if (dtype_f32) return unit_bytes<float, OP_SEQ>();
-    return arith == 1 ? unit_bytes<double, OP_EXACT>() : unit_bytes<double, OP_SEQ>();
+    if (dtype_f32) return unit_bytes<float, OP_SEQ>(tw_mask);
+    return arith == 1 ? unit_bytes<double, OP_EXACT>(tw_mask) : unit_bytes<double, OP_SEQ>(tw_mask);
 }
 
 template <typename K>
@@ -1565,14 +1582,14 @@ cudaError_t prepare_kernels()
     if (e == cudaSuccess) e = prepare_tw<64>();
 #define JAC_ALLOW(K, BYTES) \
     if (e == cudaSuccess) e = allow_smem(K, BYTES)
-    JAC_ALLOW((k_fused_step<double, OP_EXACT>), (unit_bytes<double, OP_EXACT>()));
-    JAC_ALLOW((k_fused_step<double, OP_SEQ>), (unit_bytes<double, OP_SEQ>()));
-    JAC_ALLOW((k_fused_ring<float>), (unit_bytes<float, OP_SEQ>()));
-    JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes<double, OP_EXACT>()));
-    JAC_ALLOW((k_persistent<double, OP_SEQ, false>), (unit_bytes<double, OP_SEQ>()));
-    JAC_ALLOW((k_persistent<float, OP_SEQ, true>), (unit_bytes<float, OP_SEQ>()));
-    JAC_ALLOW((k_residual<double>), (residual_bytes<double>()));
-    JAC_ALLOW((k_residual<float>), (residual_bytes<float>()));
+    JAC_ALLOW((k_fused_step<double, OP_EXACT>), (unit_bytes_max<double, OP_EXACT>()));
+    JAC_ALLOW((k_fused_step<double, OP_SEQ>), (unit_bytes_max<double, OP_SEQ>()));
+    JAC_ALLOW((k_fused_ring<float>), (unit_bytes_max<float, OP_SEQ>()));
+    JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes_max<double, OP_EXACT>()));
+    JAC_ALLOW((k_persistent<double, OP_SEQ, false>), (unit_bytes_max<double, OP_SEQ>()));
+    JAC_ALLOW((k_persistent<float, OP_SEQ, true>), (unit_bytes_max<float, OP_SEQ>()));
+    JAC_ALLOW((k_residual<double>), (residual_bytes<double>(7)));
+    JAC_ALLOW((k_residual<float>), (residual_bytes<float>(7)));
 #undef JAC_ALLOW
     return e;
 }
@@ -1581,15 +1598,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
                               cudaStream_t s)
 {
     if (dtype_f32)
-        k_persistent<float, OP_SEQ, true><<<ctas, kThreads, unit_bytes<float, OP_SEQ>(), s>>>(
+        k_persistent<float, OP_SEQ, true><<<ctas, kThreads, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     else if (arith == 1)
-        k_persistent<double, OP_EXACT, false><<<ctas, kThreads, unit_bytes<double, OP_EXACT>(), s>>>(
+        k_persistent<double, OP_EXACT, false><<<ctas, kThreads, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     else
-        k_persistent<double, OP_SEQ, false><<<ctas, kThreads, unit_bytes<double, OP_SEQ>(), s>>>(
+        k_persistent<double, OP_SEQ, false><<<ctas, kThreads, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     return cudaGetLastError();
@@ -1598,10 +1615,10 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
 cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
 {
     if (dtype_f32)
-        k_residual<float><<<a.nunits, kThreads, residual_bytes<float>(), s>>>((const float*)a.pool, a.desc, a.frame,
+        k_residual<float><<<a.nunits, kThreads, residual_bytes<float>(a.tw_mask), s>>>((const float*)a.pool, a.desc, a.frame,
                                                                              a.units, p, partials);
     else
-        k_residual<double><<<a.nunits, kThreads, residual_bytes<double>(), s>>>((const double*)a.pool, a.desc,
+        k_residual<double><<<a.nunits, kThreads, residual_bytes<double>(a.tw_mask), s>>>((const double*)a.pool, a.desc,
                                                                                a.frame, a.units, p, partials);
     return cudaGetLastError();
 }

@@ -18,6 +18,7 @@ struct LaunchArgs {
     int nblocks;
     int nunits;
     int tile_w;              // tile width of the update engine: 16, 32 or 64
+    int tw_mask;             // tile widths present in the units: bit 0 = 16, 1 = 32, 2 = 64
 };
 
 struct PersistentArgs {
@@ -37,8 +38,10 @@ int engine_threads();
 bool tile_width_supported(int tw);
 int persistent_block_threads();
 const void* persistent_kernel(int dtype_f32, int arith);
-// dynamic shared memory of one persistent CTA (for occupancy queries)
-int persistent_smem_bytes(int dtype_f32, int arith);
+// dynamic shared memory of a unit-kernel (fused, persistent) CTA whose units
+// use the tile widths in tw_mask (bit 0 = 16, 1 = 32, 2 = 64): only as much
+// as those widths need, so the rest of the SM's memory stays L1 cache
+int persistent_smem_bytes(int dtype_f32, int arith, int tw_mask);
 // raises the dynamic shared memory limit of every engine kernel on the
 // current device; once per device, before the first launch or capture
 cudaError_t prepare_kernels();

@@ -165,6 +165,7 @@ struct jac_ctx {
     int zdepth = 0;               // planes per work unit (0: the whole block)
     // per block-width class (block x extent) tile widths overriding tile_w
     std::vector<std::pair<int32_t, int32_t>> class_tw;
+    int tw_mask = 2;              // tile widths present in the units (bit 0 = 16, 1 = 32, 2 = 64)
     int dtype = JAC_F64;
     int esize = 8;
     int mode = JAC_MODE_PERSISTENT;
@@ -238,6 +239,7 @@ struct jac_ctx {
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
         a.tile_w = tile_w;
+        a.tw_mask = tw_mask;
         return a;
     }
     int64_t ncells() const
@@ -340,6 +342,8 @@ int class_tile_width(const jac_ctx* h, int32_t bx)
 int build_units(jac_ctx* h)
 {
     const int64_t nblocks = (int64_t)h->hdesc.size();
+    h->tw_mask = 0;
+    h->pctas = 0;  // the persistent grid depends on the widths' shared memory
     h->ntx.resize(nblocks);
     h->nty.resize(nblocks);
     h->hunits.clear();
@@ -369,6 +373,7 @@ int build_units(jac_ctx* h)
                         u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
                         u.tw = (int16_t)TW;
                         u.pad = 0;
+                        h->tw_mask |= TW == 16 ? 1 : (TW == 32 ? 2 : 4);
                         h->hunits.push_back(u);
                     }
         }
@@ -1173,7 +1178,7 @@ int jac_iterate(jac_ctx* h, int64_t n)
                 int per_sm = 0, sms = 0;
                 CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
                                                                  persistent_block_threads(),
-                                                                 persistent_smem_bytes(f32, h->arith)),
+                                                                 persistent_smem_bytes(f32, h->arith, h->tw_mask)),
                    "occupancy");
                 CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
                 h->pctas = std::max(1, std::min(per_sm * sms, (int)h->hunits.size()));
