@@ -20,6 +20,7 @@
 // the largest and whose result is a normal number; everything else takes an
 // exact wide-accumulator path (rare: mixed signs, subnormals, huge spreads).
 #pragma once
+#include <cmath>
 
 #include <cstdint>
 #include <cstring>
@@ -764,6 +765,75 @@ JAC_HD inline bool laplacian(const W96& c, const W96& xm, const W96& xp, const W
     if (neg) out_bits |= (1ull << 63);
     out = bitsd(out_bits);
     return true;
+}
+
+// ---- binary32 residual in a 64-bit frame
+// A binary32 grid's Laplacian term L = xm + xp + ym + yp + zm + zp - 6c is
+// exact in a signed 64-bit frame of 2^(eref32 - 186) per unit (eref32 = the
+// grid's largest binary32 exponent field + 1): a value of exponent field e
+// in [eref32 - 36, eref32 - 1] is its 24-bit significand shifted left by
+// e - eref32 + 36 (at most 35), below 2^59 in magnitude, so |L| < 12 * 2^59.
+// Zero is 0; other values (tiny or subnormal) are outside the window (ok is
+// set false) and the tile is redone with the exact per-cell routines.
+JAC_HD inline int64_t of32(float v, int eref32, bool& ok)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const int sh = e - eref32 + 36;
+    const bool zero = (b & 0x7FFFFFFFu) == 0u;
+    ok = zero || (e != 0 && sh >= 0);
+    const int64_t m = (int64_t)((b & 0x7FFFFFu) | 0x800000u);
+    const int64_t w = (zero || sh < 0) ? 0 : (m << (sh & 63));
+    return (b >> 31) ? -w : w;
+}
+
+// a += L^2 over 192 bits (|L| < 2^63)
+JAC_HD inline void add_square(int64_t L, uint64_t& a0, uint64_t& a1, uint64_t& a2)
+{
+    const uint64_t u = L < 0 ? (uint64_t)(-L) : (uint64_t)L;
+    const uint64_t lo = u * u, hi = umulhi64(u, u);
+    const uint64_t s0 = a0 + lo;
+    const uint64_t c0 = s0 < lo ? 1u : 0u;
+    const uint64_t t1 = a1 + hi;
+    const uint64_t c1 = t1 < hi ? 1u : 0u;
+    const uint64_t s1 = t1 + c0;
+    const uint64_t c2 = s1 < t1 ? 1u : 0u;
+    a0 = s0;
+    a1 = s1;
+    a2 += c1 + c2;
+}
+
+// The 192-bit a2:a1:a0 rounded once to binary64, times 2^scale (the caller
+// keeps the result in the normal range).
+JAC_HD inline double u192_to_double_scaled(uint64_t a0, uint64_t a1, uint64_t a2, int scale)
+{
+    uint64_t top, rest;
+    int below;  // bits below `top`
+    if (a2) {
+        const int lz = clz64(a2);
+        top = lz ? (a2 << lz) | (a1 >> (64 - lz)) : a2;
+        rest = (lz ? a1 << lz : a1) | a0;
+        below = 128 - lz;
+    } else if (a1) {
+        const int lz = clz64(a1);
+        top = lz ? (a1 << lz) | (a0 >> (64 - lz)) : a1;
+        rest = lz ? a0 << lz : a0;
+        below = 64 - lz;
+    } else {
+        top = a0;
+        rest = 0;
+        below = 0;
+    }
+    // top has its leading bit at bit 63 (or is a0 itself): jam the sticky bit
+    const uint64_t tj = top | (rest != 0u ? 1u : 0u);
+#if defined(__CUDA_ARCH__)
+    const double t = __ull2double_rn(tj);
+    return scalbn(t, below + scale);
+#else
+    const double t = (double)tj;  // correctly rounded on the host (the oracle's platform)
+    return std::ldexp(t, below + scale);
+#endif
 }
 
 }  // namespace frame

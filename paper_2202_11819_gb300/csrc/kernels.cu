@@ -101,6 +101,7 @@ __device__ __forceinline__ T mean7(T c, T xm, T xp, T ym, T yp, T zm, T zp)
 constexpr int OP_SEQ = 0;    // binary64/binary32 left-to-right sum / 7 in floating point
 constexpr int OP_EXACT = 1;  // binary64 correctly rounded mean, grid-frame integer arithmetic
 constexpr int OP_RES = 2;    // residual: sum of L^2 with the exact Laplacian term
+constexpr int OP_RES32 = 3;  // the same for binary32 grids, L in a 64-bit frame and L^2 summed exactly
 
 template <typename T, int OP>
 struct Elem {
@@ -109,6 +110,10 @@ struct Elem {
 template <typename T>
 struct Elem<T, OP_SEQ> {
     using type = T;
+};
+template <typename T>
+struct Elem<T, OP_RES32> {
+    using type = int64_t;
 };
 
 template <typename T>
@@ -135,7 +140,11 @@ template <typename T, int OP>
 __device__ __forceinline__ typename Elem<T, OP>::type conv(T v, int eref)
 {
     if constexpr (OP == OP_SEQ) return v;
-    else return frame::of((double)v, eref);
+    else if constexpr (OP == OP_RES32) {
+        // out-of-window values are flagged by the engine (conv_ok)
+        bool ok;
+        return frame::of32((float)v, eref, ok);
+    } else return frame::of((double)v, eref);
 }
 
 // Where the value of (x, y) lives along z, for -1 <= x <= bx, -1 <= y <= by
@@ -406,11 +415,25 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     T* re = rc + RD * kThreads;                      // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int eref = (OP == OP_SEQ) ? 0 : frame_e[d.inst] + 1;
+    // OP_RES32: eref is the binary32 exponent field + 1 (frame_e holds the
+    // binary64 field of the largest value)
+    const int eref = (OP == OP_SEQ) ? 0 : (OP == OP_RES32 ? frame_e[d.inst] + 1 - 896 : frame_e[d.inst] + 1);
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const int x = x0 + tx, y = y0 + ty;
     const int64_t plane = d.plane;
     if (OP != OP_SEQ && tid == 0) slow->n = 0;
+    bool bad = false;                         // OP_RES32: a value outside the 64-bit frame
+    uint64_t q0 = 0u, q1 = 0u, q2 = 0u;       // OP_RES32: this thread's sum of L^2 in frame units
+    auto cv = [&](T v) {
+        if constexpr (OP == OP_RES32) {
+            bool ok;
+            const int64_t w = frame::of32((float)v, eref, ok);
+            bad |= !ok;
+            return w;
+        } else {
+            return conv<T, OP>(v, eref);
+        }
+    };
 
     // own column: 0 unused, 1 interior cell, 2 halo cell inside the tile.
     // The value consumed at iteration k is at sp + (k - z0) * ss: kind 1 the
@@ -429,8 +452,8 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane;
         oidx = cell_index<T>(d, p ^ 1, x, y, 0);
         const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
-        wzm = conv<T, OP>(ldv<T, CG>(zlo), eref);
-        wc = conv<T, OP>(ldv<T, CG>(col + z0 * plane), eref);
+        wzm = cv(ldv<T, CG>(zlo));
+        wc = cv(ldv<T, CG>(col + z0 * plane));
     } else if ((x == bx && y < by) || (y == by && x < bx)) {
         kind = 2;
         const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
@@ -468,13 +491,16 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
         E* slot = buf + (ty + 1) * kSW + tx + 1;
         if (kind == 1) *slot = wc;
-        else if (kind == 2) *slot = conv<T, OP>(myc[s * kThreads], eref);
-        if (er >= 0) buf[er * kSW + ec] = conv<T, OP>(mye[s * kEr], eref);
+        else if (kind == 2) *slot = cv(myc[s * kThreads]);
+        if (er >= 0) buf[er * kSW + ec] = cv(mye[s * kEr]);
         __syncthreads();
         if (kind == 1) {
-            const E wzp = conv<T, OP>(myc[s * kThreads], eref);
+            const E wzp = cv(myc[s * kThreads]);
             const int sc = (ty + 1) * kSW + tx + 1;
-            if constexpr (OP == OP_SEQ) {
+            if constexpr (OP == OP_RES32) {
+                const int64_t L = buf[sc - 1] + buf[sc + 1] + buf[sc - kSW] + buf[sc + kSW] + wzm + wzp - 6 * wc;
+                frame::add_square(L, q0, q1, q2);
+            } else if constexpr (OP == OP_SEQ) {
                 pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
             } else {
                 double o;
@@ -497,7 +523,20 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         s = s == RD - 1 ? 0 : s + 1;
     }
     cp_async_wait<0>();  // only empty groups remain; the ring is free for the next tile
-    return slow_cells<T, OP, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc, slow);
+    if constexpr (OP == OP_RES32) {
+        // L^2 was summed exactly in units of 2^(2 (eref - 186)); a value
+        // outside the frame anywhere in the tile redoes the whole tile with
+        // the exact per-cell routines
+        acc = frame::u192_to_double_scaled(q0, q1, q2, 2 * (eref - 186));
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) slow->n = kSlowMax + 1;
+        }
+        return slow_cells<T, OP_RES, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc,
+                                                   slow);
+    } else {
+        return slow_cells<T, OP, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc,
+                                               slow);
+    }
 }
 
 // The engine above for the exact mean, two planes per step: each thread
@@ -1257,14 +1296,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
     double acc = 0.0;
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
-        acc = tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+        constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
+        acc = tile_engine<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p, u.x0,
+                                                             u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
         if constexpr (sizeof(T) == 4) {
             // a binary32 unit is two engine tiles tall
             __syncthreads();
-            acc += tile_engine<T, OP_RES, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
-                                                                     p, u.x0, u.y0 + kThreads / TW, u.z0, u.z1,
-                                                                     jac_dyn_sm, &slow);
+            acc += tile_engine<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                  u.x0, u.y0 + kThreads / TW, u.z0, u.z1, jac_dyn_sm,
+                                                                  &slow);
         }
     });
     const int tid = threadIdx.x;
@@ -1521,10 +1561,11 @@ template <typename T>
 static int residual_bytes(int tw_mask)
 {
     if (tw_mask == 0) tw_mask = 7;
+    constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
     int n = 0;
-    if (tw_mask & 1) n = std::max(n, engine_bytes<T, OP_RES, 16, kRingRes>());
-    if (tw_mask & 2) n = std::max(n, engine_bytes<T, OP_RES, 32, kRingRes>());
-    if (tw_mask & 4) n = std::max(n, engine_bytes<T, OP_RES, 64, kRingRes>());
+    if (tw_mask & 1) n = std::max(n, engine_bytes<T, OPR, 16, kRingRes>());
+    if (tw_mask & 2) n = std::max(n, engine_bytes<T, OPR, 32, kRingRes>());
+    if (tw_mask & 4) n = std::max(n, engine_bytes<T, OPR, 64, kRingRes>());
     return n;
 }
 

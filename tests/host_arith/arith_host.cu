@@ -59,3 +59,20 @@ extern "C" int host_div7d(double s, double* out)
 {
     return jac::div7d(s, *out) ? 1 : 0;
 }
+
+// The binary32 residual's 64-bit frame: a value's frame integer (and
+// whether it lies in the window), and the sum of squares of n integers over
+// 192 bits rounded once and scaled by 2^scale.
+extern "C" int host_of32(float v, int eref32, long long* w)
+{
+    bool ok;
+    *w = jac::frame::of32(v, eref32, ok);
+    return ok ? 1 : 0;
+}
+
+extern "C" double host_sum_squares(const long long* L, int n, int scale)
+{
+    uint64_t a0 = 0, a1 = 0, a2 = 0;
+    for (int i = 0; i < n; ++i) jac::frame::add_square(L[i], a0, a1, a2);
+    return jac::frame::u192_to_double_scaled(a0, a1, a2, scale);
+}

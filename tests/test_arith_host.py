@@ -314,3 +314,36 @@ def test_div7d_matches_correctly_rounded_division(host_lib):
             e = (np.float64(v).view(np.uint64) >> np.uint64(52)) & np.uint64(0x7FF)
             assert e < 4 or e == 2047, v
     assert applied > 190000
+
+
+def test_binary32_residual_frame(host_lib):
+    """The binary32 residual's 64-bit frame: values convert exactly (value =
+    w * 2^(eref32 - 186)) inside the 36-binade window and are flagged outside
+    it; sums of squares of 64-bit integers round once, exactly."""
+    host_lib.host_of32.argtypes = [ctypes.c_float, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)]
+    host_lib.host_of32.restype = ctypes.c_int
+    host_lib.host_sum_squares.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    host_lib.host_sum_squares.restype = ctypes.c_double
+    rng = np.random.default_rng(16)
+    w = ctypes.c_longlong()
+    for _ in range(20000):
+        eref32 = int(rng.integers(2, 255))
+        e = int(rng.integers(max(0, eref32 - 40), eref32))
+        bits = (int(rng.integers(0, 2)) << 31) | (e << 23) | int(rng.integers(0, 2 ** 23))
+        v = np.array([bits], dtype=np.uint32).view(np.float32)[0]
+        ok = host_lib.host_of32(float(v), eref32, ctypes.byref(w))
+        inside = e != 0 and e >= eref32 - 36
+        assert ok == (1 if (inside or float(v) == 0.0) else 0), (bits, eref32)
+        if ok:
+            assert Fraction(w.value) * Fraction(2) ** (eref32 - 186) == Fraction(float(v)), (bits, eref32)
+    for _ in range(3000):
+        n = int(rng.integers(1, 200))
+        L = rng.integers(-(2 ** 62), 2 ** 62, size=n, dtype=np.int64)
+        L[rng.random(n) < 0.3] >>= int(rng.integers(0, 60))
+        scale = int(rng.integers(-400, 200))
+        got = host_lib.host_sum_squares(np.ascontiguousarray(L).ctypes.data, n, scale)
+        exact = sum(Fraction(int(x)) ** 2 for x in L) * Fraction(2) ** scale
+        assert got == float(exact), (list(L), scale)
+    for L in ([0], [1], [-1], [2 ** 62 - 1] * 200, [3, -4]):
+        a = np.ascontiguousarray(L, dtype=np.int64)
+        assert host_lib.host_sum_squares(a.ctypes.data, len(L), 0) == float(sum(Fraction(int(x)) ** 2 for x in L))
