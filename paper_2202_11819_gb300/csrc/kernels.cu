@@ -1468,6 +1468,17 @@ __global__ void k_gather(const TS* pool, TD* dense, const BlockDesc* desc, int b
 
 // Dirichlet values into the ghost planes of faces at the global boundary,
 // both buffers. One CTA per (block, face).
+// Input check of a dense write: the lowest index whose value is not finite
+// or exceeds lim in magnitude (first_bad starts at all ones).
+template <typename TS>
+__global__ void k_validate(const TS* src, int64_t n, double lim, unsigned long long* first_bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)src[i];
+        if (!(isfinite(v) && fabs(v) <= lim)) atomicMin(first_bad, (unsigned long long)i);
+    }
+}
+
 template <typename T>
 __global__ void k_init_ghosts(T* pool, const BlockDesc* desc)
 {
@@ -1750,6 +1761,17 @@ cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void*
         k_gather<double, double><<<grid, 256, 0, s>>>((const double*)a.pool, (double*)dense, a.desc, b0, dense_base,
                                                       p);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const void* src, int src_f32, int64_t n, double lim, unsigned long long* first_bad,
+                            cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t want = (n + 255) / 256;
+    const int grid = (int)std::min<int64_t>(want, 152 * 16);
+    if (src_f32) k_validate<float><<<grid, 256, 0, s>>>((const float*)src, n, lim, first_bad);
+    else k_validate<double><<<grid, 256, 0, s>>>((const double*)src, n, lim, first_bad);
     return cudaGetLastError();
 }
 

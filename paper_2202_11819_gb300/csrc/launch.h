@@ -67,6 +67,10 @@ cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, cons
                            int64_t dense_base, int p, cudaStream_t s);
 cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int b0, int nb,
                           int64_t dense_base, int p, cudaStream_t s);
+// the lowest index of src[0 .. n) that is not finite or exceeds lim in
+// magnitude, min-combined into *first_bad (which the caller sets to all ones)
+cudaError_t launch_validate(const void* src, int src_f32, int64_t n, double lim, unsigned long long* first_bad,
+                            cudaStream_t s);
 cudaError_t launch_init_ghosts(const LaunchArgs& a, int dtype_f32, cudaStream_t s);
 
 }  // namespace jac

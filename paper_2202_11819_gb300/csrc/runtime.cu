@@ -218,6 +218,7 @@ struct jac_ctx {
     uint32_t* done = nullptr;
     unsigned long long* work = nullptr;
     DeviceStatus* status = nullptr;
+    unsigned long long* dbad = nullptr;  // input check of dense writes (lowest bad index)
     int pctas = 0;
     int64_t wait_ns = 2000000000LL;
     int hold_block = -1;
@@ -782,6 +783,19 @@ int write_dense(jac_ctx* h, int i0, int i1, const void* src, size_t n, int src_f
         CU(cudaMemcpyAsync(h->dense, src, bytes, cudaMemcpyHostToDevice, h->stream), "copy in");
         dsrc = h->dense;
     }
+    // reject non-finite or out-of-range values before anything is overwritten
+    // (binary64 values must stay within 1e300, binary32 grids' within 3e38,
+    // so no sum of seven can overflow)
+    {
+        const double lim = src_f32 ? HUGE_VAL : (h->dtype == JAC_F32 ? 3.0e38 : 1.0e300);
+        unsigned long long bad = ~0ull;
+        CU(cudaMemsetAsync(h->dbad, 0xFF, sizeof(unsigned long long), h->stream), "clear check");
+        CU(launch_validate(dsrc, src_f32, (int64_t)n, lim, h->dbad, h->stream), "check values");
+        h->launches += 1;
+        CU(cudaMemcpyAsync(&bad, h->dbad, sizeof bad, cudaMemcpyDeviceToHost, h->stream), "check result");
+        CU(cudaStreamSynchronize(h->stream), "check sync");
+        if (bad != ~0ull) return fail(JAC_EINVAL, "value at %llu not finite or out of range", bad);
+    }
     // the scatter raises each frame to the largest exponent of the new interior
     CU(cudaMemcpyAsync(h->frame + i0, h->hframe.data() + i0, (size_t)(i1 - i0) * sizeof(int32_t),
                        cudaMemcpyHostToDevice, h->stream),
@@ -861,6 +875,7 @@ int open_ctx(jac_ctx* h, void* stream)
     int rc;
     if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->work))) return rc;
     if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
+    if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->dbad))) return rc;
     if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
     if ((rc = dev_alloc(h, ns * sizeof(double), (void**)&h->dres_inst))) return rc;
     if ((rc = dev_alloc(h, ns * sizeof(int32_t), (void**)&h->frame))) return rc;
@@ -1069,8 +1084,6 @@ int jac_write(jac_ctx* h, const double* host, size_t n_cells)
     if (rc) return rc;
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    for (size_t i = 0; i < n_cells; ++i)
-        if (!value_ok(host[i], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", i);
     return write_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 0, false);
 }
 
@@ -1081,8 +1094,6 @@ int jac_write_f32(jac_ctx* h, const float* host, size_t n_cells)
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if (h->dtype != JAC_F32) return fail(JAC_EINVAL, "jac_write_f32 needs an F32 context");
     if ((int64_t)n_cells != h->ncells()) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->ncells());
-    for (size_t i = 0; i < n_cells; ++i)
-        if (!std::isfinite(host[i])) return fail(JAC_EINVAL, "value at %zu not finite", i);
     return write_dense(h, h->first_active(), h->last_active() + 1, host, n_cells, 1, false);
 }
 
@@ -1276,8 +1287,6 @@ int jac_write_instance(jac_ctx* h, int32_t i, const double* host, size_t n_cells
     if (i < 0 || i >= (int32_t)h->inst.size() || !h->inst[i].active) return fail(JAC_EINVAL, "grid slot %d not in use", i);
     if (!host) return fail(JAC_EINVAL, "null host pointer");
     if ((int64_t)n_cells != h->icells(i)) return fail(JAC_EINVAL, "n_cells %zu != %lld", n_cells, (long long)h->icells(i));
-    for (size_t q = 0; q < n_cells; ++q)
-        if (!value_ok(host[q], h->dtype)) return fail(JAC_EINVAL, "value at %zu not finite or out of range", q);
     return write_dense(h, i, i + 1, host, n_cells, 0, false);
 }
 

@@ -177,13 +177,31 @@ def test_zero_iterations_and_reread():
         assert np.array_equal(J.read(), u0)
 
 
-def test_write_rejects_non_finite():
-    with Jacobi3D((4, 4, 4), (2, 2, 2)) as J:
-        bad = np.zeros((4, 4, 4))
-        bad[1, 2, 3] = np.inf
+@pytest.mark.parametrize("bad_value", [np.inf, -np.inf, np.nan, 2e300])
+def test_write_rejects_bad_values_and_leaves_the_grid(bad_value):
+    """Host and device writes check every value on the device before
+    anything is overwritten: the error names the first bad index."""
+    import torch
+
+    with Jacobi3D((6, 5, 4), (3, 3, 2)) as J:
+        good = synth.grid_uniform01(3, 6, 5, 4)
+        J.write(good)
+        bad = good.copy()
+        bad[2, 3, 4] = bad_value  # flat index 2*30 + 3*6 + 4 = 82
+        bad[3, 4, 5] = np.nan
         with pytest.raises(_lib.JacError) as e:
             J.write(bad)
+        assert e.value.code == _lib.JAC_EINVAL and "82" in str(e.value)
+        assert np.array_equal(J.read(), good)
+        with pytest.raises(_lib.JacError) as e:
+            J.write_device(torch.from_numpy(bad.reshape(-1)).cuda())
         assert e.value.code == _lib.JAC_EINVAL
+        assert np.array_equal(J.read(), good)
+    with Jacobi3D((6, 5, 4), (3, 3, 2), dtype="f32") as J:
+        big = np.zeros((4, 5, 6))
+        big[0, 0, 1] = 3.1e38  # finite in binary64, beyond the binary32 grid's range
+        with pytest.raises(_lib.JacError):
+            J.write(big)
 
 
 def test_persistent_wait_timeout_reports_status_and_context_recovers():
