@@ -186,20 +186,22 @@ int jac_set_arith(jac_ctx *h, int32_t arith);
 /* ------------------------------------------------------------------ */
 
 /* Set the interior from a host array of n_cells = nx*ny*nz binary64 values
- * (x fastest). Values must be finite with magnitude <= 1e300 (JAC_EINVAL
- * otherwise, checked on the host); F32 contexts round them to nearest.
- * The copy goes through pinned staging; the call returns after the data has
- * left `host` (the host buffer may be reused at once). Resets the
- * iteration count. */
+ * (x fastest). Values must be finite with magnitude <= 1e300 (<= 3e38 for
+ * F32 contexts, which round them to nearest). They are copied to a device
+ * staging buffer and checked there before anything is overwritten: a bad
+ * value gives JAC_EINVAL naming the lowest bad index (jac_last_error) and
+ * leaves the grid as it was. Synchronises; the host buffer may be reused on
+ * return. Resets the iteration count. */
 int jac_write(jac_ctx *h, const double *host, size_t n_cells);
 
-/* As jac_write, from a host binary32 array (F32 contexts only: exact). */
+/* As jac_write, from a host binary32 array (F32 contexts only: exact; values
+ * must be finite). */
 int jac_write_f32(jac_ctx *h, const float *host, size_t n_cells);
 
 /* As jac_write, from device memory already on this GPU: `dev` holds n_cells
  * values of type `dtype` (which must equal the context's dtype), x fastest.
- * Stream-ordered, no host sync; the caller keeps `dev` alive until the
- * context's stream passes this point. The values are NOT range-checked. */
+ * The values are checked as for jac_write (binary32: finite) before the grid
+ * is touched, which synchronises the context's stream. */
 int jac_write_device(jac_ctx *h, const void *dev, size_t n_cells, int32_t dtype);
 
 /* Copy the interior to a host array of n_cells binary64 values (x fastest;
