@@ -72,6 +72,9 @@ def parse():
 
 # ----------------------------------------------------------------- helpers
 def dist_setup(n_gpus):
+    """Ranks are independent replicas (one per GPU, launched by torchrun):
+    the process group only carries the timing barriers and the max over
+    ranks. NCCL on GPUs, gloo without (the CPU tests of this path)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -81,8 +84,11 @@ def dist_setup(n_gpus):
 
         import torch
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
         pg = dist
     return rank, world, local, pg
 
@@ -97,7 +103,8 @@ def max_over_ranks(pg, v: float) -> float:
         return v
     import torch
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
 
