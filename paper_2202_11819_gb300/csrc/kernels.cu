@@ -41,7 +41,14 @@ namespace jac {
 // (512 / TW) columns of a block; TW (16, 32 or 64) is chosen per context (the
 // autotuner times the three). Each tile covers a z range [z0, z1) of the
 // block, so the z depth of a work unit is chosen too.
-constexpr int kThreads = 512;
+constexpr int kThreads = 512;  // the most threads of any engine CTA (slow-list encoding)
+// Threads per CTA of the engines: 256 for binary64 (the exact mean's integer
+// work schedules better in smaller CTAs, four per SM), 512 for binary32 (two
+// per SM). A binary32 work unit is 1024 / TW rows (two columns per thread).
+template <typename T>
+constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
+template <typename T>
+constexpr int kMinCTAs = 1024 / kNT<T>;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
@@ -225,14 +232,14 @@ struct SlowList {
 template <typename T, int OP, int TW>
 __host__ __device__ constexpr int smem_bytes()
 {
-    return 2 * (kThreads / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
+    return 2 * (kNT<T> / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
 }
 
 // Extra ring slots of a tile (the halo ring around the TW x 512/TW interior).
-template <int TW>
+template <typename T, int TW>
 __host__ __device__ constexpr int ring_extra()
 {
-    return 2 * TW + 2 * (kThreads / TW);
+    return 2 * TW + 2 * (kNT<T> / TW);
 }
 
 // Shared memory of the engine: the double-buffered exchange plane, then the
@@ -241,7 +248,7 @@ __host__ __device__ constexpr int ring_extra()
 template <typename T, int OP, int TW, int RD>
 __host__ __device__ constexpr int engine_bytes()
 {
-    return smem_bytes<T, OP, TW>() + RD * (kThreads + ring_extra<TW>()) * (int)sizeof(T);
+    return smem_bytes<T, OP, TW>() + RD * (kNT<T> + ring_extra<T, TW>()) * (int)sizeof(T);
 }
 
 // Planes in flight per stream: binary64 values are 8 bytes and the exact
@@ -285,10 +292,10 @@ template <typename T, bool PULL, int TW>
 __device__ __forceinline__ HaloSlot<T> halo_slot(const T* pool, const BlockDesc* desc, const BlockDesc& d, int p,
                                                  int x0, int y0, int z0, int tid)
 {
-    constexpr int kTW = TW, kTY = kThreads / TW;
+    constexpr int kTW = TW, kTY = kNT<T> / TW;
     const int bx = d.ext[0], by = d.ext[1];
     HaloSlot<T> h{-1, 0, pool, 0};
-    if (tid >= ring_extra<TW>()) return h;
+    if (tid >= ring_extra<T, TW>()) return h;
     int hx, hy;
     if (tid < kTW) {
         h.er = 0;
@@ -342,7 +349,7 @@ __device__ __forceinline__ double slow_cells(T* __restrict__ pool, const BlockDe
         if (n > 0) {
             if (n <= kSlowMax) {
                 if constexpr (OP == OP_EXACT) {
-                    for (int i = tid; i < n; i += kThreads) {
+                    for (int i = tid; i < n; i += kNT<T>) {
                         const uint32_t c = slow->cell[i];
                         const int kk = (int)(c >> 9), t = (int)(c & 511u);
                         const int cx = x0 + t % kTX, cy = y0 + t / kTX;
@@ -408,11 +415,11 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
                               unsigned char* smraw, SlowList* slow)
 {
     using E = typename Elem<T, OP>::type;
-    constexpr int kTX = TW, kTY = kThreads / TW, kTW = TW, kSW = TW + 2, kEr = ring_extra<TW>();
+    constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kTW = TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
     static_assert(RD >= 2, "ring depth");
     E* sm = (E*)smraw;
-    T* rc = (T*)(smraw + smem_bytes<T, OP, TW>());  // [RD][kThreads]
-    T* re = rc + RD * kThreads;                      // [RD][kEr]
+    T* rc = (T*)(smraw + smem_bytes<T, OP, TW>());  // [RD][kN]
+    T* re = rc + RD * kN;                            // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     // OP_RES32: eref is the binary32 exponent field + 1 (frame_e holds the
@@ -464,13 +471,13 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     const int er = hs.er, ec = hs.ec;
     const T* ep = hs.p;
     const int64_t es = hs.stride;
-    T* const myc = rc + tid;                     // ring slot s: myc[s * kThreads]
+    T* const myc = rc + tid;                     // ring slot s: myc[s * kN]
     T* const mye = re + (tid < kEr ? tid : 0);   // ring slot s: mye[s * kEr]
     int next = z0;                               // the next iteration to copy
     auto issue = [&](int s) {
         if (next < z1) {
-            if (kind == 1) cp_async<sizeof(T)>(myc + s * kThreads, next + 1 == z1 ? zhi : sp);
-            else if (kind == 2) cp_async<sizeof(T)>(myc + s * kThreads, sp);
+            if (kind == 1) cp_async<sizeof(T)>(myc + s * kN, next + 1 == z1 ? zhi : sp);
+            else if (kind == 2) cp_async<sizeof(T)>(myc + s * kN, sp);
             if (er >= 0) cp_async<sizeof(T)>(mye + s * kEr, ep);
         }
         cp_async_commit();  // one group per iteration, empty past the range
@@ -491,11 +498,11 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
         E* slot = buf + (ty + 1) * kSW + tx + 1;
         if (kind == 1) *slot = wc;
-        else if (kind == 2) *slot = cv(myc[s * kThreads]);
+        else if (kind == 2) *slot = cv(myc[s * kN]);
         if (er >= 0) buf[er * kSW + ec] = cv(mye[s * kEr]);
         __syncthreads();
         if (kind == 1) {
-            const E wzp = cv(myc[s * kThreads]);
+            const E wzp = cv(myc[s * kN]);
             const int sc = (ty + 1) * kSW + tx + 1;
             if constexpr (OP == OP_RES32) {
                 const int64_t L = buf[sc - 1] + buf[sc + 1] + buf[sc - kSW] + buf[sc + kSW] + wzm + wzp - 6 * wc;
@@ -546,16 +553,16 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
 // holds two planes, double-buffered; the ring, its slots and the slow list
 // are those of the single-plane engine (RD even). A range with an odd number
 // of planes ends with a single-plane step.
-template <int TW>
+template <typename T, int TW>
 __host__ __device__ constexpr int pair_smem_bytes()
 {
-    return 4 * ((kThreads / TW + 2) * (TW + 2) + 1) * (int)sizeof(frame::W96);
+    return 4 * ((kNT<T> / TW + 2) * (TW + 2) + 1) * (int)sizeof(frame::W96);
 }
 
 template <typename T, int TW, int RD>
 __host__ __device__ constexpr int pair_engine_bytes()
 {
-    return pair_smem_bytes<TW>() + RD * (kThreads + ring_extra<TW>()) * (int)sizeof(T);
+    return pair_smem_bytes<T, TW>() + RD * (kNT<T> + ring_extra<T, TW>()) * (int)sizeof(T);
 }
 
 // cp.async of one 8- or 4-byte value, issued only when `on` (a predicated
@@ -585,13 +592,13 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
                                  unsigned char* smraw, SlowList* slow)
 {
     using E = frame::W96;
-    constexpr int kTX = TW, kTY = kThreads / TW, kSW = TW + 2, kEr = ring_extra<TW>();
+    constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
     constexpr int kPlane = (kTY + 2) * kSW + 1;  // + one slot written by threads without a halo slot
-    constexpr uint32_t kRowC = kThreads * sizeof(T), kRowE = kEr * sizeof(T);
+    constexpr uint32_t kRowC = kN * sizeof(T), kRowE = kEr * sizeof(T);
     static_assert(RD >= 4 && RD % 2 == 0, "ring depth");
     E* const sm = (E*)smraw;                                   // [2 buffers][2 planes][kPlane]
-    T* const rc = (T*)(smraw + pair_smem_bytes<TW>());         // [RD][kThreads]
-    T* const re = rc + RD * kThreads;                          // [RD][kEr]
+    T* const rc = (T*)(smraw + pair_smem_bytes<T, TW>());      // [RD][kN]
+    T* const re = rc + RD * kN;                                // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     const int eref = frame_e[d.inst] + 1;
@@ -665,8 +672,8 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         cp_async_wait<RD / 2 - 1>();  // this thread's copies for k, k+1 have landed
         E* const b0 = sm + bsel * (2 * kPlane);
         E* const b1 = b0 + kPlane;
-        const T v0 = rc[s * kThreads + tid];
-        const T v1 = rc[(s + 1) * kThreads + tid];
+        const T v0 = rc[s * kN + tid];
+        const T v1 = rc[(s + 1) * kN + tid];
         // planes k+1, k+2 of the own column (plane z1 from the register)
         const E c0 = frame::of((double)(k + 1 >= z1 ? zhiv : v0), eref);
         const E c1 = frame::of((double)(k + 2 >= z1 ? zhiv : v1), eref);
@@ -743,7 +750,7 @@ constexpr int kSeqRing = (kSeqAhead<T> + 3) * kSeqBatch;  // planes in the ring
 template <int TW>
 __host__ __device__ constexpr int seq_plane()
 {
-    return (kThreads / TW + 2) * (TW + 2) + 1;  // + one slot written by threads without a halo slot
+    return (kNT<float> / TW + 2) * (TW + 2) + 1;  // + one slot written by threads without a halo slot
 }
 
 template <typename T, int TW>
@@ -808,7 +815,7 @@ __device__ void tile_engine_ring(T* __restrict__ pool, const BlockDesc* __restri
     // whose planes and copies all lie inside the range skip the range checks.
     constexpr int kNB = RD / kB;
     static_assert(RD % kB == 0, "ring of whole batches");
-    const bool halo_warp = (tid & ~31) < ring_extra<TW>();  // warp-uniform
+    const bool halo_warp = (tid & ~31) < ring_extra<T, TW>();  // warp-uniform
     const bool own_on = oend > z0, halo_on = hend > z0;
     int cq = z0;  // the next plane to copy
     // copy batch into slots sb * kB .. sb * kB + kB - 1
@@ -892,7 +899,7 @@ constexpr int kR2Ring = (kR2Ahead + 3) * kR2Batch;
 template <int TW>
 __host__ __device__ constexpr int ring2_rows()
 {
-    return 2 * kThreads / TW;
+    return 2 * kNT<float> / TW;
 }
 
 template <int TW>
@@ -1120,7 +1127,7 @@ __device__ __forceinline__ void f32_unit(float* pool, const BlockDesc* desc, int
         tile_engine_ring2<CG, TW>(pool, desc, b, p, x0, y0, z0, z1, jac_dyn_sm);
     } else {
         tile_engine_ring<float, true, CG, TW>(pool, desc, b, p, x0, y0, z0, z1, jac_dyn_sm);
-        tile_engine_ring<float, true, CG, TW>(pool, desc, b, p, x0, y0 + kThreads / TW, z0, z1, jac_dyn_sm);
+        tile_engine_ring<float, true, CG, TW>(pool, desc, b, p, x0, y0 + kNT<float> / TW, z0, z1, jac_dyn_sm);
     }
 }
 
@@ -1141,7 +1148,7 @@ __device__ __forceinline__ void with_tw(int tw, F&& f)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
+__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_ring(T* pool, const BlockDesc* desc, const TileUnit* units, int p)
 {
     const TileUnit u = units[blockIdx.x];
     with_tw(u.tw, [&](auto tw_c) {
@@ -1151,22 +1158,22 @@ __global__ void __launch_bounds__(kThreads, 2) k_fused_ring(T* pool, const Block
 }
 
 template <typename T, int OP, int TW>
-__global__ void __launch_bounds__(kThreads, 2) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                                int b, int p)
 {
     __shared__ SlowList slow;
     if constexpr (OP == OP_EXACT)
         tile_engine_pair<T, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                        blockIdx.y * (kThreads / TW), 0, desc[b].ext[2], jac_dyn_sm,
+                                                        blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
                                                         &slow);
     else
         tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                       blockIdx.y * (kThreads / TW), 0, desc[b].ext[2], jac_dyn_sm,
+                                                       blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
                                                        &slow);
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(kThreads, 2) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p)
 {
     __shared__ SlowList slow;
@@ -1212,7 +1219,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
 template <typename T, int OP, bool RING>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
@@ -1286,12 +1293,12 @@ __global__ void __launch_bounds__(kThreads, 2)
 // Residual: per CTA the sum over its tile of L^2 (L the exact Laplacian term
 // rounded once), in a fixed order (per thread over k, then a fixed tree).
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const BlockDesc* desc,
+__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_residual(const T* pool, const BlockDesc* desc,
                                                           const int32_t* frame_e, const TileUnit* units, int p,
                                                           double* partials)
 {
     __shared__ SlowList slow;
-    __shared__ double red[kThreads];
+    __shared__ double red[kNT<T>];
     const TileUnit u = units[blockIdx.x];
     double acc = 0.0;
     with_tw(u.tw, [&](auto tw_c) {
@@ -1303,14 +1310,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_residual(const T* pool, const B
             // a binary32 unit is two engine tiles tall
             __syncthreads();
             acc += tile_engine<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                  u.x0, u.y0 + kThreads / TW, u.z0, u.z1, jac_dyn_sm,
+                                                                  u.x0, u.y0 + kNT<float> / TW, u.z0, u.z1, jac_dyn_sm,
                                                                   &slow);
         }
     });
     const int tid = threadIdx.x;
     red[tid] = acc;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
+    for (int s = kNT<T> / 2; s > 0; s >>= 1) {
         if (tid < s) red[tid] = red[tid] + red[tid + s];
         __syncthreads();
     }
@@ -1497,8 +1504,8 @@ __global__ void k_init_ghosts(T* pool, const BlockDesc* desc)
 
 // ---------------------------------------------------------------- launchers
 
-int tile_rows(int tw, bool f32) { return (f32 ? 2 : 1) * kThreads / tw; }
-int engine_threads() { return kThreads; }
+int tile_rows(int tw, bool f32) { return f32 ? 2 * kNT<float> / tw : kNT<double> / tw; }
+int engine_threads(bool f32) { return f32 ? kNT<float> : kNT<double>; }
 bool tile_width_supported(int tw) { return tw == 16 || tw == 32 || tw == 64; }
 
 #define JAC_TW_DISPATCH(tw, CALL) \
@@ -1523,14 +1530,17 @@ bool tile_width_supported(int tw) { return tw == 16 || tw == 32 || tw == 64; }
 template <typename T, int TW>
 static void stencil_block_t(const LaunchArgs& a, int arith, int b, int nx_tiles, int ny_tiles, int p, cudaStream_t s)
 {
-    dim3 grid(nx_tiles, ny_tiles, 1);
+    // ny_tiles counts work-unit rows (1024 / TW for binary32); the stencil
+    // engine's tile is kNT<T> / TW rows
+    const int per = tile_rows(TW, sizeof(T) == 4) / (kNT<T> / TW);
+    dim3 grid(nx_tiles, ny_tiles * per, 1);
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_stencil_block<T, OP_EXACT, TW><<<grid, kThreads, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
+            k_stencil_block<T, OP_EXACT, TW><<<grid, kNT<T>, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
             return;
         }
     }
-    k_stencil_block<T, OP_SEQ, TW><<<grid, kThreads, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
+    k_stencil_block<T, OP_SEQ, TW><<<grid, kNT<T>, kernel_bytes<T, OP_SEQ, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
 }
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
@@ -1583,12 +1593,12 @@ static int residual_bytes(int tw_mask)
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
 {
     if (dtype_f32)
-        k_fused_ring<float><<<a.nunits, kThreads, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
+        k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
-        k_fused_step<double, OP_EXACT><<<a.nunits, kThreads, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+        k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p);
     else
-        k_fused_step<double, OP_SEQ><<<a.nunits, kThreads, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
+        k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p);
     return cudaGetLastError();
 }
@@ -1600,7 +1610,7 @@ const void* persistent_kernel(int dtype_f32, int arith)
                       : (const void*)k_persistent<double, OP_SEQ, false>;
 }
 
-int persistent_block_threads() { return kThreads; }
+int persistent_block_threads(int dtype_f32) { return dtype_f32 ? kNT<float> : kNT<double>; }
 
 int persistent_smem_bytes(int dtype_f32, int arith, int tw_mask)
 {
@@ -1650,15 +1660,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
                               cudaStream_t s)
 {
     if (dtype_f32)
-        k_persistent<float, OP_SEQ, true><<<ctas, kThreads, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
+        k_persistent<float, OP_SEQ, true><<<ctas, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     else if (arith == 1)
-        k_persistent<double, OP_EXACT, false><<<ctas, kThreads, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+        k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     else
-        k_persistent<double, OP_SEQ, false><<<ctas, kThreads, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
+        k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after);
     return cudaGetLastError();
@@ -1667,10 +1677,10 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
 cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
 {
     if (dtype_f32)
-        k_residual<float><<<a.nunits, kThreads, residual_bytes<float>(a.tw_mask), s>>>((const float*)a.pool, a.desc, a.frame,
+        k_residual<float><<<a.nunits, kNT<float>, residual_bytes<float>(a.tw_mask), s>>>((const float*)a.pool, a.desc, a.frame,
                                                                              a.units, p, partials);
     else
-        k_residual<double><<<a.nunits, kThreads, residual_bytes<double>(a.tw_mask), s>>>((const double*)a.pool, a.desc,
+        k_residual<double><<<a.nunits, kNT<double>, residual_bytes<double>(a.tw_mask), s>>>((const double*)a.pool, a.desc,
                                                                                a.frame, a.units, p, partials);
     return cudaGetLastError();
 }

@@ -34,9 +34,9 @@ struct PersistentArgs {
 
 // rows of a work unit's tile: 512 / tw (binary64), 1024 / tw (binary32: two columns per thread)
 int tile_rows(int tw, bool f32);
-int engine_threads();
+int engine_threads(bool f32);
 bool tile_width_supported(int tw);
-int persistent_block_threads();
+int persistent_block_threads(int dtype_f32);
 const void* persistent_kernel(int dtype_f32, int arith);
 // dynamic shared memory of a unit-kernel (fused, persistent) CTA whose units
 // use the tile widths in tw_mask (bit 0 = 16, 1 = 32, 2 = 64): only as much

@@ -1188,7 +1188,7 @@ int jac_iterate(jac_ctx* h, int64_t n)
             if (h->pctas == 0) {
                 int per_sm = 0, sms = 0;
                 CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
-                                                                 persistent_block_threads(),
+                                                                 persistent_block_threads(f32),
                                                                  persistent_smem_bytes(f32, h->arith, h->tw_mask)),
                    "occupancy");
                 CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");

@@ -311,3 +311,19 @@ def test_f32_error_against_f64_within_proven_bound():
     err = np.max(np.abs(u32 - u64))
     assert 0 < err <= bound
     assert abs(r32 - r64) <= 0.05 * r64
+
+
+@pytest.mark.parametrize("mode", ["unfused", "graph"])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_unfused_forms_cover_tall_blocks(mode, dtype):
+    """Per-block launches over blocks taller than one engine tile (64 rows,
+    and binary32 work units of two engine tiles) update every row."""
+    dims, block = (64, 64, 12), (64, 64, 6)
+    u0 = grid(31, dims)
+    if dtype == "f32":
+        u0 = u0.astype(np.float32)
+        want = oracle.jacobi_f32(u0, BC_MIXED, 4)
+    else:
+        want = oracle.jacobi(u0, BC_MIXED, 4, oracle.RULE_EXACT)
+    got, _ = run(u0, dims, block, 4, mode, bc=BC_MIXED, dtype=dtype)
+    assert np.array_equal(got, want)
