@@ -239,6 +239,7 @@ __host__ __device__ constexpr int smem_bytes()
 template <typename T, int TW>
 __host__ __device__ constexpr int ring_extra()
 {
+    static_assert(2 * TW + 2 * (kNT<T> / TW) <= kNT<T>, "every halo-ring slot needs a thread");
     return 2 * TW + 2 * (kNT<T> / TW);
 }
 
