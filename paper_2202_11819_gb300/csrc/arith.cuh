@@ -569,12 +569,11 @@ JAC_HD inline W96 of(double v, int eref)
     const bool ok = wn >= 0 && se - (uint32_t)lo_e <= (uint32_t)wn;
     const bool zero = ((hi & 0x7FFFFFFFu) | lo) == 0u;
     const int sc = (int)se - (eref - 31);  // 0 .. 30 when ok
-    const uint32_t mh = ok ? ((hi & 0xFFFFFu) | 0x100000u) : 0u;
-    const uint32_t ml = ok ? lo : 0u;
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
     W96 w;
-    w.w0 = fsl(0u, ml, sc & 31);
-    w.w1 = fsl(ml, mh, sc & 31);
-    w.w2 = fsl(mh, 0u, sc & 31) | ((ok || zero) ? 0u : kMarker);
+    w.w0 = ok ? fsl(0u, lo, sc & 31) : 0u;
+    w.w1 = ok ? fsl(lo, mh, sc & 31) : 0u;
+    w.w2 = ok ? fsl(mh, 0u, sc & 31) : (zero ? 0u : kMarker);
     w.w3 = 0u;
     return w;
 }
@@ -699,27 +698,47 @@ JAC_HD inline bool mean7(const W96& c, const W96& xm, const W96& xp, const W96& 
     return mean7_of_sum(s0, s1, s2, eref, out);
 }
 
-// The mean from a sum in the top binades of the frame: 2^80 <= S < 2^93
-// (top word in [2^16, kMarker)), for eref >= 7. Then N = S >> 23 is at
-// least 2^57 and Q = floor(N / 7) at least 2^54, so Q has two bits or more
-// below the binary64 rounding position: one correctly rounded conversion of
-// Q with the sticky bit (bits of S below 2^23, or a remainder) jammed into
-// its last bit rounds the exact mean. The result's exponent field is at
-// least eref - 6 >= 1 (a normal number) and S is not zero, so no per-cell
-// checks remain. The scale 2^(23 + eref - 1106) is the constant scale_hi =
-// (uint32_t)(eref - 1083) << 20 added to the high word of the conversion.
-JAC_HD inline bool sum_in_top(uint32_t s2) { return s2 - 65536u < kMarker - 65536u; }
+// The mean from a sum in the top binades of the frame: 2^82 <= S < 2^86
+// (top word in [2^18, 2^22); a sum of in-frame values is below 7 * 2^83), for
+// eref >= 7. Then N = S >> 25 lies in [2^57, 2^61) and Q = floor(N / 7) in
+// [2^54.19, 2^58.2), so Q has two bits or more below the binary64 rounding
+// position: one correctly rounded conversion of Q with the sticky bit (bits
+// of S below 2^25, or a remainder) jammed into its last bit rounds the exact
+// mean. The result's exponent field is at least eref - 4 >= 1 (a normal
+// number) and S is not zero, so no per-cell checks remain.
+//   Q is the high half of N * C with C = ceil(2^64 / 7) = (2^64 + 5) / 7:
+//   N C / 2^64 = N / 7 + 5 N / (7 2^64), and for N < 2^61 the excess is below
+//   5 / 56 < 1 / 7, so it never carries past the next integer (N / 7 has
+//   fractional part at most 6 / 7). The remainder N - 7 Q is then in [0, 6].
+// The scale 2^(25 + eref - 1106) is the constant scale_hi =
+// (uint32_t)(eref - 1081) << 20 added to the high word of the conversion.
+JAC_HD inline bool sum_in_top(uint32_t s2) { return s2 - (1u << 18) < (1u << 22) - (1u << 18); }
 
 JAC_HD inline double mean7_top(uint32_t s0, uint32_t s1, uint32_t s2, uint32_t scale_hi)
 {
-    const uint64_t N = ((uint64_t)fsr(s1, s2, 23) << 32) | fsr(s0, s1, 23);
-    const bool st0 = (s0 & 0x7FFFFFu) != 0u;
-    const uint64_t Qa = umulhi64(N, 0x2492492492492492ull);
-    const uint32_t Ra = (uint32_t)N - 7u * (uint32_t)Qa;
-    const uint32_t fix = Ra >= 7u ? 1u : 0u;
-    const uint64_t Q = Qa + fix;
-    const uint32_t R = Ra - 7u * fix;
-    const uint64_t qj = Q | ((R != 0u || st0) ? 1ull : 0ull);
+    const uint32_t nl = fsr(s0, s1, 25), nh = fsr(s1, s2, 25);  // N = S >> 25, nh < 2^29
+    uint32_t ql, qh;
+#if defined(__CUDA_ARCH__)
+    // high half of N * C over 32-bit limbs; the middle column
+    // lo(nl cl) carry + nl ch + nh cl stays below 2^62 (no carry out)
+    asm("{\n\t.reg .u32 t, m0, m1;\n\t"
+        "mul.hi.u32 t, %2, 0x92492493;\n\t"
+        "mad.lo.cc.u32 m0, %2, 0x24924924, t;\n\t"
+        "madc.hi.u32 m1, %2, 0x24924924, 0;\n\t"
+        "mad.lo.cc.u32 m0, %3, 0x92492493, m0;\n\t"
+        "madc.hi.u32 m1, %3, 0x92492493, m1;\n\t"
+        "mad.lo.cc.u32 %0, %3, 0x24924924, m1;\n\t"
+        "madc.hi.u32 %1, %3, 0x24924924, 0;\n\t"
+        "}"
+        : "=r"(ql), "=r"(qh)
+        : "r"(nl), "r"(nh));
+#else
+    const uint64_t q = umulhi64(((uint64_t)nh << 32) | nl, 0x2492492492492493ull);
+    ql = (uint32_t)q;
+    qh = (uint32_t)(q >> 32);
+#endif
+    const uint32_t sticky = (nl - 7u * ql) | (s0 & 0x1FFFFFFu);  // remainder, dropped bits
+    const uint64_t qj = ((uint64_t)qh << 32) | (ql | (sticky != 0u ? 1u : 0u));
     return bitsd(dbits(u64_to_double_rn(qj)) + ((uint64_t)scale_hi << 32));
 }
 

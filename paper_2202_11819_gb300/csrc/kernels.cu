@@ -606,7 +606,7 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     const int eref = frame_e[d.inst] + 1;
     const bool top_ok = eref >= 7;                          // frame::mean7_top applies
-    const uint32_t scale_hi = (uint32_t)(eref - 1083) << 20;  // its scale 2^(23 + eref - 1106)
+    const uint32_t scale_hi = (uint32_t)(eref - 1081) << 20;  // its scale 2^(25 + eref - 1106)
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const int x = x0 + tx, y = y0 + ty;
     const int64_t plane = d.plane;
@@ -656,11 +656,13 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     auto copy_pair = [&](int sl) {  // plane-iterations next, next + 1 into slots sl, sl + 1
         cp_async_if<sizeof(T)>(rc_s + sl * kRowC, osrc, next < olim);
         cp_async_if<sizeof(T)>(rc_s + (sl + 1) * kRowC, osrc + ostr, next + 1 < olim);
-        cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
-        cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+        if (halo_warp) {  // warps without a halo slot issue no halo copies
+            cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
+            cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+            hsrc += 2 * hstr;
+        }
         cp_async_commit();
         osrc += 2 * ostr;
-        hsrc += 2 * hstr;
         next += 2;
     };
 #pragma unroll

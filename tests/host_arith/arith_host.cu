@@ -49,7 +49,7 @@ extern "C" int host_frame_mean7_top(const double* v, int eref, double* out)
     uint32_t s0, s1, s2;
     sum7(w[0], w[1], w[2], w[3], w[4], w[5], w[6], s0, s1, s2);
     if (eref < 7 || !sum_in_top(s2)) return 0;
-    *out = mean7_top(s0, s1, s2, (uint32_t)(eref - 1083) << 20);
+    *out = mean7_top(s0, s1, s2, (uint32_t)(eref - 1081) << 20);
     return 1;
 }
 

@@ -239,15 +239,16 @@ def test_grid_frame_mean7_top_binades_fast_path(host_lib):
 
 
 
-def tie_cases(rng, n):
+def tie_cases(rng, n, w_exp=20, eps_exp=70):
     """Triples of seven doubles around a binary64 midpoint t in [0.5, 1):
-    the exact mean is t (a tie), or t plus or minus 2^-70 / 7, where the bits
-    that decide the rounding lie far below the 53rd and below the top 64 bits
-    of the frame sum. Values: five in [0.5, 1), one in [0.25, 0.5) and
-    w = 2^-20 (+- 2^-70)."""
+    the exact mean is t (a tie), or t plus or minus eps / 7 with eps =
+    2^-eps_exp, where the bits that decide the rounding lie far below the
+    53rd (with a frame whose top binade is [1, 2), eps is bit 82 - eps_exp
+    of the frame sum). Values: five in [0.5, 1), one in [0.25, 0.5) and
+    w = 2^-w_exp (+- eps)."""
     out = []
-    w = Fraction(1, 2 ** 20)
-    eps = Fraction(1, 2 ** 70)
+    w = Fraction(1, 2 ** w_exp)
+    eps = Fraction(1, 2 ** eps_exp)
     while len(out) < 3 * n:
         t = Fraction(2 * int(rng.integers(2 ** 52, 2 ** 53)) + 1, 2 ** 54)  # odd multiple of 2^-54 in [0.5, 1)
         target = 7 * t - w
@@ -275,7 +276,11 @@ def test_grid_frame_mean7_ties_and_sticky_near_ties(host_lib):
     rng = np.random.default_rng(14)
     out = ctypes.c_double()
     n_top = n_gen = 0
-    for vals in tie_cases(rng, 400):
+    # the deciding bit: 12 (deep in the dropped bits), 24 (the last bit the
+    # fixed-shift mean drops), 25 (the first it keeps), 1 (near the bottom)
+    cases = (tie_cases(rng, 100, 20, 70) + tie_cases(rng, 100, 20, 58) + tie_cases(rng, 100, 20, 57)
+             + tie_cases(rng, 100, 29, 81))
+    for vals in cases:
         a = np.ascontiguousarray(vals, dtype=np.float64)
         want = oracle.exact_mean7(a)
         exact = sum(Fraction(float(x)) for x in a) / 7
@@ -347,3 +352,20 @@ def test_binary32_residual_frame(host_lib):
     for L in ([0], [1], [-1], [2 ** 62 - 1] * 200, [3, -4]):
         a = np.ascontiguousarray(L, dtype=np.int64)
         assert host_lib.host_sum_squares(a.ctypes.data, len(L), 0) == float(sum(Fraction(int(x)) ** 2 for x in L))
+
+
+def test_top_quotient_multiplier_has_no_overshoot_below_2_61():
+    """floor(N * ceil(2^64 / 7) / 2^64) = floor(N / 7) for every N < 2^61,
+    the range of N = S >> 25 on the fixed-shift path: the multiplier's excess
+    5 N / (7 2^64) stays below 1 / 7. Checked on random N, on the largest N of
+    each residue class, and shown to fail further up (the bound is needed)."""
+    c = (2 ** 64 + 5) // 7
+    assert 7 * c == 2 ** 64 + 5
+    rng = np.random.default_rng(16)
+    ns = [int(x) for x in rng.integers(2 ** 57, 2 ** 61, size=20000, dtype=np.uint64)]
+    ns += [2 ** 61 - 1 - k for k in range(64)] + [2 ** 57 + k for k in range(64)]
+    for n in ns:
+        assert (n * c) >> 64 == n // 7, n
+    # above 2^64 / 5 the excess can carry past the next integer
+    bad = [n for n in (2 ** 64 - 1 - k for k in range(14)) if (n * c) >> 64 != n // 7]
+    assert bad
