@@ -517,7 +517,7 @@ JAC_HD inline uint32_t fsl(uint32_t lo, uint32_t hi, int s)  // ((hi:lo) << s) >
 #if defined(__CUDA_ARCH__)
     return __funnelshift_l(lo, hi, s);
 #else
-    return (uint32_t)(((((uint64_t)hi << 32) | lo) << s) >> 32);
+    return (uint32_t)(((((uint64_t)hi << 32) | lo) << (s & 31)) >> 32);
 #endif
 }
 
@@ -571,9 +571,9 @@ JAC_HD inline W96 of(double v, int eref)
     const int sc = (int)se - (eref - 31);  // 0 .. 30 when ok
     const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
     W96 w;
-    w.w0 = ok ? fsl(0u, lo, sc & 31) : 0u;
-    w.w1 = ok ? fsl(lo, mh, sc & 31) : 0u;
-    w.w2 = ok ? fsl(mh, 0u, sc & 31) : (zero ? 0u : kMarker);
+    w.w0 = ok ? fsl(0u, lo, sc) : 0u;
+    w.w1 = ok ? fsl(lo, mh, sc) : 0u;
+    w.w2 = ok ? fsl(mh, 0u, sc) : (zero ? 0u : kMarker);
     w.w3 = 0u;
     return w;
 }
@@ -646,6 +646,37 @@ JAC_HD inline void sum7(const W96& a, const W96& b, const W96& c, const W96& d, 
     s0 = (uint32_t)lo;
     s1 = (uint32_t)(lo >> 32);
     s2 = hi;
+#endif
+}
+
+// S = a + b + c + d + e + f over 96 bits, in one carry chain.
+JAC_HD inline void sum6(const W96& a, const W96& b, const W96& c, const W96& d, const W96& e, const W96& f,
+                        uint32_t& s0, uint32_t& s1, uint32_t& s2)
+{
+#if defined(__CUDA_ARCH__)
+    asm("add.cc.u32 %0, %3, %6;\n\t"
+        "addc.cc.u32 %1, %4, %7;\n\t"
+        "addc.u32 %2, %5, %8;\n\t"
+        "add.cc.u32 %0, %0, %9;\n\t"
+        "addc.cc.u32 %1, %1, %10;\n\t"
+        "addc.u32 %2, %2, %11;\n\t"
+        "add.cc.u32 %0, %0, %12;\n\t"
+        "addc.cc.u32 %1, %1, %13;\n\t"
+        "addc.u32 %2, %2, %14;\n\t"
+        "add.cc.u32 %0, %0, %15;\n\t"
+        "addc.cc.u32 %1, %1, %16;\n\t"
+        "addc.u32 %2, %2, %17;\n\t"
+        "add.cc.u32 %0, %0, %18;\n\t"
+        "addc.cc.u32 %1, %1, %19;\n\t"
+        "addc.u32 %2, %2, %20;"
+        : "=&r"(s0), "=&r"(s1), "=&r"(s2)
+        : "r"(a.w0), "r"(a.w1), "r"(a.w2), "r"(b.w0), "r"(b.w1), "r"(b.w2), "r"(c.w0), "r"(c.w1), "r"(c.w2),
+          "r"(d.w0), "r"(d.w1), "r"(d.w2), "r"(e.w0), "r"(e.w1), "r"(e.w2), "r"(f.w0), "r"(f.w1), "r"(f.w2));
+#else
+    const W96 t = add(add(add(a, b), add(c, d)), add(e, f));
+    s0 = t.w0;
+    s1 = t.w1;
+    s2 = t.w2;
 #endif
 }
 

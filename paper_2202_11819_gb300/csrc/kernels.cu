@@ -648,10 +648,13 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     const T* hsrc = hs.p;
     const int64_t hstr = hs.stride;
     const int hlim = hv ? z1 : z0;
-    const bool halo_warp = (tid & ~31) < kEr;  // warp-uniform
+    // a warp with a halo slot (from a vote, so the compiler treats the
+    // branches on it as warp-uniform)
+    const bool halo_warp = __any_sync(0xffffffffu, tid < kEr);
     const int own = (ty + 1) * kSW + tx + 1;
     const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + tid);
-    const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(re + (tid < kEr ? tid : 0));
+    const T* const mye = re + (tid < kEr ? tid : 0);  // ring slot s: mye[s * kEr]
+    const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(mye);
     int next = z0;  // the next plane-iteration to copy
     auto copy_pair = [&](int sl) {  // plane-iterations next, next + 1 into slots sl, sl + 1
         cp_async_if<sizeof(T)>(rc_s + sl * kRowC, osrc, next < olim);
@@ -671,8 +674,9 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
 
     int s = 0;  // ring slot of plane-iteration k (even)
     int bsel = 0;
-    auto step = [&](auto two_c, int k) {
+    auto step = [&](auto two_c, auto last_c, int k) {
         constexpr bool TWO = decltype(two_c)::value;
+        constexpr bool LAST = decltype(last_c)::value;  // plane z1 may be among k+1, k+2
         copy_pair(s == 0 ? RD - 2 : s - 2);
         cp_async_wait<RD / 2 - 1>();  // this thread's copies for k, k+1 have landed
         E* const b0 = sm + bsel * (2 * kPlane);
@@ -680,42 +684,45 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         const T v0 = rc[s * kN + tid];
         const T v1 = rc[(s + 1) * kN + tid];
         // planes k+1, k+2 of the own column (plane z1 from the register)
-        const E c0 = frame::of((double)(k + 1 >= z1 ? zhiv : v0), eref);
-        const E c1 = frame::of((double)(k + 2 >= z1 ? zhiv : v1), eref);
+        const E c0 = frame::of((double)(LAST && k + 1 >= z1 ? zhiv : v0), eref);
+        const E c1 = frame::of((double)(LAST && k + 2 >= z1 ? zhiv : v1), eref);
         b0[own] = wc;
         if (TWO) b1[own] = c0;
         if (halo_warp) {
-            b0[hslot] = frame::of((double)re[s * kEr + (tid < kEr ? tid : 0)], eref);
-            if (TWO) b1[hslot] = frame::of((double)re[(s + 1) * kEr + (tid < kEr ? tid : 0)], eref);
+            b0[hslot] = frame::of((double)mye[s * kEr], eref);
+            if (TWO) b1[hslot] = frame::of((double)mye[(s + 1) * kEr], eref);
         }
         __syncthreads();
         double o0, o1 = 0.0;
         bool ok0 = true, ok1 = true;
-        uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 65536u;
-        frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
-        if (TWO) frame::sum7(c0, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], wc, c1, e0, e1, e2);
+        uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 0u;
+        if (TWO) {  // planes k and k+1 share the term wc + c0
+            const E t = frame::add(wc, c0);
+            frame::sum6(t, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, a0, a1, a2);
+            frame::sum6(t, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], c1, e0, e1, e2);
+        } else {
+            frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
+        }
         // the fixed-shift mean when every computing lane's sums lie in the
         // top binades of the frame (nearly always), else the general one
-        const bool top = top_ok && frame::sum_in_top(a2) && frame::sum_in_top(e2);
+        const bool top = top_ok && frame::sum_in_top(a2) && (!TWO || frame::sum_in_top(e2));
         if (__all_sync(0xffffffffu, top || !k1)) {
             o0 = frame::mean7_top(a0, a1, a2, scale_hi);
             if (TWO) o1 = frame::mean7_top(e0, e1, e2, scale_hi);
         } else {
             ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
             if (TWO) ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
-        }
-        if (k1 && ok0) out[0] = (T)o0;
-        if (TWO && k1 && ok1) out[plane] = (T)o1;
-        if (k1 && !(ok0 && ok1)) {
-            if (!ok0) {
+            if (k1 && !ok0) {
                 const int i = atomicAdd(&slow->n, 1);
                 if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
             }
-            if (!ok1) {
+            if (TWO && k1 && !ok1) {
                 const int i = atomicAdd(&slow->n, 1);
                 if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
             }
         }
+        if (k1 && ok0) out[0] = (T)o0;
+        if (TWO && k1 && ok1) out[plane] = (T)o1;
         out += 2 * plane;
         wzm = c0;
         wc = c1;
@@ -723,8 +730,19 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         bsel ^= 1;
     };
     int k = z0;
-    for (; k + 1 < z1; k += 2) step(std::true_type{}, k);
-    if (k < z1) step(std::false_type{}, k);
+    // two steps per pass (the carried planes alternate registers), planes
+    // k+1 .. k+4 below z1 (all from the ring); the last one to four planes
+    // after the loop
+    for (; k + 4 < z1; k += 4) {
+        step(std::true_type{}, std::false_type{}, k);
+        step(std::true_type{}, std::false_type{}, k + 2);
+    }
+    if (k + 2 < z1) {
+        step(std::true_type{}, std::false_type{}, k);
+        k += 2;
+    }
+    if (k + 1 < z1) step(std::true_type{}, std::true_type{}, k);
+    else if (k < z1) step(std::false_type{}, std::true_type{}, k);
     cp_async_wait<0>();
     slow_cells<T, OP_EXACT, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y,
                                           cell_index<T>(d, p ^ 1, x, y, 0), 0.0, slow);
