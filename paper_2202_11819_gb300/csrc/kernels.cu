@@ -693,8 +693,6 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
             if (TWO) b1[hslot] = frame::of((double)mye[(s + 1) * kEr], eref);
         }
         __syncthreads();
-        double o0, o1 = 0.0;
-        bool ok0 = true, ok1 = true;
         uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 0u;
         if (TWO) {  // planes k and k+1 share the term wc + c0
             const E t = frame::add(wc, c0);
@@ -704,25 +702,33 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
             frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
         }
         // the fixed-shift mean when every computing lane's sums lie in the
-        // top binades of the frame (nearly always), else the general one
+        // top binades of the frame (nearly always), else the general one;
+        // each branch stores its own results
         const bool top = top_ok && frame::sum_in_top(a2) && (!TWO || frame::sum_in_top(e2));
         if (__all_sync(0xffffffffu, top || !k1)) {
-            o0 = frame::mean7_top(a0, a1, a2, scale_hi);
-            if (TWO) o1 = frame::mean7_top(e0, e1, e2, scale_hi);
+            const double o0 = frame::mean7_top(a0, a1, a2, scale_hi);
+            if (k1) out[0] = (T)o0;
+            if (TWO) {
+                const double o1 = frame::mean7_top(e0, e1, e2, scale_hi);
+                if (k1) out[plane] = (T)o1;
+            }
         } else {
-            ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
-            if (TWO) ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
+            double o0, o1;
+            const bool ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
+            if (k1 && ok0) out[0] = (T)o0;
             if (k1 && !ok0) {
                 const int i = atomicAdd(&slow->n, 1);
                 if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
             }
-            if (TWO && k1 && !ok1) {
-                const int i = atomicAdd(&slow->n, 1);
-                if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+            if (TWO) {
+                const bool ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
+                if (k1 && ok1) out[plane] = (T)o1;
+                if (k1 && !ok1) {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+                }
             }
         }
-        if (k1 && ok0) out[0] = (T)o0;
-        if (TWO && k1 && ok1) out[plane] = (T)o1;
         out += 2 * plane;
         wzm = c0;
         wc = c1;
