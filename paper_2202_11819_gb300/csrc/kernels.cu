@@ -642,26 +642,38 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         olim = z1 - 1;
         wc = frame::of((double)ldv<T, CG>(s.p + z0 * s.stride), eref);
     }
-    const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid);
+    // halo-ring slots: with kSplit (2 kEr threads available) thread
+    // (hq, hj) = (tid / kEr, tid % kEr) streams slot hj for the planes of
+    // parity hq, one copy and one conversion per step; otherwise thread hj =
+    // tid < kEr streams slot hj for both planes of a step
+    constexpr bool kSplit = 2 * kEr <= kN;
+    constexpr int kHT = kSplit ? 2 * kEr : kEr;  // threads with a halo role
+    const int hq = kSplit && tid >= kEr ? 1 : 0;
+    const int hj = tid - hq * kEr;
+    const HaloSlot<T> hs = halo_slot<T, PULL, TW>(pool, desc, d, p, x0, y0, z0, tid < kHT ? hj : kN);
     const bool hv = hs.er >= 0;
-    const int hslot = hv ? hs.er * kSW + hs.ec : kPlane - 1;
-    const T* hsrc = hs.p;
+    const int hslot = (hv ? hs.er * kSW + hs.ec : kPlane - 1) + hq * kPlane;  // in buffer hq of the pair
     const int64_t hstr = hs.stride;
+    const T* hsrc = hs.p + hq * hstr;
     const int hlim = hv ? z1 : z0;
-    // a warp with a halo slot (from a vote, so the compiler treats the
+    // a warp with a halo role (from a vote, so the compiler treats the
     // branches on it as warp-uniform)
-    const bool halo_warp = __any_sync(0xffffffffu, tid < kEr);
+    const bool halo_warp = __any_sync(0xffffffffu, tid < kHT);
     const int own = (ty + 1) * kSW + tx + 1;
     const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + tid);
-    const T* const mye = re + (tid < kEr ? tid : 0);  // ring slot s: mye[s * kEr]
+    const T* const mye = re + (tid < kHT ? hj : 0) + hq * kEr;  // ring slot s: mye[s * kEr]
     const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(mye);
     int next = z0;  // the next plane-iteration to copy
     auto copy_pair = [&](int sl) {  // plane-iterations next, next + 1 into slots sl, sl + 1
         cp_async_if<sizeof(T)>(rc_s + sl * kRowC, osrc, next < olim);
         cp_async_if<sizeof(T)>(rc_s + (sl + 1) * kRowC, osrc + ostr, next + 1 < olim);
-        if (halo_warp) {  // warps without a halo slot issue no halo copies
-            cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
-            cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+        if (halo_warp) {  // warps without a halo role issue no halo copies
+            if constexpr (kSplit) {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next + hq < hlim);
+            } else {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
+                cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+            }
             hsrc += 2 * hstr;
         }
         cp_async_commit();
@@ -689,8 +701,12 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         b0[own] = wc;
         if (TWO) b1[own] = c0;
         if (halo_warp) {
-            b0[hslot] = frame::of((double)mye[s * kEr], eref);
-            if (TWO) b1[hslot] = frame::of((double)mye[(s + 1) * kEr], eref);
+            if constexpr (kSplit) {
+                if (TWO || hq == 0) b0[hslot] = frame::of((double)mye[s * kEr], eref);
+            } else {
+                b0[hslot] = frame::of((double)mye[s * kEr], eref);
+                if (TWO) b1[hslot] = frame::of((double)mye[(s + 1) * kEr], eref);
+            }
         }
         __syncthreads();
         uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 0u;
