@@ -87,8 +87,9 @@ JAC_HD inline uint64_t mulhi_u64(uint64_t a, uint64_t b)
 }
 
 // RN(s / 7) for a binary64 s whose exponent field e is in [4, 2046] (so s
-// and the quotient are normal), in integer arithmetic plus one integer ->
-// binary64 conversion. N = significand << 11 lies in [2^63, 2^64); Qa, the
+// and the quotient are normal), in integer arithmetic only (no binary64
+// instruction: the sequential rule's six additions already fill that pipe).
+// N = significand << 11 lies in [2^63, 2^64); Qa, the
 // high word of N * floor(2^64/7), is floor(N/7) or one less, and has 61 or 62
 // bits, so converting it rounds away its d = 8 or 9 low bits. That rounding
 // equals the rounding of the exact quotient N/7: the two could differ only
@@ -106,19 +107,57 @@ JAC_HD inline bool div7d(double s, double& out)
     const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
     const uint64_t N = (((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 11);
     const uint64_t Qa = mulhi_u64(N, 0x2492492492492492ull);
-#if defined(__CUDA_ARCH__)
-    const uint64_t qb = dbits(__ull2double_rn(Qa));
-#else
-    const uint64_t qb = dbits((double)(int64_t)Qa);
-#endif
-    out = bitsd((qb + ((uint64_t)((int64_t)e - 1086) << 52)) | (b & 0x8000000000000000ull));
+    // RN(Qa) to 53 bits, ties to even, by adding 2^(k-1) - 1 plus bit k and
+    // dropping the k low bits (k = 8 or 9): R in [2^52, 2^53], RN(Qa) = R 2^k.
+    // Then RN(Qa) has exponent field 1074 + k + (R's hidden bit), so adding R
+    // to (1074 + k + e - 1086) << 52 both encodes it and applies the rescale
+    // (a carry of R into 2^53 moves to the next binade by itself).
+    const int k = (uint32_t)(Qa >> 32) >= (1u << 29) ? 9 : 8;
+    const uint64_t R = (Qa + (((1ull << (k - 1)) - 1u) + ((Qa >> k) & 1u))) >> k;
+    out = bitsd((R + ((uint64_t)((int)e + k - 12) << 52)) | (b & 0x8000000000000000ull));
     return e >= 4u && e <= 2046u;
+}
+
+// RN(a + b) for binary64 a, b >= 0 in integer arithmetic. Returns false
+// (out unset) unless the larger has exponent field in [1, 2044] and the
+// smaller is normal in that range or +0; then the sum is normal and finite.
+// With hi >= lo (nonnegative doubles order like their bits) and d the
+// difference of their exponent fields, the significands shifted left by 10
+// are mh in [2^62, 2^63) and ml; ml >> min(d, 63) is added to mh, and the
+// bits it drops become a sticky bit in bit 0 (below the rounding point, which
+// is bit 10, or bit 11 when the sum reaches 2^63). For d >= 54 the result is
+// hi, as lo is then below half an ulp of hi: the sticky bit alone gives
+// that. Rounding to nearest, ties to even, adds 2^(k-1) - 1 plus bit k and
+// drops k bits; R in [2^52, 2^53] then encodes with exponent field
+// eh - 11 + k + (R's hidden bit), a carry into 2^53 moving up a binade.
+JAC_HD inline bool dadd_nonneg(double a, double b, double& out)
+{
+    const uint64_t x = dbits(a), y = dbits(b);
+    const uint64_t hi = x > y ? x : y, lo = x > y ? y : x;
+    const uint32_t eh = (uint32_t)(hi >> 52), el = (uint32_t)(lo >> 52);  // >= 2048 with the sign bit
+    const bool lo_zero = lo == 0u;
+    const bool ok = eh - 1u < 2044u && (el - 1u < 2044u || lo_zero);
+    const uint32_t dd = eh - el;
+    const int d = (int)(dd < 63u ? dd : 63u);
+    const uint64_t mh = ((hi & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    const uint64_t ml = ((lo & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << 10;
+    const uint64_t sh = ml >> d;
+    const uint64_t S = (mh + sh) | ((sh << d) != ml ? 1u : 0u);
+    const int k = (S >> 63) != 0u ? 11 : 10;
+    const uint64_t R = (S + (((1ull << (k - 1)) - 1u) + ((S >> k) & 1u))) >> k;
+    const uint64_t r = R + ((uint64_t)((int)eh - 11 + k) << 52);
+    out = bitsd(lo_zero ? hi : r);
+    return ok;
 }
 
 __device__ __forceinline__ double mean7_seq(double c, double xm, double xp, double ym, double yp,
                                             double zm, double zp)
 {
-    double s = __dadd_rn(c, xm);
+    // the first two additions in integer arithmetic (this rule is bound by
+    // the binary64 pipe); a lane whose values do not qualify takes the pipe
+    double s;
+    const bool ok1 = dadd_nonneg(c, xm, s);
+    if (!ok1) s = __dadd_rn(c, xm);
     s = __dadd_rn(s, xp);
     s = __dadd_rn(s, ym);
     s = __dadd_rn(s, yp);

@@ -55,6 +55,13 @@ extern "C" int host_frame_mean7_top(const double* v, int eref, double* out)
 
 // The binary64 division by 7 of the sequential rule: 1 and RN(s / 7) when
 // its integer path applies, else 0.
+// The integer addition of the sequential rule: 1 and RN(a + b) when it
+// applies, else 0.
+extern "C" int host_dadd_nonneg(double a, double b, double* out)
+{
+    return jac::dadd_nonneg(a, b, *out) ? 1 : 0;
+}
+
 extern "C" int host_div7d(double s, double* out)
 {
     return jac::div7d(s, *out) ? 1 : 0;

@@ -321,6 +321,59 @@ def test_div7d_matches_correctly_rounded_division(host_lib):
     assert applied > 190000
 
 
+def test_dadd_nonneg_matches_ieee_addition(host_lib):
+    """The integer addition of the sequential rule equals IEEE binary64
+    addition (round to nearest even) wherever it applies: random pairs over
+    every exponent gap (0 to 70), exact ties, carries into the next binade,
+    zeros, the top of its range, and refusal (return 0) for negative,
+    subnormal, infinite, NaN and too-large operands."""
+    host_lib.host_dadd_nonneg.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    host_lib.host_dadd_nonneg.restype = ctypes.c_int
+    rng = np.random.default_rng(17)
+    out = ctypes.c_double()
+    pairs = []
+    n = 60000
+    ea = rng.integers(1, 2045, size=n)
+    gap = rng.integers(0, 71, size=n)
+    eb = np.maximum(ea - gap, 1)
+    ma = rng.integers(0, 2 ** 52, size=n, dtype=np.uint64)
+    mb = rng.integers(0, 2 ** 52, size=n, dtype=np.uint64)
+    a = ((ea.astype(np.uint64) << np.uint64(52)) | ma).view(np.float64)
+    b = ((eb.astype(np.uint64) << np.uint64(52)) | mb).view(np.float64)
+    pairs += list(zip(a, b)) + list(zip(b, a))
+    # exact ties and near-ties: b is half an ulp of a (times an odd factor) or just off it
+    for _ in range(4000):
+        e = int(rng.integers(-200, 200))
+        av = float(np.ldexp(1.0 + int(rng.integers(0, 2 ** 52)) * 2.0 ** -52, e))
+        half = float(np.ldexp(1.0, e - 53))
+        for f in (1.0, 3.0, 1.0 + 2.0 ** -40, 1.0 - 2.0 ** -40, 2.0 ** -10, 5.0):
+            pairs.append((av, half * f))
+    # carries into the next binade
+    for e in (-1000, -3, 0, 1, 700, 1020):
+        top = float(np.ldexp(2.0 - 2.0 ** -52, e))
+        for bv in (np.ldexp(1.0, e - 52), np.ldexp(1.0, e - 53), np.ldexp(1.5, e - 53), np.ldexp(1.0, e)):
+            pairs.append((top, float(bv)))
+    pairs += [(0.0, 1.0), (1.0, 0.0), (0.0, 0.0), (1.0, 1.0), (0.5, 0.25), (1.7976931348623157e308, 1.0)]
+    applied = 0
+    for x, y in pairs:
+        x, y = float(x), float(y)
+        if host_lib.host_dadd_nonneg(x, y, ctypes.byref(out)):
+            applied += 1
+            want = np.float64(x) + np.float64(y)
+            assert np.float64(out.value).tobytes() == want.tobytes(), (x, y)
+        else:
+            hi = max(x, y)
+            lo = min(x, y)
+            eh = int(np.float64(hi).view(np.uint64) >> np.uint64(52))
+            el = int(np.float64(lo).view(np.uint64) >> np.uint64(52))
+            assert not (1 <= eh <= 2044 and (1 <= el <= 2044 or lo == 0.0)), (x, y)
+    assert applied > 0.95 * len(pairs)
+    assert host_lib.host_dadd_nonneg(0.0, 0.0, ctypes.byref(out)) == 0  # +0 alone: the larger must be normal
+    for bad in ((-1.0, 1.0), (1.0, -0.5), (5e-324, 1.0), (float("inf"), 1.0), (float("nan"), 1.0),
+                (float(np.ldexp(1.0, 1022)), 1.0), (1.0, -0.0)):
+        assert host_lib.host_dadd_nonneg(bad[0], bad[1], ctypes.byref(out)) == 0, bad
+
+
 def test_binary32_residual_frame(host_lib):
     """The binary32 residual's 64-bit frame: values convert exactly (value =
     w * 2^(eref32 - 186)) inside the 36-binade window and are flagged outside
