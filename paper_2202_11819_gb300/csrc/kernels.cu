@@ -556,16 +556,25 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
 // holds two planes, double-buffered; the ring, its slots and the slow list
 // are those of the single-plane engine (RD even). A range with an odd number
 // of planes ends with a single-plane step.
-template <typename T, int TW>
+// Ops the pair engine runs: the exact mean and the residuals (the
+// sequential rule keeps the single-plane engine: it is bound by the binary64
+// pipe either way). Its exchange element is the op's frame value.
+template <int OP>
+constexpr bool kPairOp = OP == OP_EXACT || OP == OP_RES || OP == OP_RES32;
+
+template <int OP>
+using PairElem = std::conditional_t<OP == OP_RES32, int64_t, frame::W96>;
+
+template <typename T, int OP, int TW>
 __host__ __device__ constexpr int pair_smem_bytes()
 {
-    return 4 * ((kNT<T> / TW + 2) * (TW + 2) + 1) * (int)sizeof(frame::W96);
+    return 4 * ((kNT<T> / TW + 2) * (TW + 2) + 1) * (int)sizeof(PairElem<OP>);
 }
 
-template <typename T, int TW, int RD>
+template <typename T, int OP, int TW, int RD>
 __host__ __device__ constexpr int pair_engine_bytes()
 {
-    return pair_smem_bytes<T, TW>() + RD * (kNT<T> + ring_extra<T, TW>()) * (int)sizeof(T);
+    return pair_smem_bytes<T, OP, TW>() + RD * (kNT<T> + ring_extra<T, TW>()) * (int)sizeof(T);
 }
 
 // cp.async of one 8- or 4-byte value, issued only when `on` (a predicated
@@ -589,22 +598,39 @@ __device__ __forceinline__ void cp_async_if_off(uint32_t dst, const void* src, b
         : "memory");
 }
 
-template <typename T, bool PULL, bool CG, int RD, int TW>
-__device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
-                                 const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
-                                 unsigned char* smraw, SlowList* slow)
+template <typename T, int OP, bool PULL, bool CG, int RD, int TW>
+__device__ double tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                                   const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
+                                   unsigned char* smraw, SlowList* slow)
 {
-    using E = frame::W96;
+    static_assert(kPairOp<OP>, "op");
+    using E = PairElem<OP>;
     constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
     constexpr int kPlane = (kTY + 2) * kSW + 1;  // + one slot written by threads without a halo slot
     constexpr uint32_t kRowC = kN * sizeof(T), kRowE = kEr * sizeof(T);
     static_assert(RD >= 4 && RD % 2 == 0, "ring depth");
     E* const sm = (E*)smraw;                                   // [2 buffers][2 planes][kPlane]
-    T* const rc = (T*)(smraw + pair_smem_bytes<T, TW>());      // [RD][kN]
+    T* const rc = (T*)(smraw + pair_smem_bytes<T, OP, TW>());  // [RD][kN]
     T* const re = rc + RD * kN;                                // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int eref = frame_e[d.inst] + 1;
+    // OP_RES32: eref is the binary32 exponent field + 1 (frame_e holds the
+    // binary64 field of the largest value)
+    const int eref = OP == OP_RES32 ? frame_e[d.inst] + 1 - 896 : frame_e[d.inst] + 1;
+    bool bad = false;                    // OP_RES32: a value outside the 64-bit frame
+    uint64_t q0 = 0u, q1 = 0u, q2 = 0u;  // OP_RES32: this thread's sum of L^2 in frame units
+    double acc = 0.0;                    // OP_RES: this thread's sum of L^2
+    // a value as an exchange element (its frame value)
+    auto cvt = [&](T v, int er) -> E {
+        if constexpr (OP == OP_RES32) {
+            bool ok;
+            const int64_t w = frame::of32((float)v, er, ok);
+            bad |= !ok;
+            return w;
+        } else {
+            return frame::of((double)v, er);
+        }
+    };
     const bool top_ok = eref >= 7;                          // frame::mean7_top applies
     const uint32_t scale_hi = (uint32_t)(eref - 1081) << 20;  // its scale 2^(25 + eref - 1106)
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
@@ -631,8 +657,8 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         zhiv = ldv<T, CG>(z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane);
         out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
         const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
-        wzm = frame::of((double)ldv<T, CG>(zlo), eref);
-        wc = frame::of((double)ldv<T, CG>(col + z0 * plane), eref);
+        wzm = cvt(ldv<T, CG>(zlo), eref);
+        wc = cvt(ldv<T, CG>(col + z0 * plane), eref);
     } else if (k2) {
         // a halo cell inside the tile streams like an interior column (its
         // own plane carried, the plane above copied), without computing
@@ -640,7 +666,7 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         osrc = s.p + (z0 + 1) * s.stride;
         ostr = s.stride;
         olim = z1 - 1;
-        wc = frame::of((double)ldv<T, CG>(s.p + z0 * s.stride), eref);
+        wc = cvt(ldv<T, CG>(s.p + z0 * s.stride), eref);
     }
     // halo-ring slots: with kSplit (2 kEr threads available) thread
     // (hq, hj) = (tid / kEr, tid % kEr) streams slot hj for the planes of
@@ -696,52 +722,78 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
         const T v0 = rc[s * kN + tid];
         const T v1 = rc[(s + 1) * kN + tid];
         // planes k+1, k+2 of the own column (plane z1 from the register)
-        const E c0 = frame::of((double)(LAST && k + 1 >= z1 ? zhiv : v0), eref);
-        const E c1 = frame::of((double)(LAST && k + 2 >= z1 ? zhiv : v1), eref);
+        const E c0 = cvt((LAST && k + 1 >= z1 ? zhiv : v0), eref);
+        const E c1 = cvt((LAST && k + 2 >= z1 ? zhiv : v1), eref);
         b0[own] = wc;
         if (TWO) b1[own] = c0;
         if (halo_warp) {
             if constexpr (kSplit) {
-                if (TWO || hq == 0) b0[hslot] = frame::of((double)mye[s * kEr], eref);
+                if (TWO || hq == 0) b0[hslot] = cvt(mye[s * kEr], eref);
             } else {
-                b0[hslot] = frame::of((double)mye[s * kEr], eref);
-                if (TWO) b1[hslot] = frame::of((double)mye[(s + 1) * kEr], eref);
+                b0[hslot] = cvt(mye[s * kEr], eref);
+                if (TWO) b1[hslot] = cvt(mye[(s + 1) * kEr], eref);
             }
         }
         __syncthreads();
-        uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 0u;
-        if (TWO) {  // planes k and k+1 share the term wc + c0
-            const E t = frame::add(wc, c0);
-            frame::sum6(t, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, a0, a1, a2);
-            frame::sum6(t, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], c1, e0, e1, e2);
-        } else {
-            frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
-        }
-        // the fixed-shift mean when every computing lane's sums lie in the
-        // top binades of the frame (nearly always), else the general one;
-        // each branch stores its own results
-        const bool top = top_ok && frame::sum_in_top(a2) && (!TWO || frame::sum_in_top(e2));
-        if (__all_sync(0xffffffffu, top || !k1)) {
-            const double o0 = frame::mean7_top(a0, a1, a2, scale_hi);
-            if (k1) out[0] = (T)o0;
+        if constexpr (OP == OP_RES32) {
+            // L = xm + xp + ym + yp + zm + zp - 6c, exact in the 64-bit frame
+            const int64_t L0 = b0[own - 1] + b0[own + 1] + b0[own - kSW] + b0[own + kSW] + wzm + c0 - 6 * wc;
+            if (k1) frame::add_square(L0, q0, q1, q2);
             if (TWO) {
-                const double o1 = frame::mean7_top(e0, e1, e2, scale_hi);
-                if (k1) out[plane] = (T)o1;
+                const int64_t L1 = b1[own - 1] + b1[own + 1] + b1[own - kSW] + b1[own + kSW] + wc + c1 - 6 * c0;
+                if (k1) frame::add_square(L1, q0, q1, q2);
             }
-        } else {
-            double o0, o1;
-            const bool ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
-            if (k1 && ok0) out[0] = (T)o0;
+        } else if constexpr (OP == OP_RES) {
+            double o;
+            const bool ok0 = frame::laplacian(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, eref, o);
+            if (k1 && ok0) acc = fma(o, o, acc);
             if (k1 && !ok0) {
                 const int i = atomicAdd(&slow->n, 1);
                 if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
             }
             if (TWO) {
-                const bool ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
-                if (k1 && ok1) out[plane] = (T)o1;
+                const bool ok1 = frame::laplacian(c0, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], wc, c1, eref, o);
+                if (k1 && ok1) acc = fma(o, o, acc);
                 if (k1 && !ok1) {
                     const int i = atomicAdd(&slow->n, 1);
                     if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+                }
+            }
+        } else {
+            uint32_t a0, a1, a2, e0 = 0u, e1 = 0u, e2 = 0u;
+            if (TWO) {  // planes k and k+1 share the term wc + c0
+                const E t = frame::add(wc, c0);
+                frame::sum6(t, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, a0, a1, a2);
+                frame::sum6(t, b1[own - 1], b1[own + 1], b1[own - kSW], b1[own + kSW], c1, e0, e1, e2);
+            } else {
+                frame::sum7(wc, b0[own - 1], b0[own + 1], b0[own - kSW], b0[own + kSW], wzm, c0, a0, a1, a2);
+            }
+            // the fixed-shift mean when every computing lane's sums lie in the
+            // top binades of the frame (nearly always), else the general one;
+            // each branch stores its own results
+            const bool top = top_ok && frame::sum_in_top(a2) && (!TWO || frame::sum_in_top(e2));
+            if (__all_sync(0xffffffffu, top || !k1)) {
+                const double o0 = frame::mean7_top(a0, a1, a2, scale_hi);
+                if (k1) out[0] = (T)o0;
+                if (TWO) {
+                    const double o1 = frame::mean7_top(e0, e1, e2, scale_hi);
+                    if (k1) out[plane] = (T)o1;
+                }
+            } else {
+                double o0, o1;
+                const bool ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o0);
+                if (k1 && ok0) out[0] = (T)o0;
+                if (k1 && !ok0) {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
+                }
+                if (TWO) {
+                    const bool ok1 = frame::mean7_of_sum(e0, e1, e2, eref, o1);
+                    if (k1 && ok1) out[plane] = (T)o1;
+                    if (k1 && !ok1) {
+                        const int i = atomicAdd(&slow->n, 1);
+                        if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+                    }
                 }
             }
         }
@@ -766,15 +818,28 @@ __device__ void tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restri
     if (k + 1 < z1) step(std::true_type{}, std::true_type{}, k);
     else if (k < z1) step(std::false_type{}, std::true_type{}, k);
     cp_async_wait<0>();
-    slow_cells<T, OP_EXACT, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y,
-                                          cell_index<T>(d, p ^ 1, x, y, 0), 0.0, slow);
+    if constexpr (OP == OP_RES32) {
+        // L^2 was summed exactly in units of 2^(2 (eref - 186)); a value
+        // outside the frame anywhere in the tile redoes the whole tile with
+        // the exact per-cell routines
+        acc = frame::u192_to_double_scaled(q0, q1, q2, 2 * (eref - 186));
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) slow->n = kSlowMax + 1;
+        }
+        return slow_cells<T, OP_RES, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, 0, acc, slow);
+    } else if constexpr (OP == OP_RES) {
+        return slow_cells<T, OP_RES, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, 0, acc, slow);
+    } else {
+        return slow_cells<T, OP_EXACT, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y,
+                                                     cell_index<T>(d, p ^ 1, x, y, 0), 0.0, slow);
+    }
 }
 
 // Dynamic shared memory of the update kernels for op OP.
 template <typename T, int OP, int TW>
 __host__ __device__ constexpr int kernel_bytes()
 {
-    if constexpr (OP == OP_EXACT) return pair_engine_bytes<T, TW, kRing<T>>();
+    if constexpr (OP == OP_EXACT) return pair_engine_bytes<T, OP, TW, kRing<T>>();
     else return engine_bytes<T, OP, TW, kRing<T>>();
 }
 
@@ -1208,7 +1273,7 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_stencil_block(T* pool, 
 {
     __shared__ SlowList slow;
     if constexpr (OP == OP_EXACT)
-        tile_engine_pair<T, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
+        tile_engine_pair<T, OP_EXACT, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
                                                         blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
                                                         &slow);
     else
@@ -1226,7 +1291,7 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, con
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
         if constexpr (OP == OP_EXACT)
-            tile_engine_pair<T, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+            tile_engine_pair<T, OP_EXACT, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
                                                            jac_dyn_sm, &slow);
         else
             tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
@@ -1320,7 +1385,7 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
                 // barrier above order them after the neighbours' releases
                 f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             } else if constexpr (OP == OP_EXACT) {
-                tile_engine_pair<T, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
+                tile_engine_pair<T, OP_EXACT, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
                                                               u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
             } else {
                 tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
@@ -1349,14 +1414,14 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_residual(const T* pool,
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
         constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
-        acc = tile_engine<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p, u.x0,
-                                                             u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+        acc = tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
+                                                                  u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
         if constexpr (sizeof(T) == 4) {
             // a binary32 unit is two engine tiles tall
             __syncthreads();
-            acc += tile_engine<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                  u.x0, u.y0 + kNT<float> / TW, u.z0, u.z1, jac_dyn_sm,
-                                                                  &slow);
+            acc += tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
+                                                                       p, u.x0, u.y0 + kNT<float> / TW, u.z0, u.z1,
+                                                                       jac_dyn_sm, &slow);
         }
     });
     const int tid = threadIdx.x;
@@ -1629,9 +1694,9 @@ static int residual_bytes(int tw_mask)
     if (tw_mask == 0) tw_mask = 7;
     constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
     int n = 0;
-    if (tw_mask & 1) n = std::max(n, engine_bytes<T, OPR, 16, kRingRes>());
-    if (tw_mask & 2) n = std::max(n, engine_bytes<T, OPR, 32, kRingRes>());
-    if (tw_mask & 4) n = std::max(n, engine_bytes<T, OPR, 64, kRingRes>());
+    if (tw_mask & 1) n = std::max(n, pair_engine_bytes<T, OPR, 16, kRingRes>());
+    if (tw_mask & 2) n = std::max(n, pair_engine_bytes<T, OPR, 32, kRingRes>());
+    if (tw_mask & 4) n = std::max(n, pair_engine_bytes<T, OPR, 64, kRingRes>());
     return n;
 }
 
