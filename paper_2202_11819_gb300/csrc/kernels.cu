@@ -110,19 +110,6 @@ constexpr int OP_EXACT = 1;  // binary64 correctly rounded mean, grid-frame inte
 constexpr int OP_RES = 2;    // residual: sum of L^2 with the exact Laplacian term
 constexpr int OP_RES32 = 3;  // the same for binary32 grids, L in a 64-bit frame and L^2 summed exactly
 
-template <typename T, int OP>
-struct Elem {
-    using type = frame::W96;
-};
-template <typename T>
-struct Elem<T, OP_SEQ> {
-    using type = T;
-};
-template <typename T>
-struct Elem<T, OP_RES32> {
-    using type = int64_t;
-};
-
 template <typename T>
 __device__ __forceinline__ const T* bc_ptr(const BlockDesc& d, int f);
 template <>
@@ -141,17 +128,6 @@ __device__ __forceinline__ T ldv(const T* p)
 {
     if constexpr (CG) return __ldcg(p);
     else return __ldg(p);
-}
-
-template <typename T, int OP>
-__device__ __forceinline__ typename Elem<T, OP>::type conv(T v, int eref)
-{
-    if constexpr (OP == OP_SEQ) return v;
-    else if constexpr (OP == OP_RES32) {
-        // out-of-window values are flagged by the engine (conv_ok)
-        bool ok;
-        return frame::of32((float)v, eref, ok);
-    } else return frame::of((double)v, eref);
 }
 
 // Where the value of (x, y) lives along z, for -1 <= x <= bx, -1 <= y <= by
@@ -229,10 +205,13 @@ struct SlowList {
     uint32_t cell[kSlowMax];  // (k << 9) | tid
 };
 
+// The single-plane engine's double-buffered exchange plane (the sequential
+// rule: the values themselves).
 template <typename T, int OP, int TW>
 __host__ __device__ constexpr int smem_bytes()
 {
-    return 2 * (kNT<T> / TW + 2) * (TW + 2) * (int)sizeof(typename Elem<T, OP>::type);
+    static_assert(OP == OP_SEQ, "the single-plane engine runs the sequential rule");
+    return 2 * (kNT<T> / TW + 2) * (TW + 2) * (int)sizeof(T);
 }
 
 // Extra ring slots of a tile (the halo ring around the TW x 512/TW interior).
@@ -398,52 +377,34 @@ __device__ __forceinline__ double slow_cells(T* __restrict__ pool, const BlockDe
     return acc;
 }
 
-// The z-marching engine over one tile (x0 .. x0+TW-1, y0 .. y0+512/TW-1,
-// planes z0 .. z1-1) of block b, reading buffer p.
-//   OP_SEQ / OP_EXACT: writes the interior of buffer p^1;
-//   OP_RES:           returns this thread's sum of L^2 (thread 0 also adds the
-//                     cells recomputed exactly, in (k, tid) order).
+// The single-plane z-marching engine over one tile (x0 .. x0+TW-1, y0 ..
+// y0+512/TW-1, planes z0 .. z1-1) of block b, reading buffer p and writing
+// the interior of buffer p^1 by the sequential rule (the exact mean and the
+// residuals run on the two-plane engine below).
 // Every shared slot of the tile plane (the interior plus its halo ring) is a
 // stream along z (pointer + plane stride, or a constant): own columns, halo
 // cells that fall inside the tile where it overhangs the block edge, and one
 // extra ring slot for each of the first 2 (TW + 512/TW) threads. Each stream
 // is copied RD - 1 planes ahead into a per-thread ring in shared memory
 // (cp.async: the data in flight holds no registers and the loop needs no
-// register rotation); each value is converted once (to the grid frame for
-// the exact ops), stored in a double-buffered shared plane (one barrier per
-// plane), and the z neighbours are carried in registers.
+// register rotation); each value is stored in a double-buffered shared plane
+// (one barrier per plane), and the z neighbours are carried in registers.
 template <typename T, int OP, bool PULL, bool CG, int RD, int TW>
-__device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
-                              const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
-                              unsigned char* smraw, SlowList* slow)
+__device__ void tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p, int x0, int y0,
+                            int z0, int z1, unsigned char* smraw)
 {
-    using E = typename Elem<T, OP>::type;
-    constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kTW = TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
+    static_assert(OP == OP_SEQ, "the single-plane engine runs the sequential rule");
+    using E = T;
+    constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
     static_assert(RD >= 2, "ring depth");
     E* sm = (E*)smraw;
     T* rc = (T*)(smraw + smem_bytes<T, OP, TW>());  // [RD][kN]
     T* re = rc + RD * kN;                            // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    // OP_RES32: eref is the binary32 exponent field + 1 (frame_e holds the
-    // binary64 field of the largest value)
-    const int eref = (OP == OP_SEQ) ? 0 : (OP == OP_RES32 ? frame_e[d.inst] + 1 - 896 : frame_e[d.inst] + 1);
     const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
     const int x = x0 + tx, y = y0 + ty;
     const int64_t plane = d.plane;
-    if (OP != OP_SEQ && tid == 0) slow->n = 0;
-    bool bad = false;                         // OP_RES32: a value outside the 64-bit frame
-    uint64_t q0 = 0u, q1 = 0u, q2 = 0u;       // OP_RES32: this thread's sum of L^2 in frame units
-    auto cv = [&](T v) {
-        if constexpr (OP == OP_RES32) {
-            bool ok;
-            const int64_t w = frame::of32((float)v, eref, ok);
-            bad |= !ok;
-            return w;
-        } else {
-            return conv<T, OP>(v, eref);
-        }
-    };
 
     // own column: 0 unused, 1 interior cell, 2 halo cell inside the tile.
     // The value consumed at iteration k is at sp + (k - z0) * ss: kind 1 the
@@ -462,8 +423,8 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         zhi = z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane;
         oidx = cell_index<T>(d, p ^ 1, x, y, 0);
         const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
-        wzm = cv(ldv<T, CG>(zlo));
-        wc = cv(ldv<T, CG>(col + z0 * plane));
+        wzm = ldv<T, CG>(zlo);
+        wc = ldv<T, CG>(col + z0 * plane);
     } else if ((x == bx && y < by) || (y == by && x < bx)) {
         kind = 2;
         const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, x, y);
@@ -490,9 +451,7 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
     };
 #pragma unroll
     for (int i = 0; i < RD - 1; ++i) issue(i);
-    if (OP != OP_SEQ) __syncthreads();  // slow->n = 0 visible before any append
 
-    double acc = 0.0;
     int s = 0;  // ring slot of iteration k; iteration k + RD - 1 goes to s - 1
 #pragma unroll 2
     for (int k = z0; k < z1; ++k) {
@@ -501,52 +460,19 @@ __device__ double tile_engine(T* __restrict__ pool, const BlockDesc* __restrict_
         E* buf = sm + (k & 1) * ((kTY + 2) * kSW);
         E* slot = buf + (ty + 1) * kSW + tx + 1;
         if (kind == 1) *slot = wc;
-        else if (kind == 2) *slot = cv(myc[s * kN]);
-        if (er >= 0) buf[er * kSW + ec] = cv(mye[s * kEr]);
+        else if (kind == 2) *slot = myc[s * kN];
+        if (er >= 0) buf[er * kSW + ec] = mye[s * kEr];
         __syncthreads();
         if (kind == 1) {
-            const E wzp = cv(myc[s * kN]);
+            const E wzp = myc[s * kN];
             const int sc = (ty + 1) * kSW + tx + 1;
-            if constexpr (OP == OP_RES32) {
-                const int64_t L = buf[sc - 1] + buf[sc + 1] + buf[sc - kSW] + buf[sc + kSW] + wzm + wzp - 6 * wc;
-                frame::add_square(L, q0, q1, q2);
-            } else if constexpr (OP == OP_SEQ) {
-                pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
-            } else {
-                double o;
-                bool ok;
-                if constexpr (OP == OP_EXACT) {
-                    ok = frame::mean7(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
-                    if (ok) pool[oidx + k * plane] = (T)o;
-                } else {
-                    ok = frame::laplacian(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp, eref, o);
-                    if (ok) acc = fma(o, o, acc);
-                }
-                if (!ok) {
-                    const int i = atomicAdd(&slow->n, 1);
-                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
-                }
-            }
+            pool[oidx + k * plane] = mean7<T, 0>(wc, buf[sc - 1], buf[sc + 1], buf[sc - kSW], buf[sc + kSW], wzm, wzp);
             wzm = wc;
             wc = wzp;
         }
         s = s == RD - 1 ? 0 : s + 1;
     }
     cp_async_wait<0>();  // only empty groups remain; the ring is free for the next tile
-    if constexpr (OP == OP_RES32) {
-        // L^2 was summed exactly in units of 2^(2 (eref - 186)); a value
-        // outside the frame anywhere in the tile redoes the whole tile with
-        // the exact per-cell routines
-        acc = frame::u192_to_double_scaled(q0, q1, q2, 2 * (eref - 186));
-        if (__syncthreads_or(bad)) {
-            if (tid == 0) slow->n = kSlowMax + 1;
-        }
-        return slow_cells<T, OP_RES, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc,
-                                                   slow);
-    } else {
-        return slow_cells<T, OP, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, kind == 1, x, y, oidx, acc,
-                                               slow);
-    }
 }
 
 // The engine above for the exact mean, two planes per step: each thread
@@ -1277,9 +1203,8 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_stencil_block(T* pool, 
                                                         blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
                                                         &slow);
     else
-        tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                       blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
-                                                       &slow);
+        tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, b, p, blockIdx.x * TW, blockIdx.y * (kNT<T> / TW),
+                                                       0, desc[b].ext[2], jac_dyn_sm);
 }
 
 template <typename T, int OP>
@@ -1294,8 +1219,7 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, con
             tile_engine_pair<T, OP_EXACT, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
                                                            jac_dyn_sm, &slow);
         else
-            tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
-                                                          jac_dyn_sm, &slow);
+            tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
     });
 }
 
@@ -1388,8 +1312,8 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
                 tile_engine_pair<T, OP_EXACT, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
                                                               u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
             } else {
-                tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0,
-                                                             u.z0, u.z1, jac_dyn_sm, &slow);
+                tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1,
+                                                             jac_dyn_sm);
             }
         });
         __syncthreads();
