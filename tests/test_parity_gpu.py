@@ -144,6 +144,26 @@ def test_exact_arith_slow_paths():
     assert np.array_equal(got2, want)
 
 
+@pytest.mark.parametrize("mode", MODES)
+def test_sequential_rule_special_values(mode):
+    """The sequential rule on values its integer first addition and integer
+    division refuse (negative, subnormal, zero, sums whose quotient leaves the
+    normal range): those lanes take the binary64 pipe, and every cell stays
+    bit-exact against the oracle."""
+    dims, block = (18, 10, 9), (6, 5, 3)
+    rng = np.random.default_rng(2)
+    u0 = rng.random(dims[::-1]) * 2.0 ** rng.integers(-80, 40, size=dims[::-1])
+    u0 *= rng.choice([-1.0, 1.0], size=u0.shape)
+    u0.reshape(-1)[::17] = 0.0
+    u0.reshape(-1)[5::23] = 2.0 ** -1070
+    u0.reshape(-1)[7::29] = -(2.0 ** -1050)
+    u0.reshape(-1)[3::31] = 2.0 ** -1020
+    bc = (3.0, -2.0, 1e-200, 0.0, -5e10, 7.0)
+    want = oracle.jacobi(u0, bc, 5, oracle.RULE_SEQ)
+    got, _ = run(u0, dims, block, 5, mode, "seq", bc=bc)
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_residual_parity(dtype):
     dims, block = (30, 22, 18), (10, 11, 6)
@@ -156,6 +176,34 @@ def test_residual_parity(dtype):
             J.iterate(n)
             u = J.read(np.float32 if dtype == "f32" else np.float64)
             want = oracle.residual(u, BC_MIXED)
+            got = J.residual()
+            assert abs(got - want) <= 1e-12 * want
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_residual_slow_paths(dtype):
+    """Residual parity where the frames do not hold every value: negative
+    values, zeros, subnormals and exponent spreads wider than the binary64
+    frame (31 binades: cells go to the exact per-cell list) and the binary32
+    one (36 binades: the whole tile is redone exactly)."""
+    dims, block = (34, 19, 13), (12, 7, 5)
+    rng = np.random.default_rng(21)
+    if dtype == "f64":
+        u0 = rng.random(dims[::-1]) * 2.0 ** rng.integers(-80, 40, size=dims[::-1])
+        u0.reshape(-1)[5::23] = 2.0 ** -1070
+        bc = (3.0, -2.0, 1e-200, 0.0, -5e10, 7.0)
+    else:
+        u0 = (rng.random(dims[::-1]) * 2.0 ** rng.integers(-60, 30, size=dims[::-1])).astype(np.float32)
+        u0.reshape(-1)[5::23] = np.float32(2.0 ** -140)
+        bc = (3.0, -2.0, 1e-30, 0.0, -5e10, 7.0)
+    u0 *= rng.choice([-1.0, 1.0], size=u0.shape).astype(u0.dtype)
+    u0.reshape(-1)[::17] = 0.0
+    with Jacobi3D(dims, block, dtype=dtype, bc=bc) as J:
+        J.write(u0)
+        for n in (0, 2):
+            J.iterate(n)
+            u = J.read(np.float32 if dtype == "f32" else np.float64)
+            want = oracle.residual(u, bc)
             got = J.residual()
             assert abs(got - want) <= 1e-12 * want
 
