@@ -413,7 +413,7 @@ def run_ours(a, rank, world, local, pg):
         return
     cpu = None
     if not a.no_cpu:
-        budget = 1.0e8 if (a.arith == "exact" and a.dtype == "f64") else 2.0e9
+        budget = 4.1e8 if (a.arith == "exact" and a.dtype == "f64") else 2.0e9  # about 10-15 s of oracle work
         rate, it, dt, cores = oracle_rate(a, budget)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"full {g[0]}x{g[1]}x{g[2]} grid, {it} iteration(s), {dt:.1f} s"}
