@@ -475,16 +475,17 @@ __device__ void tile_engine(T* __restrict__ pool, const BlockDesc* __restrict__ 
     cp_async_wait<0>();  // only empty groups remain; the ring is free for the next tile
 }
 
-// The engine above for the exact mean, two planes per step: each thread
+// The two-plane engine: the engine above, two planes per step. Each thread
 // computes cells (k, k+1) of its column between one pair of barriers, so the
 // per-plane bookkeeping (copies, waits, barrier, addressing) is shared by two
 // cells and the two cells' integer chains interleave. The exchange buffer
-// holds two planes, double-buffered; the ring, its slots and the slow list
-// are those of the single-plane engine (RD even). A range with an odd number
-// of planes ends with a single-plane step.
-// Ops the pair engine runs: the exact mean and the residuals (the
-// sequential rule keeps the single-plane engine: it is bound by the binary64
-// pipe either way). Its exchange element is the op's frame value.
+// holds two planes, double-buffered, of frame values (each value converted
+// once); the rings work as in the single-plane engine (RD even), with the
+// halo ring spread over two threads per slot (one plane each) where the CTA
+// has the threads. A range with an odd number of planes ends with a
+// single-plane step; cells the frame cannot hold go to the slow list.
+// Ops it runs: the exact mean and the residuals (the sequential rule keeps
+// the single-plane engine: it is bound by the binary64 pipe either way).
 template <int OP>
 constexpr bool kPairOp = OP == OP_EXACT || OP == OP_RES || OP == OP_RES32;
 
