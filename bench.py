@@ -365,26 +365,35 @@ def run_ours(a, rank, world, local, pg):
         e2e = None
         if not a.no_e2e:
             e2e_steps = max(1, min(a.steps, 3))
+            parts = np.zeros(3)  # host seconds: write (copy in, check, scatter), iterate + residual, read
             barrier(pg)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                if a.dtype == "f32":
-                    _lib.jac_write_f32(J.h, host_in.numpy())
-                else:
-                    _lib.jac_write(J.h, host_in.numpy())
-                J.iterate(a.iters)
-                r = J.residual()
-                if a.dtype == "f32":
-                    _lib.jac_read_f32(J.h, host_out.numpy())
-                else:
-                    _lib.jac_read(J.h, host_out.numpy())
-            torch.cuda.synchronize()
-            e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
+            with ClockSampler(local) as e2e_clk:
+                t0 = time.perf_counter()
+                for _ in range(e2e_steps):
+                    t = time.perf_counter()
+                    if a.dtype == "f32":
+                        _lib.jac_write_f32(J.h, host_in.numpy())
+                    else:
+                        _lib.jac_write(J.h, host_in.numpy())
+                    t1 = time.perf_counter()
+                    J.iterate(a.iters)
+                    r = J.residual()
+                    t2 = time.perf_counter()
+                    if a.dtype == "f32":
+                        _lib.jac_read_f32(J.h, host_out.numpy())
+                    else:
+                        _lib.jac_read(J.h, host_out.numpy())
+                    parts += (t1 - t, t2 - t1, time.perf_counter() - t2)
+                torch.cuda.synchronize()
+                e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
             nbytes = ncell * np.dtype(np_dt).itemsize
             e2e = {"value": world * ncell * a.iters * e2e_steps / e2e_wall, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
-                   "residual": r}
+                   "residual": r,
+                   "ms_per_step": {k: round(1e3 * v / e2e_steps, 2)
+                                   for k, v in zip(("write", "iterate_and_residual", "read"), parts)},
+                   "clocks": e2e_clk.summary()}
 
         # ---- other issue forms on the same grid (fewer iterations)
         forms = None
