@@ -1201,8 +1201,8 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_stencil_block(T* pool, 
     __shared__ SlowList slow;
     if constexpr (OP == OP_EXACT)
         tile_engine_pair<T, OP_EXACT, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                        blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2], jac_dyn_sm,
-                                                        &slow);
+                                                                  blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2],
+                                                                  jac_dyn_sm, &slow);
     else
         tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, b, p, blockIdx.x * TW, blockIdx.y * (kNT<T> / TW),
                                                        0, desc[b].ext[2], jac_dyn_sm);
@@ -1217,8 +1217,8 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, con
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
         if constexpr (OP == OP_EXACT)
-            tile_engine_pair<T, OP_EXACT, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
-                                                           jac_dyn_sm, &slow);
+            tile_engine_pair<T, OP_EXACT, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0,
+                                                                     u.z0, u.z1, jac_dyn_sm, &slow);
         else
             tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
     });
@@ -1310,8 +1310,8 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
                 // barrier above order them after the neighbours' releases
                 f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             } else if constexpr (OP == OP_EXACT) {
-                tile_engine_pair<T, OP_EXACT, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0,
-                                                              u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+                tile_engine_pair<T, OP_EXACT, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1,
+                                                                        u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
             } else {
                 tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1,
                                                              jac_dyn_sm);
