@@ -204,6 +204,8 @@ struct jac_ctx {
     void* halo = nullptr;                 // send region then recv region
     std::vector<int64_t> send_off, recv_off;  // per block*6 + face, elements
     std::vector<int32_t> fsize;           // per block*6 + face
+    std::vector<int32_t> maxface;         // per block: its largest face with a neighbour
+    void* dface = nullptr;                // device: send_off then recv_off (the six-face kernels' tables)
     std::vector<cudaStream_t> comm, comp;
     // Two event sets: one for eager issue and one used only while capturing a
     // graph (a wait may not name an event whose last record was captured).
@@ -580,8 +582,20 @@ int ensure_halo(jac_ctx* h)
         }
     }
     for (int64_t i = 0; i < nblocks * 6; ++i) h->recv_off[i] = h->send_off[i] + total;
+    h->maxface.assign(nblocks, 0);
+    for (int64_t b = 0; b < nblocks; ++b)
+        for (int f = 0; f < 6; ++f)
+            if (h->hdesc[b].nbr[f] >= 0) h->maxface[b] = std::max(h->maxface[b], h->fsize[b * 6 + f]);
     int rc;
     if ((rc = dev_alloc(h, (size_t)(2 * total) * h->esize, &h->halo))) return rc;
+    if ((rc = dev_alloc(h, (size_t)(2 * nblocks * 6) * sizeof(int64_t), &h->dface))) return rc;
+    CU(cudaMemcpyAsync(h->dface, h->send_off.data(), (size_t)(nblocks * 6) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                       h->stream),
+       "face table");
+    CU(cudaMemcpyAsync((int64_t*)h->dface + nblocks * 6, h->recv_off.data(), (size_t)(nblocks * 6) * sizeof(int64_t),
+                       cudaMemcpyHostToDevice, h->stream),
+       "face table");
+    CU(cudaStreamSynchronize(h->stream), "face table");
     int lo = 0, hi = 0;
     CU(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priority range");
     h->comm.resize(nblocks);
@@ -610,9 +624,16 @@ int ensure_halo(jac_ctx* h)
 // neighbour, copy them into the neighbours' receive buffers, then once all
 // six halos of a block have arrived unpack them and update the block.
 // `capture`: the iteration is being recorded into a graph, where the
-// cross-iteration waits are implied by the order of graph launches.
+// cross-iteration waits are implied by the order of graph launches. The
+// graph holds the six-face form of pack and unpack (one kernel per block
+// each, one thread per cell of the block's largest face visiting the six
+// faces: Section III-D1), about half the nodes of the per-face form, which
+// the eager flow keeps.
 int issue_unfused(jac_ctx* h, int p, bool capture)
 {
+    const bool six = capture;
+    const int64_t* dsend = (const int64_t*)h->dface;
+    const int64_t* drecv = dsend + (int64_t)h->hdesc.size() * 6;
     const LaunchArgs a = h->args();
     const int f32 = h->dtype == JAC_F32;
     const int64_t nblocks = (int64_t)h->hdesc.size();
@@ -623,11 +644,19 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
         const BlockDesc& d = h->hdesc[b];
         cudaStream_t s = h->comm[b];
         if (!capture) CU(cudaStreamWaitEvent(s, E.updated[b], 0), "wait updated");
-        for (int f = 0; f < 6; ++f) {
-            if (d.nbr[f] < 0) continue;
-            CU(launch_pack_face(a, f32, (int)b, f, p, send + h->send_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
-               "pack");
-            h->launches += 1;
+        if (six) {
+            if (h->maxface[b] > 0) {
+                CU(launch_pack6(a, f32, (int)b, p, send, dsend + b * 6, h->maxface[b], s), "pack6");
+                h->launches += 1;
+            }
+        } else {
+            for (int f = 0; f < 6; ++f) {
+                if (d.nbr[f] < 0) continue;
+                CU(launch_pack_face(a, f32, (int)b, f, p, send + h->send_off[b * 6 + f] * es, h->fsize[b * 6 + f],
+                                    s),
+                   "pack");
+                h->launches += 1;
+            }
         }
         for (int f = 0; f < 6; ++f) {
             const int n = d.nbr[f];
@@ -645,11 +674,19 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
         cudaStream_t s = h->comm[b];
         for (int f = 0; f < 6; ++f)
             if (d.nbr[f] >= 0) CU(cudaStreamWaitEvent(s, E.sent[d.nbr[f]], 0), "wait sent");
-        for (int f = 0; f < 6; ++f) {
-            if (d.nbr[f] < 0) continue;
-            CU(launch_unpack_face(a, f32, (int)b, f, p, send + h->recv_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
-               "unpack");
-            h->launches += 1;
+        if (six) {
+            if (h->maxface[b] > 0) {
+                CU(launch_unpack6(a, f32, (int)b, p, send, drecv + b * 6, h->maxface[b], s), "unpack6");
+                h->launches += 1;
+            }
+        } else {
+            for (int f = 0; f < 6; ++f) {
+                if (d.nbr[f] < 0) continue;
+                CU(launch_unpack_face(a, f32, (int)b, f, p, send + h->recv_off[b * 6 + f] * es, h->fsize[b * 6 + f],
+                                      s),
+                   "unpack");
+                h->launches += 1;
+            }
         }
         CU(cudaEventRecord(E.unpacked[b], s), "record unpacked");
         CU(cudaStreamWaitEvent(h->comp[b], E.unpacked[b], 0), "wait unpacked (update)");
@@ -704,14 +741,12 @@ int ensure_graph(jac_ctx* h, int p)
     return JAC_OK;
 }
 
-// kernels per graph launch of the unfused flow
+// kernels per graph launch of the unfused flow (its six-face form: pack6
+// and unpack6 for a block with a neighbour, then the update)
 int64_t unfused_kernels(const jac_ctx* h)
 {
     int64_t n = 0;
-    for (const BlockDesc& d : h->hdesc) {
-        n += 1;
-        for (int f = 0; f < 6; ++f) n += d.nbr[f] >= 0 ? 2 : 0;
-    }
+    for (size_t b = 0; b < h->hdesc.size(); ++b) n += 1 + (h->maxface[b] > 0 ? 2 : 0);
     return n;
 }
 
