@@ -382,6 +382,51 @@ int build_units(jac_ctx* h)
         }
         I.u1 = (int32_t)h->hunits.size();
     }
+    // The last wave: when the units leave it at most half full, split its
+    // units in z (each in place, so every instance's units stay together),
+    // so the wave holds twice as many units of half the work.
+    if (!h->hunits.empty() && !h->inst.empty()) {
+        const int f32 = h->dtype == JAC_F32;
+        int per_sm = 0, sms = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
+                                                         persistent_block_threads(f32),
+                                                         persistent_smem_bytes(f32, h->arith, h->tw_mask)),
+           "occupancy");
+        CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+        const int64_t slots = (int64_t)per_sm * sms, n = (int64_t)h->hunits.size();
+        const int64_t r = slots > 0 ? n % slots : 0;
+        if (r > 0 && 2 * r <= slots) {
+            std::vector<TileUnit> tail(h->hunits.end() - r, h->hunits.end());
+            h->hunits.resize(n - r);
+            for (const TileUnit& u : tail) {
+                if (u.z1 - u.z0 < 2) {
+                    h->hunits.push_back(u);
+                    continue;
+                }
+                TileUnit lo = u, hi = u;
+                lo.z1 = hi.z0 = (int16_t)((u.z0 + u.z1) / 2);
+                h->hunits.push_back(lo);
+                h->hunits.push_back(hi);
+            }
+            // instance unit ranges and the per-block unit counts follow the new list
+            seg.clear();
+            for (Instance& I : h->inst) {
+                if (!I.active) continue;
+                I.u0 = -1;
+            }
+            for (int32_t b = 0; b < (int32_t)nblocks; ++b) h->hdesc[b].ntiles = 0;
+            for (size_t i = 0; i < h->hunits.size(); ++i) {
+                const int32_t b = h->hunits[i].block;
+                h->hdesc[b].ntiles += 1;
+                Instance& I = h->inst[h->hdesc[b].inst];
+                if (I.u0 < 0) {
+                    I.u0 = (int32_t)i;
+                    seg.push_back((int32_t)i);
+                }
+                I.u1 = (int32_t)i + 1;
+            }
+        }
+    }
     seg.push_back((int32_t)h->hunits.size());
     int rc;
     const size_t need = std::max<size_t>(1, h->hunits.size());
