@@ -292,13 +292,18 @@ static void sweep_f64(const double *src, double *dst, int64_t nx, int64_t ny, in
                 double out;
                 if (rule == ORC_RULE_SEQ) {
                     double s = c;
-                    s = s + xm;
-                    s = s + xp;
+                    if (ORC_MUTANT == 7) {
+                        s = s + (xm + xp);
+                    } else {
+                        s = s + xm;
+                        s = s + xp;
+                    }
                     s = s + ym;
                     s = s + yp;
                     s = s + zm;
                     if (ORC_MUTANT != 1) s = s + zp;
-                    out = s / (ORC_MUTANT == 6 ? 6.0 : 7.0);
+                    if (ORC_MUTANT == 8) out = s * (1.0 / 7.0);
+                    else out = s / (ORC_MUTANT == 6 ? 6.0 : 7.0);
                 } else {
                     double v[7] = {c, xm, xp, ym, yp, zm, zp};
                     out = exact_mean7(v);
@@ -371,7 +376,7 @@ int orc_jacobi_f32(int64_t nx, int64_t ny, int64_t nz, const double *bc, const f
                     s = s + a[gi(i, j + 1, k, nx, ny)];
                     s = s + a[gi(i, j, k - 1, nx, ny)];
                     s = s + a[gi(i, j, k + 1, nx, ny)];
-                    b[gi(i, j, k, nx, ny)] = s / 7.0f;
+                    b[gi(i, j, k, nx, ny)] = (ORC_MUTANT == 9) ? s * (1.0f / 7.0f) : s / 7.0f;
                 }
         float *t = a;
         a = b;

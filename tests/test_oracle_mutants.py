@@ -23,6 +23,9 @@ MUTANTS = {
     4: "correctly rounded mean truncates instead of rounding",
     5: "residual adds 6c instead of subtracting it",
     6: "sequential mean divides by 6",
+    7: "sequential sum adds xm + xp first (reordered)",
+    8: "sequential mean multiplies by fl(1/7) instead of dividing by 7",
+    9: "binary32 mean multiplies by fl(1/7) instead of dividing by 7",
 }
 
 CHECKS = [
@@ -34,6 +37,8 @@ CHECKS = [
     lambda: pins.test_limit_is_dense_dirichlet_solution(oracle.RULE_EXACT, synth.DIRICHLET_X0),
     lambda: pins.test_residual_of_sine_mode_closed_form((6, 5, 7), (1, 2, 3)),
     lambda: pins.test_exact_mean7_adversarial(),
+    lambda: pins.test_seq_rule_equals_per_operation_rounding((3, 4, 5)),
+    lambda: pins.test_f32_equals_per_operation_rounding((3, 4, 5)),
 ]
 
 

@@ -6,7 +6,11 @@ transposed axis, a wrong rounding) fails at least one of them:
 
 - constant fields are fixed points (exact for the correctly rounded mean);
 - separable sine modes decay by the closed-form factor per iteration;
-- exact-rational brute force on tiny grids (Python ``fractions``);
+- exact-rational brute force on tiny grids (Python ``fractions``): the
+  correctly rounded mean against the rational mean rounded once, and the
+  left-to-right rule (binary64 and binary32) against an emulation that rounds
+  the exact result of every addition and of the division, as IEEE 754
+  defines each operation;
 - the iteration's limit equals a dense linear solve of the discrete
   Dirichlet problem built here from the problem statement;
 - maximum principle, monotone residual decay, the asymptotic rate;
@@ -112,6 +116,97 @@ def test_seq_rule_within_roundoff_of_exact_rational(shape):
         assert float(worst) <= k * per_step
         if k == 1:
             assert float(worst) > 0.0  # rounding did happen: the test is not vacuous
+
+
+# ------------------------------------------ P3' per-operation rounding (IEEE 754)
+def _signs_equal(a, b):
+    return np.array_equal(np.signbit(a), np.signbit(b))
+
+
+def test_round_to_format_binary64_is_the_correctly_rounded_conversion():
+    # CPython converts a Fraction to float with one correct rounding
+    # (ties to even); the definition written out must agree everywhere,
+    # including ties, the subnormal range and the top binade
+    rng = np.random.default_rng(23)
+    cases = [Fraction(1) + Fraction(1, 2 ** 53), Fraction(1) + Fraction(3, 2 ** 53),
+             Fraction(1, 2 ** 1075), Fraction(3, 2 ** 1076), Fraction(1, 2 ** 1076),
+             Fraction(2 ** 53 + 1) * 2 ** 970, Fraction(1, 3), Fraction(-2, 7)]
+    for _ in range(3000):
+        num = int(rng.integers(1, 2 ** 62))
+        den = int(rng.integers(1, 2 ** 62))
+        cases.append(Fraction(num, den) * Fraction(2) ** int(rng.integers(-1130, 960)))
+    for x in cases:
+        assert er.round_to_format(x, er.BINARY64) == Fraction(float(x)), x
+
+
+def test_round_to_format_binary32_is_ieee_single():
+    # numpy's binary32 addition and division are IEEE single operations
+    rng = np.random.default_rng(24)
+    for _ in range(20000):
+        a = np.float32(rng.standard_normal() * 2.0 ** int(rng.integers(-150, 60)))
+        b = np.float32(rng.standard_normal() * 2.0 ** int(rng.integers(-150, 60)))
+        got = er.add_rn(float(a), float(b), er.BINARY32)
+        want = a + b
+        assert np.float32(got) == want and math.copysign(1.0, got) == math.copysign(1.0, float(want))
+        q = er.div_rn(float(a), 7.0, er.BINARY32)
+        assert np.float32(q) == a / np.float32(7.0)
+        assert math.copysign(1.0, q) == math.copysign(1.0, float(a / np.float32(7.0)))
+    # a tie, and a quotient that underflows to a signed zero
+    assert er.add_rn(1.0, 2.0 ** -24, er.BINARY32) == 1.0
+    assert er.add_rn(1.0 + 2.0 ** -23, 2.0 ** -24, er.BINARY32) == 1.0 + 2.0 ** -22
+    assert math.copysign(1.0, er.div_rn(-(2.0 ** -149), 7.0, er.BINARY32)) < 0
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 4, 5)])
+def test_seq_rule_equals_per_operation_rounding(shape):
+    nx, ny, nz = shape
+    u0 = rand_grid(3, nx, ny, nz)
+    for k in range(1, 7):
+        want = np.array(er.iterate_sequential(u0, BC_MIXED, k, er.BINARY64))
+        got = oracle.jacobi(u0, BC_MIXED, k, oracle.RULE_SEQ)
+        assert np.array_equal(got, want) and _signs_equal(got, want), f"iteration {k}"
+
+
+def test_seq_rule_equals_per_operation_rounding_mixed_signs_and_tiny_values():
+    # negative values, exact cancellations, subnormal sums and quotients that
+    # underflow to a signed zero
+    nx, ny, nz = 3, 4, 5
+    rng = np.random.default_rng(25)
+    u0 = rng.standard_normal((nz, ny, nx)) * 2.0 ** rng.integers(-40, 20, size=(nz, ny, nx))
+    flat = u0.reshape(-1)
+    flat[::7] = 2.0 ** -1074 * rng.integers(-5, 6, size=flat[::7].shape)
+    flat[3::11] = -0.0
+    flat[5::13] = -flat[4::13][: flat[5::13].size]
+    bc = (-0.75, 3.0, -(2.0 ** -1073), 0.0, -0.0, 1e-300)
+    for k in range(1, 5):
+        want = np.array(er.iterate_sequential(u0, bc, k, er.BINARY64))
+        got = oracle.jacobi(u0, bc, k, oracle.RULE_SEQ)
+        assert np.array_equal(got, want) and _signs_equal(got, want), f"iteration {k}"
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 4, 5)])
+def test_f32_equals_per_operation_rounding(shape):
+    nx, ny, nz = shape
+    u0 = rand_grid(3, nx, ny, nz).astype(np.float32)
+    bc = [float(np.float32(b)) for b in BC_MIXED]
+    for k in range(1, 7):
+        want = np.array(er.iterate_sequential(u0, bc, k, er.BINARY32), dtype=np.float32)
+        got = oracle.jacobi_f32(u0, bc, k)
+        assert np.array_equal(got, want) and _signs_equal(got, want), f"iteration {k}"
+
+
+def test_f32_equals_per_operation_rounding_mixed_signs_and_tiny_values():
+    nx, ny, nz = 4, 3, 4
+    rng = np.random.default_rng(26)
+    u0 = (rng.standard_normal((nz, ny, nx)) * 2.0 ** rng.integers(-140, 30, size=(nz, ny, nx))).astype(np.float32)
+    flat = u0.reshape(-1)
+    flat[::5] = np.float32(2.0 ** -149) * rng.integers(-4, 5, size=flat[::5].shape).astype(np.float32)
+    flat[2::9] = np.float32(-0.0)
+    bc = [float(np.float32(b)) for b in (0.5, -2.0, 2.0 ** -140, -0.0, 1e30, -1e-30)]
+    for k in range(1, 5):
+        want = np.array(er.iterate_sequential(u0, bc, k, er.BINARY32), dtype=np.float32)
+        got = oracle.jacobi_f32(u0, bc, k)
+        assert np.array_equal(got, want) and _signs_equal(got, want), f"iteration {k}"
 
 
 def test_seq_and_exact_rules_differ_somewhere():
