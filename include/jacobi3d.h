@@ -226,11 +226,18 @@ int jac_read_device(jac_ctx *h, void *dev, size_t n_cells, int32_t dtype);
 int jac_iterate(jac_ctx *h, int64_t n_iters);
 
 /* rho(u) = sqrt( sum over interior cells of L^2 ),
- * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly and rounded once
- * to binary64, squared and accumulated in binary64 on the GPU with a
- * deterministic reduction order. The paper runs a fixed iteration count
- * and prints no residual (Section IV-A); this is the convergence measure
- * the library adds. Synchronises the stream; JAC_ETIMEOUT as for jac_read. */
+ * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly. Binary64 grids:
+ * L is rounded once to binary64 and accumulated in binary64 by fused
+ * multiply-adds (acc = fma(L, L, acc)). Binary32 grids: L^2 is summed
+ * exactly per thread and rounded once. The per-thread sums are combined by
+ * a fixed tree per work unit, and the units' partials in unit order. That
+ * order is fixed by the grid, the block dims, the tile width and z depth, and
+ * the unit split the runtime derives from the device's SM count and
+ * occupancy: repeated calls on one device and configuration give the same
+ * bits, other configurations agree within 1e-12 relative. The paper runs a
+ * fixed iteration count and prints no residual (Section IV-A); this is the
+ * convergence measure the library adds. Synchronises the stream;
+ * JAC_ETIMEOUT as for jac_read. */
 int jac_residual(jac_ctx *h, double *out);
 
 /* Enqueue the residual computation and write rho into device memory
@@ -294,7 +301,13 @@ int jac_info(jac_ctx *h, jac_info_t *info);
  *   out      device pointer to one double, receives rho (same definition
  *            as jac_residual).
  *   stream   cudaStream_t (NULL: legacy default stream); stream-ordered,
- *            no host sync.
+ *            no host sync. The kernels run on the stream's device; the
+ *            calling thread's current device is the same after the call as
+ *            before it.
+ * Arithmetic: L exact, rounded once to binary64, accumulated in binary64 by
+ * fused multiply-adds (acc = fma(L, L, acc)) per column over z, then a fixed
+ * tree; binary32 values are widened exactly. The order differs from
+ * jac_residual's, so the two agree within 1e-12 relative, not bit for bit.
  * Scratch: the per-CTA partial sums live in a fixed 65536-double (512 KiB)
  * static device array of the library, held by every GPU that loads the
  * library until the process exits. A grid needing more than 65536 partials

@@ -51,8 +51,9 @@ __device__ __forceinline__ double dense_at(const T* u, int nx, int ny, int nz, c
 }
 
 // One partial per CTA: the sum over its 32 x 8 columns (all k) of L^2, L the
-// exact Laplacian term rounded once; fixed order (per thread over k, then a
-// fixed tree), so the result is deterministic.
+// exact Laplacian term rounded once, accumulated with fused multiply-adds
+// (acc = fma(L, L, acc)); fixed order (per thread over k, then a fixed tree),
+// so the result is deterministic.
 template <typename T>
 __global__ void __launch_bounds__(kDX * kDY)
 k_residual_dense(const T* u, int nx, int ny, int nz, double b0, double b1, double b2, double b3, double b4, double b5,
@@ -101,6 +102,25 @@ __global__ void k_sum_dense_partials(const double* partials, int n, double* out)
     if (threadIdx.x == 0) out[0] = sqrt(red[0]);
 }
 
+// Makes `dev` the calling thread's current device for the guard's lifetime
+// and puts the caller's device back on every return path.
+struct DeviceGuard {
+    int prev = -1;
+    bool switched = false;
+    cudaError_t enter(int dev)
+    {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess || prev == dev) return e;
+        e = cudaSetDevice(dev);
+        switched = e == cudaSuccess;
+        return e;
+    }
+    ~DeviceGuard()
+    {
+        if (switched) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" int jac_residual_dense_noalloc(const void* u, int32_t dtype, int64_t nx, int64_t ny, int64_t nz,
@@ -118,7 +138,10 @@ extern "C" int jac_residual_dense_noalloc(const void* u, int32_t dtype, int64_t 
     cudaError_t e = s ? cudaStreamGetDevice(s, &dev) : cudaGetDevice(&dev);
     if (e != cudaSuccess) return JAC_ECUDA;
     if (dev < 0 || dev >= kMaxDevices) return JAC_EINVAL;
-    if (cudaSetDevice(dev) != cudaSuccess) return JAC_ECUDA;
+    // the symbol lookup and the launches need the stream's device current;
+    // the caller's current device is restored on return
+    DeviceGuard guard;
+    if (guard.enter(dev) != cudaSuccess) return JAC_ECUDA;
     double* partials;
     {
         // first call on a device: look up the device address of the static

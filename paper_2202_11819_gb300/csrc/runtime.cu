@@ -1153,9 +1153,12 @@ int jac_set_arith(jac_ctx* h, int32_t arith)
     if (rc) return rc;
     if (arith != JAC_ARITH_SEQ && arith != JAC_ARITH_EXACT) return fail(JAC_EINVAL, "unknown arith %d", arith);
     if (h->dtype == JAC_F32 && arith != JAC_ARITH_SEQ) return fail(JAC_EINVAL, "F32 contexts use JAC_ARITH_SEQ");
-    if (arith != h->arith) destroy_graphs(h);
+    if (arith == h->arith) return JAC_OK;
+    destroy_graphs(h);
     h->arith = arith;
-    return JAC_OK;
+    // the last wave's unit split follows the persistent kernel's occupancy,
+    // which depends on the rule
+    return h->dirty ? JAC_OK : build_units(h);
 }
 
 int jac_write(jac_ctx* h, const double* host, size_t n_cells)

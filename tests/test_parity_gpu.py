@@ -375,3 +375,61 @@ def test_unfused_forms_cover_tall_blocks(mode, dtype):
         want = oracle.jacobi(u0, BC_MIXED, 4, oracle.RULE_EXACT)
     got, _ = run(u0, dims, block, 4, mode, bc=BC_MIXED, dtype=dtype)
     assert np.array_equal(got, want)
+
+
+_SEQ_1000 = {}
+
+
+def _seq_oracle_1000(dims):
+    # the left-to-right oracle at the benchmark's iteration count, computed
+    # once per grid for the forms that compare with it
+    if dims not in _SEQ_1000:
+        u0 = synth.grid_uniform01(0, *dims)
+        _SEQ_1000[dims] = (u0, oracle.jacobi(u0, synth.DIRICHLET_X0, 1000, oracle.RULE_SEQ))
+    return _SEQ_1000[dims]
+
+
+@pytest.mark.parametrize("mode", ["fused", "persistent"])
+def test_exact_rule_within_1e12_relative_of_sequential_oracle_at_1000_iterations(mode):
+    """The benchmark's rule (correctly rounded mean), blocks (64^3), boundary
+    values and seed, at its 1000 iterations per step, against the
+    left-to-right oracle element by element: |u - u_seq| <= 1e-12 |u_seq|.
+    For non-negative data each rule stays within 7 units of roundoff of the
+    exact mean relative to the cell value, so n iterations differ by at most
+    n * 8 * 2^-53 = 8.9e-13 relative at n = 1000."""
+    dims, block = (192, 128, 128), (64, 64, 64)
+    u0, want = _seq_oracle_1000(dims)
+    got, _ = run(u0, dims, block, 1000, mode, "exact")
+    assert not np.array_equal(got, want)  # the two rules do round differently
+    assert np.all(np.abs(got - want) <= 1e-12 * np.abs(want))
+
+
+def _tiles(info, dims, block):
+    tw = info["tile_w"]
+    th = 256 // tw
+    zd = info["zdepth"] if info["zdepth"] > 0 else block[2]
+    nb = [-(-dims[a] // block[a]) for a in range(3)]
+    per = -(-block[0] // tw) * -(-block[1] // th) * -(-block[2] // zd)
+    return nb[0] * nb[1] * nb[2] * per
+
+
+def test_last_wave_split_in_z_gives_the_oracle_result():
+    """The runtime splits the units of a last wave it would leave at most half
+    full in z. Grids where the split fires and where it does not must both
+    match the oracle bit for bit, in the fused and persistent forms."""
+    block = (64, 64, 64)
+    seen = {True: 0, False: 0}
+    for dims in [(128, 64, 64), (320, 320, 64), (64, 64, 128), (448, 448, 64)]:
+        u0 = grid(37, dims)
+        want = oracle.jacobi(u0, BC_MIXED, 3, oracle.RULE_EXACT)
+        for mode in ("fused", "persistent"):
+            with Jacobi3D(dims, block, bc=BC_MIXED, mode=mode) as J:
+                J.write(u0)
+                J.iterate(3)
+                got = J.read()
+                info = J.info()
+            split = info["n_units"] > _tiles(info, dims, block)
+            assert info["n_units"] >= _tiles(info, dims, block)
+            seen[split] += 1
+            assert np.array_equal(got, want), (dims, mode, split)
+    assert seen[True] > 0 and seen[False] > 0, seen
