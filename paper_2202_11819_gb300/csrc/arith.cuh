@@ -927,4 +927,116 @@ JAC_HD inline double u192_to_double_scaled(uint64_t a0, uint64_t a1, uint64_t a2
 
 }  // namespace frame
 
+// ------------------------------------------------------------------------
+// The 64-bit frame of the correctly rounded mean.
+// A grid whose largest value has exponent field eref - 1 places every value
+// of exponent field e in [eref - 9, eref - 1] at its 53-bit significand
+// shifted left by e - (eref - 9) <= 8: an integer below 2^61 in units of
+// 2^(eref - 1084). Seven such values sum to less than 7 * 2^61 < 2^64, so the
+// sum of a cell and its six neighbours is one exact 64-bit integer, and the
+// exchange plane holds 8 bytes per value instead of the 96-bit frame's 16.
+// Values outside those nine binades (negative, zero or subnormal where the
+// caller does not accept them, tiny) are flagged: the engine then takes the
+// 96-bit frame for that step.
+// ------------------------------------------------------------------------
+namespace nframe {
+
+constexpr int kWindow = 9;  // exponent fields eref - 9 .. eref - 1
+
+// elo_hi = (eref - 9) << 20: the window's lowest exponent field placed
+// where it sits in the high word of a binary64.
+JAC_HD inline uint32_t elo_hi(int eref) { return (uint32_t)(eref - kWindow) << 20; }
+
+// A value as a frame integer; ok is false unless it is a positive normal
+// number inside the window. t = hi - elo_hi is below 9 * 2^20 exactly for
+// those (a sign bit, a smaller exponent or a zero wrap it far above).
+JAC_HD inline uint64_t of(double v, uint32_t elo_hi, bool& ok)
+{
+    const uint64_t b = dbits(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t t = hi - elo_hi;
+    ok = t < ((uint32_t)kWindow << 20);
+    const int sh = (int)(t >> 20);  // 0 .. 8 when ok
+    const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+    return ((uint64_t)frame::fsl(lo, mh, sh) << 32) | frame::fsl(0u, lo, sh);
+}
+
+// As `of`, and +0 is accepted as the frame integer 0 (the implicit bit is
+// dropped when both words are zero, so any shift of it stays 0).
+JAC_HD inline uint64_t of0(double v, uint32_t elo_hi, bool& ok)
+{
+    const uint64_t b = dbits(v);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const bool zero = (hi | lo) == 0u;
+    const uint32_t t = hi - elo_hi;
+    ok = zero || t < ((uint32_t)kWindow << 20);
+    const int sh = (int)(t >> 20);
+    const uint32_t mh = (hi & 0xFFFFFu) | (zero ? 0u : 0x100000u);
+    return ((uint64_t)frame::fsl(lo, mh, sh) << 32) | frame::fsl(0u, lo, sh);
+}
+
+// The frame integer as a 96-bit frame value (units of 2^(eref - 1106)):
+// the same number shifted left by 22.
+JAC_HD inline frame::W96 widen(uint64_t w)
+{
+    frame::W96 r;
+    const uint32_t lo = (uint32_t)w, hi = (uint32_t)(w >> 32);
+    r.w0 = lo << 22;
+    r.w1 = frame::fsl(lo, hi, 22);
+    r.w2 = hi >> 10;
+    r.w3 = 0u;
+    return r;
+}
+
+// scale_hi = (eref - 1081) << 20, the exponent offset mean7 adds.
+JAC_HD inline uint32_t scale_hi(int eref) { return (uint32_t)(eref - 1081) << 20; }
+
+// RN(S / 7) in units of 2^(eref - 1084), for a frame sum S with
+// 2^52 <= S < 7 * 2^61 (the cell's own value is in the window, so S is at
+// least its significand) and eref >= 13 (so the result is normal).
+//   S has a nonzero high word (S >= 2^52), whose leading zeros lz <= 11
+//   normalise it: N = S << lz lies in [2^63, 2^64). M = N >> 3 lies in
+//   [2^60, 2^61), below 2^64 / 5, so the high half of M * ceil(2^64 / 7) is
+//   floor(M / 7) exactly (its excess 5 M / (7 2^64) stays below 1/7, and the
+//   fraction of M / 7 is at most 6/7) and Q = floor(M / 7) has 58 or 59 bits:
+//   at least two below the binary64 rounding position. The sticky
+//   information (a nonzero remainder M - 7Q, or a nonzero bit among the three
+//   N drops) jammed into Q's last bit therefore lets one correctly rounded
+//   integer -> binary64 conversion round the exact quotient S / 7 =
+//   (Q + f) 2^(3 - lz). The scale 2^(3 - lz + eref - 1084) is added to the
+//   exponent field: the result's field is at least eref - 12 >= 1.
+JAC_HD inline double mean7(uint64_t S, uint32_t scale_hi)
+{
+    const uint32_t hi = (uint32_t)(S >> 32), lo = (uint32_t)S;
+    const int lz = clz32(hi);
+    const uint32_t nh = frame::fsl(lo, hi, lz), nl = frame::fsl(0u, lo, lz);
+    const uint32_t mh = nh >> 3, ml = frame::fsr(nl, nh, 3);
+    uint32_t ql, qh;
+#if defined(__CUDA_ARCH__)
+    // high half of M * C over 32-bit limbs, C = ceil(2^64 / 7); the middle
+    // column lo(ml cl) carry + ml ch + mh cl stays below 2^62 (no carry out)
+    asm("{\n\t.reg .u32 t, m0, m1;\n\t"
+        "mul.hi.u32 t, %2, 0x92492493;\n\t"
+        "mad.lo.cc.u32 m0, %2, 0x24924924, t;\n\t"
+        "madc.hi.u32 m1, %2, 0x24924924, 0;\n\t"
+        "mad.lo.cc.u32 m0, %3, 0x92492493, m0;\n\t"
+        "madc.hi.u32 m1, %3, 0x92492493, m1;\n\t"
+        "mad.lo.cc.u32 %0, %3, 0x24924924, m1;\n\t"
+        "madc.hi.u32 %1, %3, 0x24924924, 0;\n\t"
+        "}"
+        : "=r"(ql), "=r"(qh)
+        : "r"(ml), "r"(mh));
+#else
+    const uint64_t q = frame::umulhi64(((uint64_t)mh << 32) | ml, 0x2492492492492493ull);
+    ql = (uint32_t)q;
+    qh = (uint32_t)(q >> 32);
+#endif
+    const uint32_t sticky = (ml - 7u * ql) | (nl & 7u);
+    const uint64_t qj = ((uint64_t)qh << 32) | (ql | (sticky != 0u ? 1u : 0u));
+    const uint64_t d = dbits(frame::u64_to_double_rn(qj));
+    return bitsd(d + ((uint64_t)(scale_hi - ((uint32_t)lz << 20)) << 32));
+}
+
+}  // namespace nframe
+
 }  // namespace jac

@@ -43,6 +43,7 @@ struct BlockDesc {
     float bcf[6];     // the same rounded to binary32 (binary32 grids)
     int32_t pad;
     alignas(8) float bcf2[6][2];  // each binary32 value twice (a constant source for 8-byte pair copies)
+    alignas(16) double bc2[6][2];  // each binary64 value twice (a constant source for 16-byte pair loads)
 };
 
 // One unit of fused / persistent work: a column tile of one block over the

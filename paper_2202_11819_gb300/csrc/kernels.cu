@@ -49,6 +49,10 @@ template <typename T>
 constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
 template <typename T>
 constexpr int kMinCTAs = 1024 / kNT<T>;
+// The exact mean's two-column engine keeps four cells' values live per
+// thread: three 256-thread CTAs per SM (85 registers each) instead of four.
+template <typename T, int OP>
+constexpr int kMinCTAsOp = (sizeof(T) == 8 && OP == 1) ? 3 : kMinCTAs<T>;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
@@ -762,12 +766,808 @@ __device__ double tile_engine_pair(T* __restrict__ pool, const BlockDesc* __rest
     }
 }
 
+// ------------------------------------------------------- 64-bit frame engine
+// The correctly rounded mean with the grid's values held as 64-bit frame
+// integers (nframe): 8 bytes per exchange-plane value, one 64-bit sum per
+// cell, one normalising division by 7. A step whose tile plane holds a value
+// outside the frame's nine binades (a tile-wide vote at the step's barrier)
+// is redone in the 96-bit frame from the raw values, which are still in the
+// prefetch rings (own planes k+1, k+2 and the halo ring) or in global memory
+// (own planes k-1, k); the next step tries the 64-bit frame again.
+
+// One halo-ring slot per thread for tid < 2 (TW + TY), as halo_slot, except
+// that a tile overhanging the block edge takes its right column and bottom
+// row of halo at the edge itself (x = bx, y = by), so every own-column lane
+// of the engine is an interior cell.
+template <bool PULL, int TW>
+__device__ __forceinline__ HaloSlot<double> halo_slot_edge(const double* pool, const BlockDesc* desc,
+                                                           const BlockDesc& d, int p, int x0, int y0, int z0, int tid)
+{
+    using T = double;
+    constexpr int kTW = TW, kTY = kNT<T> / TW;
+    const int bx = d.ext[0], by = d.ext[1];
+    HaloSlot<T> h{-1, 0, pool, 0};
+    if (tid >= ring_extra<T, TW>()) return h;
+    const int xr = min(x0 + kTW, bx), yb = min(y0 + kTY, by);  // the right column and bottom row
+    int hx, hy;
+    if (tid < kTW) {
+        hx = x0 + tid;
+        hy = y0 - 1;
+        h.er = hx < bx ? 0 : -1;
+        h.ec = tid + 1;
+    } else if (tid < 2 * kTW) {
+        const int c = tid - kTW;
+        hx = x0 + c;
+        hy = yb;
+        h.er = hx < bx ? yb - y0 + 1 : -1;
+        h.ec = c + 1;
+    } else if (tid < 2 * kTW + kTY) {
+        const int r = tid - 2 * kTW;
+        hx = x0 - 1;
+        hy = y0 + r;
+        h.er = hy < by ? r + 1 : -1;
+        h.ec = 0;
+    } else {
+        const int r = tid - 2 * kTW - kTY;
+        hx = xr;
+        hy = y0 + r;
+        h.er = hy < by ? r + 1 : -1;
+        h.ec = xr - x0 + 1;
+    }
+    if (h.er >= 0) {
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, hx, hy);
+        h.p = s.p + z0 * s.stride;
+        h.stride = s.stride;
+    }
+    return h;
+}
+
+template <int TW>
+__host__ __device__ constexpr int narrow_plane()
+{
+    return (kNT<double> / TW + 2) * (TW + 2) + 1;  // + one slot written by lanes without a slot of their own
+}
+
+// [2 buffers][2 planes][plane] 64-bit values, then one 96-bit plane (the
+// fallback step's second plane; its first is the current 64-bit buffer).
+template <int TW>
+__host__ __device__ constexpr int narrow_smem_bytes()
+{
+    return 4 * narrow_plane<TW>() * 8 + narrow_plane<TW>() * (int)sizeof(frame::W96);
+}
+
+template <int TW, int RD>
+__host__ __device__ constexpr int narrow_engine_bytes()
+{
+    return narrow_smem_bytes<TW>() + RD * (kNT<double> + ring_extra<double, TW>()) * (int)sizeof(double);
+}
+
+// The exact mean over one tile of block b (TW x 256/TW columns, planes z0 ..
+// z1-1), reading buffer p and writing buffer p^1. PULL: halo values come
+// from the neighbouring blocks (the fused and persistent forms); otherwise
+// from the block's ghost layer (only for blocks whose ghost layer the
+// unfused flow has filled). Each thread owns one column and computes two
+// planes per step; copies run RD - 2 planes ahead.
+template <bool PULL, bool CG, int RD, int TW>
+__device__ void tile_engine_narrow(double* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                                   const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
+                                   unsigned char* smraw, SlowList* slow)
+{
+    using T = double;
+    using W = frame::W96;
+    constexpr int kN = kNT<T>, kTX = TW, kTY = kN / TW, kSW = TW + 2, kEr = ring_extra<T, TW>();
+    constexpr int kPlane = narrow_plane<TW>();
+    constexpr uint32_t kRowC = kN * sizeof(T), kRowE = kEr * sizeof(T);
+    static_assert(RD >= 4 && RD % 2 == 0, "ring depth");
+    static_assert(2 * kPlane * 8 == kPlane * (int)sizeof(W), "a 64-bit plane pair holds one 96-bit plane");
+    uint64_t* const nsm = (uint64_t*)smraw;                   // [2 buffers][2 planes][kPlane]
+    W* const wx = (W*)(smraw + 4 * kPlane * 8);               // [kPlane]
+    T* const rc = (T*)(smraw + narrow_smem_bytes<TW>());      // [RD][kN]
+    T* const re = rc + RD * kN;                               // [RD][kEr]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int eref = frame_e[d.inst] + 1;
+    // the 64-bit frame needs eref >= 13 (normal results); below that every
+    // step takes the 96-bit frame
+    const bool nok = eref >= 13;
+    const uint32_t elo = nframe::elo_hi(eref), nscale = nframe::scale_hi(eref);
+    const int tid = threadIdx.x, tx = tid % kTX, ty = tid / kTX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int64_t plane = d.plane;
+    if (tid == 0) slow->n = 0;
+
+    // own stream (interior columns only): the plane above the current one,
+    // planes z0+1 .. z1-1 copied; plane z1 is held in a register; the two
+    // current planes are carried as frame integers with their window flags
+    const bool k1 = x < bx && y < by;
+    const T* osrc = pool;
+    int olim = z0;
+    T zhiv = T(0);
+    T* out = pool;
+    uint64_t wzm = 0u, wc = 0u;
+    bool gzm = true, gc = true;
+    if (k1) {
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        osrc = col + (z0 + 1) * plane;
+        olim = z1 - 1;
+        zhiv = ldv<T, CG>(z1 == bz ? z_source<T, PULL>(pool, desc, d, p, x, y, 5) : col + z1 * plane);
+        out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
+        const T* zlo = z0 == 0 ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : col + (z0 - 1) * plane;
+        wzm = nframe::of0(ldv<T, CG>(zlo), elo, gzm);
+        wc = nframe::of(ldv<T, CG>(col + z0 * plane), elo, gc);
+    }
+    bool gzh;
+    const uint64_t zhn = nframe::of0(zhiv, elo, gzh);
+    // halo-ring slots, as in the 96-bit engine (kSplit: two threads per
+    // slot, one plane parity each)
+    constexpr bool kSplit = 2 * kEr <= kN;
+    constexpr int kHT = kSplit ? 2 * kEr : kEr;
+    const int hq = kSplit && tid >= kEr ? 1 : 0;
+    const int hj = tid - hq * kEr;
+    const HaloSlot<T> hs = halo_slot_edge<PULL, TW>(pool, desc, d, p, x0, y0, z0, tid < kHT ? hj : kN);
+    const bool hv = hs.er >= 0;
+    const int hbase = hv ? hs.er * kSW + hs.ec : kPlane - 1;  // slot within a plane
+    const int hslot = hbase + hq * kPlane;                    // within a buffer's plane pair
+    const int64_t hstr = hs.stride;
+    const T* hsrc = hs.p + hq * hstr;
+    const int hlim = hv ? z1 : z0;
+    const bool halo_warp = __any_sync(0xffffffffu, tid < kHT);
+    const int own = (ty + 1) * kSW + tx + 1;
+    const int ownw = k1 ? own : kPlane - 1;  // lanes outside the block store into the spare slot
+    const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + tid);
+    const T* const mye = re + (tid < kHT ? hj : 0) + hq * kEr;
+    const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(mye);
+    int next = z0;
+    auto copy_pair = [&](int sl) {
+        cp_async_if<sizeof(T)>(rc_s + sl * kRowC, osrc, next < olim);
+        cp_async_if<sizeof(T)>(rc_s + (sl + 1) * kRowC, osrc + plane, next + 1 < olim);
+        if (halo_warp) {
+            if constexpr (kSplit) {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next + hq < hlim);
+            } else {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
+                cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+            }
+            hsrc += 2 * hstr;
+        }
+        cp_async_commit();
+        osrc += 2 * plane;
+        next += 2;
+    };
+#pragma unroll
+    for (int i = 0; i < RD - 2; i += 2) copy_pair(i);
+    __syncthreads();  // slow->n = 0 visible before any append
+
+    int s = 0;  // ring slot of plane-iteration k (even)
+    int bsel = 0;
+    auto step = [&](auto two_c, auto last_c, int k) {
+        constexpr bool TWO = decltype(two_c)::value;
+        constexpr bool LAST = decltype(last_c)::value;  // plane z1 may be among k+1, k+2
+        copy_pair(s == 0 ? RD - 2 : s - 2);
+        cp_async_wait<RD / 2 - 1>();
+        uint64_t* const n0 = nsm + bsel * (2 * kPlane);
+        uint64_t* const n1 = n0 + kPlane;
+        bool g0, g1 = true;
+        uint64_t c0 = nframe::of(rc[s * kN + tid], elo, g0);
+        if (LAST && k + 1 >= z1) {
+            c0 = zhn;
+            g0 = gzh;
+        }
+        uint64_t c1 = 0u;
+        if (TWO) {
+            c1 = nframe::of(rc[(s + 1) * kN + tid], elo, g1);
+            if (LAST && k + 2 >= z1) {
+                c1 = zhn;
+                g1 = gzh;
+            }
+        }
+        n0[ownw] = wc;
+        if (TWO) n1[ownw] = c0;
+        bool gh = true;
+        if (halo_warp) {
+            if constexpr (kSplit) {
+                if (TWO || hq == 0) n0[hslot] = nframe::of0(mye[s * kEr], elo, gh);
+            } else {
+                bool gh1;
+                n0[hslot] = nframe::of0(mye[s * kEr], elo, gh);
+                if (TWO) {
+                    n1[hslot] = nframe::of0(mye[(s + 1) * kEr], elo, gh1);
+                    gh = gh && gh1;
+                }
+            }
+        }
+        const bool bad = !nok || (k1 && !(gzm && gc && g0 && g1)) || (hv && !gh);
+        if (!__syncthreads_or(bad)) {
+            // every value of the step is in the 64-bit frame
+            const uint64_t t = wc + c0;
+            const uint64_t S0 = t + n0[own - 1] + n0[own + 1] + n0[own - kSW] + n0[own + kSW] + wzm;
+            if (k1) out[0] = nframe::mean7(S0, nscale);
+            if (TWO) {
+                const uint64_t S1 = t + n1[own - 1] + n1[own + 1] + n1[own - kSW] + n1[own + kSW] + c1;
+                if (k1) out[plane] = nframe::mean7(S1, nscale);
+            }
+        } else {
+            // the step in the 96-bit frame: plane k in the current 64-bit
+            // buffer pair (no thread reads it any more: the decision came at
+            // the barrier all of them passed), plane k+1 in the spare plane
+            W* const A = (W*)n0;
+            W* const B = wx;
+            W fzm{}, fc{}, f0{}, f1{};
+            if (k1) {
+                // own planes k and k-1 from global memory, k+1 and k+2 from
+                // the ring (or the plane-z1 register)
+                const T* pk = osrc - (int64_t)(RD + 1) * plane;
+                const T* pzm = (k == z0 && z0 == 0) ? z_source<T, PULL>(pool, desc, d, p, x, y, 4) : pk - plane;
+                fc = frame::of(ldv<T, CG>(pk), eref);
+                fzm = frame::of(ldv<T, CG>(pzm), eref);
+                f0 = frame::of((LAST && k + 1 >= z1) ? zhiv : rc[s * kN + tid], eref);
+                if (TWO) f1 = frame::of((LAST && k + 2 >= z1) ? zhiv : rc[(s + 1) * kN + tid], eref);
+            }
+            A[ownw] = fc;
+            if (TWO) B[ownw] = f0;
+            if (halo_warp) {
+                if constexpr (kSplit) {
+                    if (TWO || hq == 0) (hq ? B : A)[hbase] = frame::of(mye[s * kEr], eref);
+                } else {
+                    A[hbase] = frame::of(mye[s * kEr], eref);
+                    if (TWO) B[hbase] = frame::of(mye[(s + 1) * kEr], eref);
+                }
+            }
+            __syncthreads();
+            uint32_t a0, a1, a2;
+            double o;
+            frame::sum7(fc, A[own - 1], A[own + 1], A[own - kSW], A[own + kSW], fzm, f0, a0, a1, a2);
+            const bool ok0 = frame::mean7_of_sum(a0, a1, a2, eref, o);
+            if (k1 && ok0) out[0] = o;
+            if (k1 && !ok0) {
+                const int i = atomicAdd(&slow->n, 1);
+                if (i < kSlowMax) slow->cell[i] = ((uint32_t)k << 9) | (uint32_t)tid;
+            }
+            if (TWO) {
+                frame::sum7(f0, B[own - 1], B[own + 1], B[own - kSW], B[own + kSW], fc, f1, a0, a1, a2);
+                const bool ok1 = frame::mean7_of_sum(a0, a1, a2, eref, o);
+                if (k1 && ok1) out[plane] = o;
+                if (k1 && !ok1) {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)(k + 1) << 9) | (uint32_t)tid;
+                }
+            }
+        }
+        out += 2 * plane;
+        wzm = c0;
+        gzm = g0;
+        wc = c1;
+        gc = g1;
+        s = s == RD - 2 ? 0 : s + 2;
+        bsel ^= 1;
+    };
+    int k = z0;
+    for (; k + 4 < z1; k += 4) {
+        step(std::true_type{}, std::false_type{}, k);
+        step(std::true_type{}, std::false_type{}, k + 2);
+    }
+    if (k + 2 < z1) {
+        step(std::true_type{}, std::false_type{}, k);
+        k += 2;
+    }
+    if (k + 1 < z1) step(std::true_type{}, std::true_type{}, k);
+    else if (k < z1) step(std::false_type{}, std::true_type{}, k);
+    cp_async_wait<0>();
+    slow_cells<T, OP_EXACT, PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y,
+                                          cell_index<T>(d, p ^ 1, x, y, 0), 0.0, slow);
+}
+
+// ----------------------------------------- two-column 64-bit frame engine
+// The 64-bit frame engine with each thread owning an x-adjacent pair of
+// columns (blocks of even x extent): a tile of TW x 512/TW cells per plane
+// for 256 threads. The pair moves as one 16-byte value everywhere (copy into
+// the ring, ring load, exchange-plane store, result store) and its two cells
+// share partial sums, so the per-step work of copies, addressing and the
+// loop is spread over four cells. The ring holds four planes, so with two
+// steps per pass every ring slot and exchange buffer is a compile-time offset.
+// Exchange-plane row: a spare slot, the left halo, the TW cells (pairs on
+// 16-byte boundaries), the right halo, a spare slot.
+constexpr int kRing2 = 4;
+
+template <int TW>
+__host__ __device__ constexpr int n2_rows()
+{
+    return 2 * kNT<double> / TW;
+}
+
+template <int TW>
+__host__ __device__ constexpr int n2_ring_extra()
+{
+    return 2 * TW + 2 * n2_rows<TW>();
+}
+
+template <int TW>
+__host__ __device__ constexpr int n2_plane()
+{
+    return (n2_rows<TW>() + 2) * (TW + 4) + 2;  // + a spare pair for lanes without a slot
+}
+
+template <int TW>
+__host__ __device__ constexpr int n2_engine_bytes()
+{
+    // exchange planes, the own-pair ring plus one slot for plane z1, the halo ring
+    return 4 * n2_plane<TW>() * 8 + ((kRing2 + 1) * 2 * kNT<double> + kRing2 * n2_ring_extra<TW>()) * (int)sizeof(double);
+}
+
+// The pair (x, x+1) of column (x, y) at plane -1 (zface 4) or bz (zface 5):
+// from the neighbouring block, the Dirichlet pair, or (not PULL) the block's
+// ghost layer. Always 16-byte aligned (x even, rows on 128-byte boundaries).
+template <bool PULL>
+__device__ __forceinline__ const double* z_pair_source(const double* pool, const BlockDesc* desc, const BlockDesc& d,
+                                                       int p, int x, int y, int zface)
+{
+    if constexpr (PULL) {
+        if (d.nbr[zface] < 0) return d.bc2[zface];
+    }
+    return z_source<double, PULL>(pool, desc, d, p, x, y, zface);
+}
+
+template <bool CG>
+__device__ __forceinline__ double2 ld_pair(const double* p)
+{
+    if constexpr (CG) return __ldcg((const double2*)p);
+    else return __ldg((const double2*)p);
+}
+
+// One halo-ring slot per thread for tid < 2 (TW + TY) of the two-column
+// tile (rows y0-1 and the bottom edge, columns x0-1 and the right edge, the
+// edges taken at the block boundary where the tile overhangs it).
+template <bool PULL, int TW>
+__device__ __forceinline__ HaloSlot<double> halo_slot_pair(const double* pool, const BlockDesc* desc,
+                                                           const BlockDesc& d, int p, int x0, int y0, int z0, int tid)
+{
+    using T = double;
+    constexpr int kTW = TW, kTY = n2_rows<TW>(), kSW = TW + 4;
+    const int bx = d.ext[0], by = d.ext[1];
+    HaloSlot<T> h{-1, 0, pool, 0};
+    if (tid >= n2_ring_extra<TW>()) return h;
+    const int xr = min(x0 + kTW, bx), yb = min(y0 + kTY, by);
+    int hx, hy;
+    // (er, ec) here is the slot's row and its index within the row
+    if (tid < kTW) {
+        hx = x0 + tid;
+        hy = y0 - 1;
+        h.er = hx < bx ? 0 : -1;
+        h.ec = 2 + tid;
+    } else if (tid < 2 * kTW) {
+        const int c = tid - kTW;
+        hx = x0 + c;
+        hy = yb;
+        h.er = hx < bx ? yb - y0 + 1 : -1;
+        h.ec = 2 + c;
+    } else if (tid < 2 * kTW + kTY) {
+        const int r = tid - 2 * kTW;
+        hx = x0 - 1;
+        hy = y0 + r;
+        h.er = hy < by ? r + 1 : -1;
+        h.ec = 1;
+    } else {
+        const int r = tid - 2 * kTW - kTY;
+        hx = xr;
+        hy = y0 + r;
+        h.er = hy < by ? r + 1 : -1;
+        h.ec = 2 + xr - x0;
+    }
+    static_assert(kSW == kTW + 4, "row layout");
+    if (h.er >= 0) {
+        const Src<T> s = xy_source<T, PULL>(pool, desc, d, p, hx, hy);
+        h.p = s.p + z0 * s.stride;
+        h.stride = s.stride;
+    }
+    return h;
+}
+
+// After the tile's loop: the cells recorded in the slow list (or, when it
+// overflowed, every cell of the tile) with the exact per-cell routine.
+// Slow-list entries of the two-column engine: (k << 10) | (tid << 1) | cell.
+template <bool PULL, bool CG, int TW>
+__device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* desc, const BlockDesc& d, int b, int p,
+                                              int x0, int y0, int z0, int z1, bool k1, int x, int y, SlowList* slow)
+{
+    constexpr int kTP = TW / 2;
+    __syncthreads();
+    const int n = slow->n;
+    if (n == 0) return;
+    const int tid = threadIdx.x;
+    if (n <= kSlowMax) {
+        for (int i = tid; i < n; i += kNT<double>) {
+            const uint32_t c = slow->cell[i];
+            const int kk = (int)(c >> 10), t = (int)((c >> 1) & 511u), cell = (int)(c & 1u);
+            const int cx = x0 + 2 * (t % kTP) + cell, cy = y0 + t / kTP;
+            pool[cell_index<double>(d, p ^ 1, cx, cy, kk)] = exact_cell<double, PULL, CG, false>(pool, desc, b, p, cx, cy, kk);
+        }
+    } else if (k1) {
+        for (int kk = z0; kk < z1; ++kk)
+            for (int cell = 0; cell < 2; ++cell)
+                pool[cell_index<double>(d, p ^ 1, x + cell, y, kk)] =
+                    exact_cell<double, PULL, CG, false>(pool, desc, b, p, x + cell, y, kk);
+    }
+}
+
+// The exact mean over one two-column tile of block b (bx even): columns x0 ..
+// x0+TW-1, rows y0 .. y0+512/TW-1, planes z0 .. z1-1; buffer p read, p^1
+// written.
+// Steps come in two kinds. The hot step (two planes below z1, compile-time
+// ring phase) has no path but the 64-bit frame: when the tile-wide vote
+// finds a value outside it, the step stops before computing and the generic
+// step resumes it. The generic step (run-time phase, the last planes of the
+// tile, the step after a fallback) falls back to the 96-bit frame itself. The
+// 96-bit path thus stays out of the hot loop, whose registers it would
+// otherwise take.
+template <bool PULL, bool CG, int TW>
+__device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* __restrict__ desc,
+                                    const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
+                                    unsigned char* smraw, SlowList* slow)
+{
+    using T = double;
+    using W = frame::W96;
+    constexpr int RD = kRing2;
+    constexpr int kN = kNT<T>, kTP = TW / 2, kSW = TW + 4, kEr = n2_ring_extra<TW>();
+    constexpr int kPlane = n2_plane<TW>();
+    constexpr uint32_t kRowC = 2 * kN * sizeof(T), kRowE = kEr * sizeof(T);
+    static_assert(kEr <= kN, "every halo-ring slot needs a thread");
+    static_assert(kPlane % 2 == 0 && kSW % 2 == 0, "pairs on 16-byte boundaries");
+    static_assert(4 * kPlane * 8 == 2 * kPlane * (int)sizeof(W), "the four 64-bit planes hold two 96-bit planes");
+    uint64_t* const nsm = (uint64_t*)smraw;                 // [2 buffers][2 planes][kPlane]
+    T* const rc = (T*)(smraw + 4 * kPlane * 8);             // [RD + 1][kN][2]: the ring, then plane z1
+    T* const re = rc + (RD + 1) * 2 * kN;                   // [RD][kEr]
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int eref = frame_e[d.inst] + 1;
+    const bool nok = eref >= 13;  // else every step takes the 96-bit frame
+    const uint32_t elo = nframe::elo_hi(eref), nscale = nframe::scale_hi(eref);
+    const int tid = threadIdx.x, tp = tid % kTP, ty = tid / kTP;
+    const int x = x0 + 2 * tp, y = y0 + ty;
+    const int plane = (int)d.plane;  // below 2^31 elements for every block shape the runtime makes
+    if (tid == 0) slow->n = 0;
+
+    // own pair stream: planes z0+1 .. z1-1 through the ring, plane z1 into its
+    // own slot at the start; the two current planes carried as frame integers
+    const bool k1 = x < bx && y < by;  // both cells: bx is even
+    const T* osrc = pool;
+    int olim = z0;
+    T* out = pool;
+    uint64_t zmA = 0u, zmB = 0u, cA = 0u, cB = 0u;
+    bool gzm = true, gc = true;
+    const uint32_t rz_s = (uint32_t)__cvta_generic_to_shared(rc + 2 * (RD * kN + tid));
+    if (k1) {
+        const T* col = pool + cell_index<T>(d, p, x, y, 0);
+        osrc = col + (int64_t)(z0 + 1) * plane;
+        olim = z1 - 1;
+        out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
+        cp_async_if<16>(rz_s, z1 == bz ? z_pair_source<PULL>(pool, desc, d, p, x, y, 5) : col + (int64_t)z1 * plane,
+                        true);
+        const double2 zl = ld_pair<CG>(z0 == 0 ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4)
+                                               : col + (int64_t)(z0 - 1) * plane);
+        const double2 c0 = ld_pair<CG>(col + (int64_t)z0 * plane);
+        bool g1, g2;
+        zmA = nframe::of0(zl.x, elo, g1);
+        zmB = nframe::of0(zl.y, elo, g2);
+        gzm = g1 && g2;
+        cA = nframe::of(c0.x, elo, g1);
+        cB = nframe::of(c0.y, elo, g2);
+        gc = g1 && g2;
+    }
+    constexpr bool kSplit = 2 * kEr <= kN;
+    constexpr int kHT = kSplit ? 2 * kEr : kEr;
+    const int hq = kSplit && tid >= kEr ? 1 : 0;
+    const int hj = tid - hq * kEr;
+    const HaloSlot<T> hs = halo_slot_pair<PULL, TW>(pool, desc, d, p, x0, y0, z0, tid < kHT ? hj : kN);
+    const bool hv = hs.er >= 0;
+    const int hbase = hv ? hs.er * kSW + hs.ec : kPlane - 1;
+    const int hslot = hbase + hq * kPlane;
+    const int hstr = (int)hs.stride;
+    const T* hsrc = hs.p + hq * hstr;
+    const int hlim = hv ? z1 : z0;
+    const bool halo_warp = __any_sync(0xffffffffu, tid < kHT);
+    const int own = (ty + 1) * kSW + 2 + 2 * tp;
+    const int ownw = k1 ? own : kPlane - 2;
+    const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + 2 * tid);
+    const T* const mye = re + (tid < kHT ? hj : 0) + hq * kEr;
+    const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(mye);
+    int next = z0;
+    // copies for the plane-iterations next, next + 1 into ring slots sl, sl + 1
+    auto copy_c = [&](auto sl_c) {  // sl a compile-time constant
+        constexpr int sl = decltype(sl_c)::value;
+        cp_async_if_off<16, sl * kRowC>(rc_s, osrc, next < olim);
+        cp_async_if_off<16, (sl + 1) * kRowC>(rc_s, osrc + plane, next + 1 < olim);
+        if (halo_warp) {
+            if constexpr (kSplit) {
+                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, next + hq < hlim);
+            } else {
+                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, next < hlim);
+                cp_async_if_off<sizeof(T), (sl + 1) * kRowE>(re_s, hsrc + hstr, next + 1 < hlim);
+            }
+            hsrc += 2 * hstr;
+        }
+        cp_async_commit();
+        osrc += 2 * plane;
+        next += 2;
+    };
+    auto copy_r = [&](int sl) {  // sl known at run time
+        cp_async_if<16>(rc_s + sl * kRowC, osrc, next < olim);
+        cp_async_if<16>(rc_s + (sl + 1) * kRowC, osrc + plane, next + 1 < olim);
+        if (halo_warp) {
+            if constexpr (kSplit) {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next + hq < hlim);
+            } else {
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
+                cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+            }
+            hsrc += 2 * hstr;
+        }
+        cp_async_commit();
+        osrc += 2 * plane;
+        next += 2;
+    };
+    copy_c(std::integral_constant<int, 0>{});
+    __syncthreads();  // slow->n = 0 visible before any append
+
+    // the current step's two new own planes (k+1, k+2) as frame integers
+    uint64_t c0A = 0u, c0B = 0u, c1A = 0u, c1B = 0u;
+    bool g0 = true, g1 = true;
+    // the 64-bit sums and means of planes k (buffer n0) and k+1 (n1)
+    auto narrow = [&](const uint64_t* n0, const uint64_t* n1, bool two) {
+        const uint64_t uA = cA + c0A, uB = cB + c0B;
+        {
+            const ulonglong2 ym = *(const ulonglong2*)(n0 + own - kSW), yp = *(const ulonglong2*)(n0 + own + kSW);
+            const uint64_t SA = uA + cB + n0[own - 1] + ym.x + yp.x + zmA;
+            const uint64_t SB = uB + cA + n0[own + 2] + ym.y + yp.y + zmB;
+            const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
+            if (k1) *(double2*)out = o;
+        }
+        if (two) {
+            const ulonglong2 ym = *(const ulonglong2*)(n1 + own - kSW), yp = *(const ulonglong2*)(n1 + own + kSW);
+            const uint64_t SA = uA + c0B + n1[own - 1] + ym.x + yp.x + c1A;
+            const uint64_t SB = uB + c0A + n1[own + 2] + ym.y + yp.y + c1B;
+            const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
+            if (k1) *(double2*)(out + plane) = o;
+        }
+    };
+    auto advance = [&](bool two) {
+        out += 2 * plane;
+        zmA = c0A;
+        zmB = c0B;
+        gzm = g0;
+        cA = c1A;
+        cB = c1B;
+        gc = g1;
+        (void)two;
+    };
+    // hot step: planes k, k+1 with k + 2 < z1, ring phase S. Returns false,
+    // with nothing computed or advanced, when the step needs the 96-bit frame.
+    auto hot = [&](auto s_c) -> bool {
+        constexpr int S = decltype(s_c)::value;
+        constexpr int BS = S / 2;
+        copy_c(std::integral_constant<int, S == 0 ? 2 : 0>{});
+        cp_async_wait<1>();
+        uint64_t* const n0 = nsm + BS * (2 * kPlane);
+        uint64_t* const n1 = n0 + kPlane;
+        bool ga, gb;
+        const double2 v0 = *(const double2*)(rc + (S * kN + tid) * 2);
+        const double2 v1 = *(const double2*)(rc + ((S + 1) * kN + tid) * 2);
+        c0A = nframe::of(v0.x, elo, ga);
+        c0B = nframe::of(v0.y, elo, gb);
+        g0 = ga && gb;
+        c1A = nframe::of(v1.x, elo, ga);
+        c1B = nframe::of(v1.y, elo, gb);
+        g1 = ga && gb;
+        *(ulonglong2*)(n0 + ownw) = make_ulonglong2(cA, cB);
+        *(ulonglong2*)(n1 + ownw) = make_ulonglong2(c0A, c0B);
+        bool gh = true;
+        if (halo_warp) {
+            if constexpr (kSplit) {
+                n0[hslot] = nframe::of0(mye[S * kEr], elo, gh);
+            } else {
+                bool gh1;
+                n0[hslot] = nframe::of0(mye[S * kEr], elo, gh);
+                n1[hslot] = nframe::of0(mye[(S + 1) * kEr], elo, gh1);
+                gh = gh && gh1;
+            }
+        }
+        const bool bad = !nok || (k1 && !(gzm && gc && g0 && g1)) || (hv && !gh);
+        if (__syncthreads_or(bad)) return false;
+        narrow(n0, n1, true);
+        advance(true);
+        return true;
+    };
+    int k = z0, ph = 0;  // the next step computes plane k (and k+1) from ring slots ph, ph + 1
+    // generic step at (k, ph); with `resume` the copies, conversions and
+    // stores were made by a hot step that found a value outside the 64-bit
+    // frame, and only its computation remains
+    auto generic = [&](bool resume) {
+        const int S = ph;
+        const bool two = k + 1 < z1;           // planes k and k+1
+        const bool zfirst = !two;              // plane k+1 is z1
+        const bool zsecond = two && k + 2 >= z1;  // plane k+2 is z1
+        uint64_t* const n0 = nsm + (S >> 1) * (2 * kPlane);
+        uint64_t* const n1 = n0 + kPlane;
+        bool fall = true;
+        if (!resume) {
+            copy_r(S == 0 ? 2 : 0);
+            cp_async_wait<1>();
+            const double2 zh = *(const double2*)(rc + (RD * kN + tid) * 2);
+            const double2 v0 = zfirst ? zh : *(const double2*)(rc + (S * kN + tid) * 2);
+            const double2 v1 = zsecond ? zh : *(const double2*)(rc + ((S + 1) * kN + tid) * 2);
+            // plane z1 is only ever a z neighbour and may be zero; every other
+            // plane becomes a cell's own value and must not be
+            bool ga, gb;
+            c0A = nframe::of0(v0.x, elo, ga);
+            c0B = nframe::of0(v0.y, elo, gb);
+            g0 = ga && gb && (zfirst || (c0A != 0u && c0B != 0u));
+            c1A = c1B = 0u;
+            g1 = true;
+            if (two) {
+                c1A = nframe::of0(v1.x, elo, ga);
+                c1B = nframe::of0(v1.y, elo, gb);
+                g1 = ga && gb && (zsecond || (c1A != 0u && c1B != 0u));
+            }
+            *(ulonglong2*)(n0 + ownw) = make_ulonglong2(cA, cB);
+            if (two) *(ulonglong2*)(n1 + ownw) = make_ulonglong2(c0A, c0B);
+            bool gh = true;
+            if (halo_warp) {
+                if constexpr (kSplit) {
+                    if (two || hq == 0) n0[hslot] = nframe::of0(mye[S * kEr], elo, gh);
+                } else {
+                    bool gh1;
+                    n0[hslot] = nframe::of0(mye[S * kEr], elo, gh);
+                    if (two) {
+                        n1[hslot] = nframe::of0(mye[(S + 1) * kEr], elo, gh1);
+                        gh = gh && gh1;
+                    }
+                }
+            }
+            const bool bad = !nok || (k1 && !(gzm && gc && g0 && g1)) || (hv && !gh);
+            if (!__syncthreads_or(bad)) {
+                narrow(n0, n1, two);
+                fall = false;
+            }
+        }
+        if (fall) {
+            // the step in the 96-bit frame from the raw values: plane k in the
+            // first pair of 64-bit planes, plane k+1 in the second (every
+            // thread has passed the step's barrier, so no 64-bit plane is read
+            // any more)
+            W* const A = (W*)nsm;
+            W* const B = A + kPlane;
+            W fc0{}, fc1{}, fz0{}, fz1{}, f00{}, f01{}, f10{}, f11{};
+            if (k1) {
+                const T* pk = osrc - (RD + 1) * plane;  // osrc is at plane k + RD + 1
+                const double2 c = ld_pair<CG>(pk);
+                const double2 zm = ld_pair<CG>((k == z0 && z0 == 0) ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4)
+                                                                    : pk - plane);
+                const double2 zh = *(const double2*)(rc + (RD * kN + tid) * 2);
+                const double2 a = zfirst ? zh : *(const double2*)(rc + (S * kN + tid) * 2);
+                const double2 bb = zsecond ? zh : *(const double2*)(rc + ((S + 1) * kN + tid) * 2);
+                fc0 = frame::of(c.x, eref);
+                fc1 = frame::of(c.y, eref);
+                fz0 = frame::of(zm.x, eref);
+                fz1 = frame::of(zm.y, eref);
+                f00 = frame::of(a.x, eref);
+                f01 = frame::of(a.y, eref);
+                if (two) {
+                    f10 = frame::of(bb.x, eref);
+                    f11 = frame::of(bb.y, eref);
+                }
+            }
+            A[ownw] = fc0;
+            A[ownw + 1] = fc1;
+            if (two) {
+                B[ownw] = f00;
+                B[ownw + 1] = f01;
+            }
+            if (halo_warp) {
+                if constexpr (kSplit) {
+                    if (two || hq == 0) (hq ? B : A)[hbase] = frame::of(mye[S * kEr], eref);
+                } else {
+                    A[hbase] = frame::of(mye[S * kEr], eref);
+                    if (two) B[hbase] = frame::of(mye[(S + 1) * kEr], eref);
+                }
+            }
+            __syncthreads();
+            auto put = [&](const W& c, const W& xm, const W& xp, const W& ym, const W& yp, const W& zm, const W& zp,
+                           T* o, int kk, int cell) {
+                uint32_t a0, a1, a2;
+                double v;
+                frame::sum7(c, xm, xp, ym, yp, zm, zp, a0, a1, a2);
+                if (frame::mean7_of_sum(a0, a1, a2, eref, v)) {
+                    *o = v;
+                } else {
+                    const int i = atomicAdd(&slow->n, 1);
+                    if (i < kSlowMax) slow->cell[i] = ((uint32_t)kk << 10) | ((uint32_t)tid << 1) | (uint32_t)cell;
+                }
+            };
+            if (k1) {
+                const int o = own;
+                put(fc0, A[o - 1], fc1, A[o - kSW], A[o + kSW], fz0, f00, out, k, 0);
+                put(fc1, fc0, A[o + 2], A[o + 1 - kSW], A[o + 1 + kSW], fz1, f01, out + 1, k, 1);
+                if (two) {
+                    put(f00, B[o - 1], f01, B[o - kSW], B[o + kSW], fc0, f10, out + plane, k + 1, 0);
+                    put(f01, f00, B[o + 2], B[o + 1 - kSW], B[o + 1 + kSW], fc1, f11, out + plane + 1, k + 1, 1);
+                }
+            }
+            __syncthreads();  // the next step's 64-bit stores overwrite A and B
+        }
+        advance(two);
+        k += two ? 2 : 1;
+        ph ^= 2;
+    };
+    using S0 = std::integral_constant<int, 0>;
+    using S2 = std::integral_constant<int, 2>;
+    for (;;) {
+        bool stop = false;
+        if (ph == 0) {
+            for (; k + 4 < z1; k += 4) {
+                if (!hot(S0{})) {
+                    stop = true;
+                    break;
+                }
+                if (!hot(S2{})) {
+                    k += 2;
+                    ph = 2;
+                    stop = true;
+                    break;
+                }
+            }
+        }
+        if (stop) generic(true);
+        // realign the ring phase, or the tile's last planes
+        while (k < z1 && (ph != 0 || k + 4 >= z1)) generic(false);
+        if (k >= z1) break;
+    }
+    cp_async_wait<0>();
+    n2_slow_cells<PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, slow);
+}
+
+// One binary64 work unit (TW x 512/TW columns) of the exact mean: the
+// two-column engine for blocks of even x extent, else the single-column
+// engine on the unit's two halves.
+template <bool PULL, bool CG, int TW>
+__device__ __forceinline__ void exact_unit(double* pool, const BlockDesc* desc, const int32_t* frame_e, int b, int p,
+                                           int x0, int y0, int z0, int z1, SlowList* slow)
+{
+    if ((desc[b].ext[0] & 1) == 0) {
+        tile_engine_narrow2<PULL, CG, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow);
+    } else {
+        tile_engine_narrow<PULL, CG, kRing<double>, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow);
+        const int y1 = y0 + kNT<double> / TW;
+        if (y1 < desc[b].ext[1]) {
+            __syncthreads();
+            tile_engine_narrow<PULL, CG, kRing<double>, TW>(pool, desc, frame_e, b, p, x0, y1, z0, z1, jac_dyn_sm,
+                                                            slow);
+        }
+    }
+}
+
+// One binary64 work unit of the sequential rule: the single-plane engine on
+// the unit's two halves (TW x 256/TW columns each).
+template <bool PULL, bool CG, int TW>
+__device__ __forceinline__ void seq_unit(double* pool, const BlockDesc* desc, int b, int p, int x0, int y0, int z0,
+                                         int z1)
+{
+    tile_engine<double, OP_SEQ, PULL, CG, kRing<double>, TW>(pool, desc, b, p, x0, y0, z0, z1, jac_dyn_sm);
+    const int y1 = y0 + kNT<double> / TW;
+    if (y1 < desc[b].ext[1]) {
+        __syncthreads();
+        tile_engine<double, OP_SEQ, PULL, CG, kRing<double>, TW>(pool, desc, b, p, x0, y1, z0, z1, jac_dyn_sm);
+    }
+}
+
 // Dynamic shared memory of the update kernels for op OP.
 template <typename T, int OP, int TW>
 __host__ __device__ constexpr int kernel_bytes()
 {
-    if constexpr (OP == OP_EXACT) return pair_engine_bytes<T, OP, TW, kRing<T>>();
-    else return engine_bytes<T, OP, TW, kRing<T>>();
+    if constexpr (OP == OP_EXACT) {
+        constexpr int a = n2_engine_bytes<TW>(), b = narrow_engine_bytes<TW, kRing<T>>();
+        return a > b ? a : b;
+    } else {
+        return engine_bytes<T, OP, TW, kRing<T>>();
+    }
 }
 
 // ------------------------------------------------------- ring engine (SEQ)
@@ -1195,21 +1995,20 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_ring(T* pool, con
 }
 
 template <typename T, int OP, int TW>
-__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                                int b, int p)
 {
     __shared__ SlowList slow;
     if constexpr (OP == OP_EXACT)
-        tile_engine_pair<T, OP_EXACT, false, false, kRing<T>, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW,
-                                                                  blockIdx.y * (kNT<T> / TW), 0, desc[b].ext[2],
-                                                                  jac_dyn_sm, &slow);
+        exact_unit<false, false, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW, blockIdx.y * (2 * kNT<T> / TW), 0,
+                                     desc[b].ext[2], &slow);
     else
         tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, b, p, blockIdx.x * TW, blockIdx.y * (kNT<T> / TW),
                                                        0, desc[b].ext[2], jac_dyn_sm);
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p)
 {
     __shared__ SlowList slow;
@@ -1217,10 +2016,9 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_fused_step(T* pool, con
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
         if constexpr (OP == OP_EXACT)
-            tile_engine_pair<T, OP_EXACT, true, false, kRing<T>, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0,
-                                                                     u.z0, u.z1, jac_dyn_sm, &slow);
+            exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
         else
-            tile_engine<T, OP, true, false, kRing<T>, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
+            seq_unit<true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
     });
 }
 
@@ -1254,7 +2052,7 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
 template <typename T, int OP, bool RING>
-__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
+__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after)
@@ -1310,11 +2108,9 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>)
                 // barrier above order them after the neighbours' releases
                 f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             } else if constexpr (OP == OP_EXACT) {
-                tile_engine_pair<T, OP_EXACT, true, true, kRing<T>, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1,
-                                                                        u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
+                exact_unit<true, true, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1, &slow);
             } else {
-                tile_engine<T, OP, true, true, kRing<T>, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1,
-                                                             jac_dyn_sm);
+                seq_unit<true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             }
         });
         __syncthreads();
@@ -1341,11 +2137,11 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_residual(const T* pool,
         constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
         acc = tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
                                                                   u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
-        if constexpr (sizeof(T) == 4) {
-            // a binary32 unit is two engine tiles tall
+        {
+            // a unit is two engine tiles tall
             __syncthreads();
             acc += tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
-                                                                       p, u.x0, u.y0 + kNT<float> / TW, u.z0, u.z1,
+                                                                       p, u.x0, u.y0 + kNT<T> / TW, u.z0, u.z1,
                                                                        jac_dyn_sm, &slow);
         }
     });
@@ -1539,7 +2335,7 @@ __global__ void k_init_ghosts(T* pool, const BlockDesc* desc)
 
 // ---------------------------------------------------------------- launchers
 
-int tile_rows(int tw, bool f32) { return f32 ? 2 * kNT<float> / tw : kNT<double> / tw; }
+int tile_rows(int tw, bool f32) { return f32 ? 2 * kNT<float> / tw : 2 * kNT<double> / tw; }
 int engine_threads(bool f32) { return f32 ? kNT<float> : kNT<double>; }
 bool tile_width_supported(int tw) { return tw == 16 || tw == 32 || tw == 64; }
 
@@ -1571,7 +2367,9 @@ static void stencil_block_t(const LaunchArgs& a, int arith, int b, int nx_tiles,
     dim3 grid(nx_tiles, ny_tiles * per, 1);
     if constexpr (sizeof(T) == 8) {
         if (arith == 1) {
-            k_stencil_block<T, OP_EXACT, TW><<<grid, kNT<T>, kernel_bytes<T, OP_EXACT, TW>(), s>>>((T*)a.pool, a.desc, a.frame, b, p);
+            // the exact-mean engines take a whole unit per CTA
+            k_stencil_block<T, OP_EXACT, TW><<<dim3(nx_tiles, ny_tiles, 1), kNT<T>, kernel_bytes<T, OP_EXACT, TW>(), s>>>(
+                (T*)a.pool, a.desc, a.frame, b, p);
             return;
         }
     }

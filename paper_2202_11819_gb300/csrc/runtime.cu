@@ -489,6 +489,7 @@ int64_t instance_geometry(const jac_ctx* h, Instance& I)
                     d.bc[f] = I.bc[f];
                     d.bcf[f] = (float)I.bc[f];
                     d.bcf2[f][0] = d.bcf2[f][1] = d.bcf[f];
+                    d.bc2[f][0] = d.bc2[f][1] = d.bc[f];
                 }
                 d.pitch = (int32_t)round_up(OX + d.ext[0] + 1, OX);
                 d.plane = (int64_t)d.pitch * (d.ext[1] + 2);

@@ -83,3 +83,51 @@ extern "C" double host_sum_squares(const long long* L, int n, int scale)
     for (int i = 0; i < n; ++i) jac::frame::add_square(L[i], a0, a1, a2);
     return jac::frame::u192_to_double_scaled(a0, a1, a2, scale);
 }
+
+// The 96-bit frame value of v (four words, the last one padding).
+extern "C" void host_frame_of(double v, int eref, uint32_t* w)
+{
+    const jac::frame::W96 r = jac::frame::of(v, eref);
+    w[0] = r.w0;
+    w[1] = r.w1;
+    w[2] = r.w2;
+    w[3] = r.w3;
+}
+
+// The 64-bit frame: a value's frame integer and whether it lies in the
+// window (zero_ok: the zero-accepting form), and the same integer widened
+// to the 96-bit frame.
+extern "C" int host_nframe_of(double v, int eref, int zero_ok, unsigned long long* w)
+{
+    bool ok;
+    const uint32_t e = jac::nframe::elo_hi(eref);
+    *w = zero_ok ? jac::nframe::of0(v, e, ok) : jac::nframe::of(v, e, ok);
+    return ok ? 1 : 0;
+}
+
+extern "C" void host_nframe_widen(unsigned long long w, uint32_t* out)
+{
+    const jac::frame::W96 r = jac::nframe::widen(w);
+    out[0] = r.w0;
+    out[1] = r.w1;
+    out[2] = r.w2;
+}
+
+// The 64-bit frame mean as the engine forms it: the cell v[0] through `of`,
+// its six neighbours through `of0`, one 64-bit sum, then mean7. Returns 0
+// (out unset) when the engine would take the 96-bit frame instead.
+extern "C" int host_nframe_mean7(const double* v, int eref, double* out)
+{
+    using namespace jac::nframe;
+    if (eref < 13) return 0;
+    const uint32_t e = elo_hi(eref);
+    bool ok;
+    uint64_t S = of(v[0], e, ok);
+    if (!ok) return 0;
+    for (int i = 1; i < 7; ++i) {
+        S += of0(v[i], e, ok);
+        if (!ok) return 0;
+    }
+    *out = mean7(S, scale_hi(eref));
+    return 1;
+}

@@ -4,6 +4,7 @@ oracle's wide-accumulator arithmetic and exact rationals. Covers both the
 fast 128-bit-frame path and the wide fallback."""
 
 import ctypes
+import math
 import os
 import subprocess
 import tempfile
@@ -422,3 +423,153 @@ def test_top_quotient_multiplier_has_no_overshoot_below_2_61():
     # above 2^64 / 5 the excess can carry past the next integer
     bad = [n for n in (2 ** 64 - 1 - k for k in range(14)) if (n * c) >> 64 != n // 7]
     assert bad
+
+
+# ---------------------------------------------------------------- 64-bit frame
+def _nframe_lib(host_lib):
+    u64p = ctypes.POINTER(ctypes.c_ulonglong)
+    host_lib.host_nframe_of.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, u64p]
+    host_lib.host_nframe_of.restype = ctypes.c_int
+    host_lib.host_nframe_widen.argtypes = [ctypes.c_ulonglong, ctypes.c_void_p]
+    host_lib.host_nframe_widen.restype = None
+    host_lib.host_frame_of.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    host_lib.host_frame_of.restype = None
+    host_lib.host_nframe_mean7.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    host_lib.host_nframe_mean7.restype = ctypes.c_int
+    return host_lib
+
+
+def _in_window_value(rng, eref):
+    e = int(rng.integers(eref - 9, eref))
+    return float(np.ldexp(1.0 + float(rng.integers(0, 2 ** 52)) * 2.0 ** -52, e - 1023))
+
+
+def test_narrow_frame_conversion_is_the_exact_scaled_value(host_lib):
+    """A value is accepted exactly when it is a positive normal number whose
+    exponent field lies in [eref - 9, eref - 1] (or +0 in the zero-accepting
+    form), and its frame integer is then v * 2^(1084 - eref) exactly; widened,
+    it equals the 96-bit frame value of the same number."""
+    lib = _nframe_lib(host_lib)
+    rng = np.random.default_rng(31)
+    w = ctypes.c_ulonglong()
+    wide = np.zeros(4, dtype=np.uint32)
+    widened = np.zeros(3, dtype=np.uint32)
+    for _ in range(6000):
+        eref = int(rng.integers(13, 2048))
+        kind = int(rng.integers(0, 6))
+        if kind <= 2:
+            v = _in_window_value(rng, eref)
+        elif kind == 3:  # just outside, below or above
+            e = eref - 10 if rng.random() < 0.5 else eref
+            v = float(np.ldexp(1.0 + rng.random(), min(max(e, 1), 2046) - 1023))
+        elif kind == 4:
+            v = -_in_window_value(rng, eref)
+        else:
+            v = [0.0, -0.0, 2.0 ** -1074, 2.0 ** -1030 * 3][int(rng.integers(0, 4))]
+        fe = exp_field(v)
+        inside = v > 0 and eref - 9 <= fe <= eref - 1
+        for zero_ok in (0, 1):
+            ok = lib.host_nframe_of(v, eref, zero_ok, ctypes.byref(w))
+            want_ok = inside or (zero_ok == 1 and v == 0.0 and math.copysign(1.0, v) > 0)
+            assert bool(ok) == want_ok, (v, eref, zero_ok)
+            if ok:
+                exact = Fraction(v) * Fraction(2) ** (1084 - eref)
+                assert exact.denominator == 1 and w.value == exact.numerator, (v, eref)
+                if v != 0.0:
+                    lib.host_frame_of(v, eref, wide.ctypes.data)
+                    lib.host_nframe_widen(w.value, widened.ctypes.data)
+                    assert list(widened) == list(wide[:3]), (v, eref)
+
+
+def test_narrow_frame_mean7_matches_oracle(host_lib):
+    """Wherever the 64-bit frame accepts a cell and its neighbours, its mean
+    is the correctly rounded one: random data over the whole window (sums
+    from 2^52 to 7 * 2^61, so every normalising shift), zeros among the
+    neighbours, the largest and smallest values, and typical [0, 1) data
+    (which it must essentially always accept)."""
+    lib = _nframe_lib(host_lib)
+    rng = np.random.default_rng(32)
+    out = ctypes.c_double()
+    hits = 0
+    cases = []
+    for _ in range(20000):
+        eref = int(rng.integers(13, 2048))
+        v = [_in_window_value(rng, eref) for _ in range(7)]
+        for i in range(1, 7):
+            if rng.random() < 0.15:
+                v[i] = 0.0
+        cases.append((v, eref))
+    for eref in (13, 14, 1024, 2047):
+        lo = float(np.ldexp(1.0, eref - 9 - 1023))
+        hi = float(np.ldexp(2.0 - 2.0 ** -52, eref - 1 - 1023))
+        cases += [([lo] + [0.0] * 6, eref), ([lo] * 7, eref), ([hi] * 7, eref), ([hi] + [lo] * 6, eref),
+                  ([lo] + [hi] * 6, eref), ([hi] + [0.0] * 6, eref)]
+    for v, eref in cases:
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        assert lib.host_nframe_mean7(a.ctypes.data, eref, ctypes.byref(out)), (v, eref)
+        want = oracle.exact_mean7(a)
+        assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (v, eref)
+        hits += 1
+    ok = 0
+    for _ in range(5000):
+        a = np.ascontiguousarray(rng.random(7))
+        if lib.host_nframe_mean7(a.ctypes.data, 1024, ctypes.byref(out)):
+            ok += 1
+            assert out.value == oracle.exact_mean7(a)
+    assert ok > 4700
+    # the general cases: accepted only inside the window, and then exact
+    for v in mean_cases(rng):
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        E = max(exp_field(x) for x in a)
+        for extra in (1, 2, 5, 9):
+            eref = max(E, 0) + extra
+            if lib.host_nframe_mean7(a.ctypes.data, eref, ctypes.byref(out)):
+                want = oracle.exact_mean7(a)
+                assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), (v, eref)
+
+
+def narrow_tie_cases(rng, n):
+    """Seven values in [2^-8, 1) whose exact sum is 7t + d 2^-60, t an odd
+    multiple of 2^-54 in [0.5, 1) (a binary64 midpoint) and d in
+    {0, 1, -1, 8, -8}: exact ties of the mean, and near-ties decided by the
+    last unit of the 64-bit frame (2^-60 for a frame whose top binade is
+    [1, 2)). With d = +-8 the three bits the normalised sum drops are zero, so
+    only the remainder of the division tells a near-tie from a tie."""
+    out = []
+    u = Fraction(1, 2 ** 60)
+    while len(out) < 5 * n:
+        t = Fraction(2 * int(rng.integers(2 ** 52, 2 ** 53)) + 1, 2 ** 54)
+        w = Fraction(int(rng.integers(2 ** 46, 2 ** 47)), 2 ** 54)  # in [2^-8, 2^-7)
+        a4 = [Fraction(int(rng.integers(2 ** 52, 2 ** 53)), 2 ** 53) for _ in range(4)]
+        R = 7 * t - w - sum(a4)
+        lo = max(Fraction(1, 2), R - Fraction(1, 2))
+        hi = min(Fraction(1), R - Fraction(1, 4))
+        if lo >= hi:
+            continue
+        a5 = Fraction(int(rng.integers(math.ceil(lo * 2 ** 53), math.floor(hi * 2 ** 53))), 2 ** 53)
+        a6 = R - a5
+        if not (Fraction(1, 4) <= a6 < Fraction(1, 2)) or (a6 * 2 ** 54).denominator != 1:
+            continue
+        for d in (0, 1, -1, 8, -8):
+            vals = [float(x) for x in a4 + [a5, a6, w + d * u]]
+            assert sum(Fraction(x) for x in vals) == 7 * t + d * u
+            out.append(vals)
+    return out
+
+
+def test_narrow_frame_mean7_ties_and_near_ties(host_lib):
+    lib = _nframe_lib(host_lib)
+    rng = np.random.default_rng(33)
+    out = ctypes.c_double()
+    n = 0
+    for vals in narrow_tie_cases(rng, 400):
+        a = np.ascontiguousarray(vals, dtype=np.float64)
+        exact = sum(Fraction(float(x)) for x in a) / 7
+        assert (exact * 2 ** 53).denominator != 1  # not representable: a tie or a near-tie
+        want = oracle.exact_mean7(a)
+        assert want == float(exact)
+        for order in (a, a[::-1].copy()):
+            assert lib.host_nframe_mean7(order.ctypes.data, 1024, ctypes.byref(out))
+            assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), vals
+            n += 1
+    assert n == 4000

@@ -406,7 +406,7 @@ def test_exact_rule_within_1e12_relative_of_sequential_oracle_at_1000_iterations
 
 def _tiles(info, dims, block):
     tw = info["tile_w"]
-    th = 256 // tw
+    th = 512 // tw  # binary64 work units: TW x 512/TW columns
     zd = info["zdepth"] if info["zdepth"] > 0 else block[2]
     nb = [-(-dims[a] // block[a]) for a in range(3)]
     per = -(-block[0] // tw) * -(-block[1] // th) * -(-block[2] // zd)
