@@ -77,6 +77,15 @@ JAC_HD inline int clz32(uint32_t x)  // 32 for x == 0
 
 JAC_HD inline int imax(int a, int b) { return a > b ? a : b; }
 
+JAC_HD inline uint32_t umulhi32(uint32_t a, uint32_t b)
+{
+#if defined(__CUDA_ARCH__)
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
 JAC_HD inline uint64_t mulhi_u64(uint64_t a, uint64_t b)
 {
 #if defined(__CUDA_ARCH__)
@@ -998,42 +1007,29 @@ JAC_HD inline uint32_t scale_hi(int eref) { return (uint32_t)(eref - 1081) << 20
 //   normalise it: N = S << lz lies in [2^63, 2^64). M = N >> 3 lies in
 //   [2^60, 2^61), below 2^64 / 5, so the high half of M * ceil(2^64 / 7) is
 //   floor(M / 7) exactly (its excess 5 M / (7 2^64) stays below 1/7, and the
-//   fraction of M / 7 is at most 6/7) and Q = floor(M / 7) has 58 or 59 bits:
-//   at least two below the binary64 rounding position. The sticky
-//   information (a nonzero remainder M - 7Q, or a nonzero bit among the three
-//   N drops) jammed into Q's last bit therefore lets one correctly rounded
-//   integer -> binary64 conversion round the exact quotient S / 7 =
-//   (Q + f) 2^(3 - lz). The scale 2^(3 - lz + eref - 1084) is added to the
-//   exponent field: the result's field is at least eref - 12 >= 1.
+//   fraction of M / 7 is at most 6/7). Q = floor(M / 7) lies in
+//   [2^57.19, 2^58.19): 58 or 59 bits, so its three lowest bits lie below the
+//   binary64 round bit. OR-ing the sticky information (the remainder
+//   M - 7Q, below 7, and the three bits N drops) into them therefore lets
+//   one correctly rounded integer -> binary64 conversion round the exact
+//   quotient S / 7 = (Q + f) 2^(3 - lz). The scale 2^(3 - lz + eref - 1084)
+//   is added to the exponent field: the result's field is at least
+//   eref - 12 >= 1.
+//   The high half of M * C, C = ch 2^32 + cl, is mh ch + floor(t / 2^32) with
+//   t = mh cl + ml ch + floor(ml cl / 2^32) < 2^62.2 (the low partial
+//   product's own low word cannot carry into it): four multiplies with
+//   64-bit accumulation and no carry chain.
 JAC_HD inline double mean7(uint64_t S, uint32_t scale_hi)
 {
+    constexpr uint32_t ch = 0x24924924u, cl = 0x92492493u;  // ceil(2^64 / 7)
     const uint32_t hi = (uint32_t)(S >> 32), lo = (uint32_t)S;
     const int lz = clz32(hi);
     const uint32_t nh = frame::fsl(lo, hi, lz), nl = frame::fsl(0u, lo, lz);
     const uint32_t mh = nh >> 3, ml = frame::fsr(nl, nh, 3);
-    uint32_t ql, qh;
-#if defined(__CUDA_ARCH__)
-    // high half of M * C over 32-bit limbs, C = ceil(2^64 / 7); the middle
-    // column lo(ml cl) carry + ml ch + mh cl stays below 2^62 (no carry out)
-    asm("{\n\t.reg .u32 t, m0, m1;\n\t"
-        "mul.hi.u32 t, %2, 0x92492493;\n\t"
-        "mad.lo.cc.u32 m0, %2, 0x24924924, t;\n\t"
-        "madc.hi.u32 m1, %2, 0x24924924, 0;\n\t"
-        "mad.lo.cc.u32 m0, %3, 0x92492493, m0;\n\t"
-        "madc.hi.u32 m1, %3, 0x92492493, m1;\n\t"
-        "mad.lo.cc.u32 %0, %3, 0x24924924, m1;\n\t"
-        "madc.hi.u32 %1, %3, 0x24924924, 0;\n\t"
-        "}"
-        : "=r"(ql), "=r"(qh)
-        : "r"(ml), "r"(mh));
-#else
-    const uint64_t q = frame::umulhi64(((uint64_t)mh << 32) | ml, 0x2492492492492493ull);
-    ql = (uint32_t)q;
-    qh = (uint32_t)(q >> 32);
-#endif
-    const uint32_t sticky = (ml - 7u * ql) | (nl & 7u);
-    const uint64_t qj = ((uint64_t)qh << 32) | (ql | (sticky != 0u ? 1u : 0u));
-    const uint64_t d = dbits(frame::u64_to_double_rn(qj));
+    const uint64_t t = (uint64_t)mh * cl + (uint64_t)ml * ch + (uint64_t)umulhi32(ml, cl);
+    const uint64_t q = (uint64_t)mh * ch + (t >> 32);
+    const uint32_t sticky = (ml - 7u * (uint32_t)q) | (nl & 7u);
+    const uint64_t d = dbits(frame::u64_to_double_rn(q | sticky));
     return bitsd(d + ((uint64_t)(scale_hi - ((uint32_t)lz << 20)) << 32));
 }
 

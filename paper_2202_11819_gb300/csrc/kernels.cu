@@ -529,6 +529,14 @@ __device__ __forceinline__ void cp_async_if_off(uint32_t dst, const void* src, b
         : "memory");
 }
 
+// cp.async of N bytes to a shared address plus a compile-time offset,
+// unconditionally.
+template <int N, int OFF>
+__device__ __forceinline__ void cp_async_off(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0+%2], [%1], %3;\n" ::"r"(dst), "l"(src), "n"(OFF), "n"(N) : "memory");
+}
+
 template <typename T, int OP, bool PULL, bool CG, int RD, int TW>
 __device__ double tile_engine_pair(T* __restrict__ pool, const BlockDesc* __restrict__ desc,
                                    const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
@@ -1229,7 +1237,10 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     // own pair stream: planes z0+1 .. z1-1 through the ring, plane z1 into its
     // own slot at the start; the two current planes carried as frame integers
     const bool k1 = x < bx && y < by;  // both cells: bx is even
+    // lanes without a column keep a fixed, readable source (the pool's first
+    // pair), so the hot steps can copy unconditionally
     const T* osrc = pool;
+    const int oplane = k1 ? plane : 0;
     int olim = z0;
     T* out = pool;
     uint64_t zmA = 0u, zmB = 0u, cA = 0u, cB = 0u;
@@ -1270,42 +1281,43 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     const uint32_t rc_s = (uint32_t)__cvta_generic_to_shared(rc + 2 * tid);
     const T* const mye = re + (tid < kHT ? hj : 0) + hq * kEr;
     const uint32_t re_s = (uint32_t)__cvta_generic_to_shared(mye);
-    int next = z0;
-    // copies for the plane-iterations next, next + 1 into ring slots sl, sl + 1
+    const int hvi = hv ? 1 : 0;
+    // copies for the plane-iterations j, j + 1 (planes j+1, j+2 of the own
+    // pair, planes j, j+1 of the halo ring) into ring slots sl, sl + 1. The
+    // hot steps' copies all lie below z1 (j = k + 2 with k + 4 < z1): no
+    // bounds to test, only whether the lane has a halo slot.
     auto copy_c = [&](auto sl_c) {  // sl a compile-time constant
         constexpr int sl = decltype(sl_c)::value;
-        cp_async_if_off<16, sl * kRowC>(rc_s, osrc, next < olim);
-        cp_async_if_off<16, (sl + 1) * kRowC>(rc_s, osrc + plane, next + 1 < olim);
+        cp_async_off<16, sl * kRowC>(rc_s, osrc);
+        cp_async_off<16, (sl + 1) * kRowC>(rc_s, osrc + oplane);
         if (halo_warp) {
             if constexpr (kSplit) {
-                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, next + hq < hlim);
+                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, hvi);
             } else {
-                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, next < hlim);
-                cp_async_if_off<sizeof(T), (sl + 1) * kRowE>(re_s, hsrc + hstr, next + 1 < hlim);
+                cp_async_if_off<sizeof(T), sl * kRowE>(re_s, hsrc, hvi);
+                cp_async_if_off<sizeof(T), (sl + 1) * kRowE>(re_s, hsrc + hstr, hvi);
             }
             hsrc += 2 * hstr;
         }
         cp_async_commit();
-        osrc += 2 * plane;
-        next += 2;
+        osrc += 2 * oplane;
     };
-    auto copy_r = [&](int sl) {  // sl known at run time
-        cp_async_if<16>(rc_s + sl * kRowC, osrc, next < olim);
-        cp_async_if<16>(rc_s + (sl + 1) * kRowC, osrc + plane, next + 1 < olim);
+    auto copy_r = [&](int sl, int j) {  // sl known at run time; j may reach z1
+        cp_async_if<16>(rc_s + sl * kRowC, osrc, j < olim);
+        cp_async_if<16>(rc_s + (sl + 1) * kRowC, osrc + oplane, j + 1 < olim);
         if (halo_warp) {
             if constexpr (kSplit) {
-                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next + hq < hlim);
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, j + hq < hlim);
             } else {
-                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, next < hlim);
-                cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, next + 1 < hlim);
+                cp_async_if<sizeof(T)>(re_s + sl * kRowE, hsrc, j < hlim);
+                cp_async_if<sizeof(T)>(re_s + (sl + 1) * kRowE, hsrc + hstr, j + 1 < hlim);
             }
             hsrc += 2 * hstr;
         }
         cp_async_commit();
-        osrc += 2 * plane;
-        next += 2;
+        osrc += 2 * oplane;
     };
-    copy_c(std::integral_constant<int, 0>{});
+    copy_r(0, z0);
     __syncthreads();  // slow->n = 0 visible before any append
 
     // the current step's two new own planes (k+1, k+2) as frame integers
@@ -1389,7 +1401,7 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         uint64_t* const n1 = n0 + kPlane;
         bool fall = true;
         if (!resume) {
-            copy_r(S == 0 ? 2 : 0);
+            copy_r(S == 0 ? 2 : 0, k + 2);
             cp_async_wait<1>();
             const double2 zh = *(const double2*)(rc + (RD * kN + tid) * 2);
             const double2 v0 = zfirst ? zh : *(const double2*)(rc + (S * kN + tid) * 2);
