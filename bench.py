@@ -67,6 +67,10 @@ def parse():
     p.add_argument("--requests", type=int, default=120, help="serve workload: requests in the trace")
     p.add_argument("--rate", type=float, default=200.0, help="serve workload: mean arrivals per second")
     p.add_argument("--budget-gb", type=float, default=120.0, help="serve workload: HBM budget")
+    p.add_argument("--plain-prefix", type=int, default=6,
+                   help="serve workload: requests of the trace's start run for real in the plain form")
+    p.add_argument("--no-extras", action="store_true",
+                   help="grid workload: skip the compact f32, serve and 64^3 results added to its line")
     return p.parse_args()
 
 
@@ -365,34 +369,61 @@ def run_ours(a, rank, world, local, pg):
         e2e = None
         if not a.no_e2e:
             e2e_steps = max(1, min(a.steps, 3))
-            parts = np.zeros(3)  # host seconds: write (copy in, check, scatter), iterate + residual, read
+            parts = []  # host seconds per step: write (copy in, check, scatter), iterate + residual, read
+
+            def host_write():
+                if a.dtype == "f32":
+                    _lib.jac_write_f32(J.h, host_in.numpy())
+                else:
+                    _lib.jac_write(J.h, host_in.numpy())
+
+            def host_read():
+                if a.dtype == "f32":
+                    _lib.jac_read_f32(J.h, host_out.numpy())
+                else:
+                    _lib.jac_read(J.h, host_out.numpy())
+
+            # set-up, as a caller would do it once: the library's staging
+            # buffer for host copies is allocated by the first host write
+            host_write()
+            host_read()
+            nbytes = ncell * np.dtype(np_dt).itemsize
+            # the link's own rate for the same pinned buffers (a plain copy)
+            dev_tmp = torch.empty_like(dev_u0)
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
+            dev_tmp.copy_(host_in, non_blocking=True)
+            torch.cuda.synchronize()
+            tc1 = time.perf_counter()
+            host_out.copy_(dev_tmp, non_blocking=True)
+            torch.cuda.synchronize()
+            tc2 = time.perf_counter()
+            del dev_tmp
             barrier(pg)
             torch.cuda.synchronize()
             with ClockSampler(local) as e2e_clk:
                 t0 = time.perf_counter()
                 for _ in range(e2e_steps):
                     t = time.perf_counter()
-                    if a.dtype == "f32":
-                        _lib.jac_write_f32(J.h, host_in.numpy())
-                    else:
-                        _lib.jac_write(J.h, host_in.numpy())
+                    host_write()
                     t1 = time.perf_counter()
                     J.iterate(a.iters)
                     r = J.residual()
                     t2 = time.perf_counter()
-                    if a.dtype == "f32":
-                        _lib.jac_read_f32(J.h, host_out.numpy())
-                    else:
-                        _lib.jac_read(J.h, host_out.numpy())
-                    parts += (t1 - t, t2 - t1, time.perf_counter() - t2)
+                    host_read()
+                    parts.append((t1 - t, t2 - t1, time.perf_counter() - t2))
                 torch.cuda.synchronize()
                 e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
-            nbytes = ncell * np.dtype(np_dt).itemsize
+            tot = np.sum(np.array(parts), axis=0)
             e2e = {"value": world * ncell * a.iters * e2e_steps / e2e_wall, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
                    "residual": r,
                    "ms_per_step": {k: round(1e3 * v / e2e_steps, 2)
-                                   for k, v in zip(("write", "iterate_and_residual", "read"), parts)},
+                                   for k, v in zip(("write", "iterate_and_residual", "read"), tot)},
+                   "write_read_ms_each_step": [[round(1e3 * w, 2), round(1e3 * rd, 2)] for w, _, rd in parts],
+                   "host_buffers_pinned": bool(host_in.is_pinned() and host_out.is_pinned()),
+                   "plain_copy_gb_per_s": {"h2d": round(nbytes / (tc1 - tc) / 1e9, 1),
+                                           "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)},
                    "clocks": e2e_clk.summary()}
 
         # ---- other issue forms on the same grid (fewer iterations)
@@ -459,7 +490,69 @@ def run_ours(a, rank, world, local, pg):
     }
     if forms is not None:
         line["forms"] = forms
+    if world == 1 and not a.no_extras:
+        line.update(extras(a, rank, world, local, pg))
     print(json.dumps(line), flush=True)
+
+
+def extras(a, rank, world, local, pg):
+    """Compact results of the benchmark's other workloads, on one GPU, each
+    with its own small step count, so one default run reports all of them:
+    the binary32 grid (1024^3, 2000 iterations, binary64 residual every 50),
+    the serving trace, and the plain 64^3 one-block grid."""
+    import copy
+
+    out = {}
+    b = copy.copy(a)
+    b.grid, b.steps, b.warmup, b.mode, b.tile_w = [1024, 1024, 1024], 1, 1, "auto", 0
+    f = run_f32(b, rank, world, local, pg, emit=False)
+    out["f32"] = {"workload": f["config"]["workload"], "value": f["value"], "unit": UNIT, "steps": 1,
+                  "ms_per_step": f["ms_per_step"], "roofline_frac": f["roofline"]["frac"],
+                  "step_hbm_frac": f["step_hbm_frac"], "launch_ms_mean": f["roofline"]["launch_ms_mean"],
+                  "error_vs_f64": f["error_vs_f64"], "speedup_vs_f64": f["speedup_vs_f64"],
+                  "residual_f64_every": f["residual_f64_every"], "clocks": f["clocks"]}
+    c = copy.copy(a)
+    sv = run_serve(c, rank, world, local, pg, emit=False)
+    out["serve"] = {k: sv[k] for k in ("config", "specified_rate", "sustainable_rate", "plain_form_prefix",
+                                       "plain_form_fifo")}
+    out["configs0"] = run_configs0(local)
+    return out
+
+
+def run_configs0(local):
+    """The plain grid: 64^3 binary64, one block (no overdecomposition), 100
+    iterations of the correctly rounded mean, per issue form. Its 4.2 MB
+    working set stays in L2, so it is launch- and latency-bound and no HBM
+    fraction applies."""
+    import torch
+
+    import synth
+    from paper_2202_11819_gb300 import Jacobi3D
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    dims, iters, reps = (64, 64, 64), 100, 10
+    ncell = dims[0] * dims[1] * dims[2]
+    dev = torch.from_numpy(synth.grid_uniform01(0, *dims).reshape(-1)).to(f"cuda:{local}")
+    res = {"workload": "Jacobi3D 64x64x64 F64, one block, 100 iterations, correctly rounded mean",
+           "hbm_frac": "n/a (the 4.2 MB working set is L2-resident)"}
+    with torch.cuda.stream(stream):
+        for mode in ("persistent", "graph_fused", "fused", "graph", "unfused"):
+            with Jacobi3D(dims, dims, bc=synth.DIRICHLET_X0, stream=stream.cuda_stream, mode=mode) as J:
+                J.write_device(dev)
+                J.iterate(iters)  # builds graphs, streams and the persistent grid outside the timing
+                J.sync()
+                ms = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    J.iterate(iters)
+                    e1.record(stream)
+                    stream.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                m = statistics.median(ms)
+                res[mode] = {"ms_per_100_iterations": round(m, 4), "cell_updates_per_s": ncell * iters / (m / 1e3)}
+    return res
 
 
 def run_batch(a, rank, world, local, pg):
@@ -559,7 +652,7 @@ def run_batch(a, rank, world, local, pg):
     print(json.dumps(line), flush=True)
 
 
-def run_f32(a, rank, world, local, pg):
+def run_f32(a, rank, world, local, pg, emit=True):
     """Precision workload: a binary32 grid (default 1024^3 in 64^3 blocks)
     iterated a.f32_iters times per step with the binary64 residual every
     a.residual_every iterations; afterwards the same grid is run in binary64
@@ -639,7 +732,7 @@ def run_f32(a, rank, world, local, pg):
         rel_l2 = float(diff.norm() / out64.norm())
     wall = max_over_ranks(pg, wall)
     if rank != 0:
-        return
+        return None
     value = world * ncell * a.f32_iters * a.steps / wall
     bound = a.f32_iters * (27.0 / 7.0 + 1.0) * 2.0 ** -24 + 2.0 ** -25
     peak, kind = measured_peaks()
@@ -676,7 +769,9 @@ def run_f32(a, rank, world, local, pg):
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def replay(srv_lib, trace, inits, rate_scale, budget, chunk, tol=1e-6, cap=3000):
@@ -734,7 +829,39 @@ def pctl(xs, q):
     return xs[k]
 
 
-def run_serve(a, rank, world, local, pg):
+def plain_prefix(trace, inits, k, tol=1e-6, cap=3000, chunk=50):
+    """The plain form as a server, run for real on the first k requests of
+    the trace at their arrival times: one request at a time, first come
+    first served, each a binary64 grid in per-block launches on per-block
+    streams (blocks of at most 64^3, the left-to-right rule), iterated in
+    chunks with a residual check until below tol or at the cap. Earlier
+    requests never wait for later ones, so the first k latencies are those
+    of the whole trace. Returns per-request latencies and iterations."""
+    from paper_2202_11819_gb300 import Jacobi3D
+
+    order = sorted(range(k), key=lambda i: trace[i].arrival_s)
+    t0 = time.perf_counter()
+    lat, its = {}, {}
+    for i in order:
+        r = trace[i]
+        wait = r.arrival_s - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        blk = tuple(min(64, v) for v in r.dims)
+        n = 0
+        with Jacobi3D(r.dims, blk, dtype="f64", bc=DIRICHLET, mode="unfused", arith="seq") as J:
+            J.write(inits[i])
+            while n < cap:
+                J.iterate(chunk)
+                n += chunk
+                if J.residual() < tol:
+                    break
+        lat[i] = time.perf_counter() - t0 - r.arrival_s
+        its[i] = n
+    return lat, its
+
+
+def run_serve(a, rank, world, local, pg, emit=True):
     """Serving workload: a seeded Poisson trace of solve requests (mean
     a.rate per second), each axis log-uniform in [32, 384], binary32 or
     binary64 with probability 1/2, each iterated until its binary64 residual
@@ -790,8 +917,13 @@ def run_serve(a, rank, world, local, pg):
 
     plain = fifo(1.0)
     plain2 = fifo(scale)
+    # the same prefix of the trace through our server and through the plain
+    # form, both run for real at the specified rate
+    kp = max(1, min(a.plain_prefix, len(trace)))
+    latp, _, _, _, _ = replay(_lib, trace[:kp], inits[:kp], 1.0, budget, chunk)
+    plat, pits = plain_prefix(trace, inits, kp)
     if rank != 0:
-        return
+        return None
     lv, lv2 = list(lat.values()), list(lat2.values())
     line = {
         "metric": "serve p50/p99 latency and cell-updates/s", "value": thr, "unit": UNIT, "n_gpus": world,
@@ -804,13 +936,26 @@ def run_serve(a, rank, world, local, pg):
                            "converged": sum(1 for i in iters if iters[i] < 3000)},
         "sustainable_rate": {"rate_per_s": a.rate * scale, "p50_s": pctl(lv2, 50), "p99_s": pctl(lv2, 99),
                              "cell_updates_per_s": updates2 / makespan2, "makespan_s": makespan2},
-        "plain_form_fifo": {"note": "binary64 per-block launches, one request at a time; measured per-iteration "
-                                    "time per shape x iterations, FIFO replay of the same arrivals",
+        "plain_form_prefix": {"note": f"the first {kp} requests of the trace at the specified rate, run for real "
+                                      "through this server and through the plain form (binary64 per-block "
+                                      "launches, one request at a time, first come first served)",
+                              "requests": kp,
+                              "ours": {"p50_s": pctl(list(latp.values()), 50), "p99_s": pctl(list(latp.values()), 99)},
+                              "plain": {"p50_s": pctl(list(plat.values()), 50), "p99_s": pctl(list(plat.values()), 99),
+                                        "iterations": [pits[i] for i in sorted(pits)]}},
+        "plain_form_fifo": {"note": "model: binary64 per-block launches, one request at a time; measured "
+                                    "per-iteration time per shape x iterations, FIFO replay of the same arrivals",
                             "specified_rate": {"p50_s": pctl(plain, 50), "p99_s": pctl(plain, 99)},
                             "sustainable_rate": {"p50_s": pctl(plain2, 50), "p99_s": pctl(plain2, 99)},
                             "cell_updates_per_s": updates / sum(svc)},
     }
-    print(json.dumps(line), flush=True)
+    line["config"]["trace_length_note"] = (
+        f"{len(trace)} of the 2000 requests the workload specifies: at the specified rate the offered load is "
+        "about 2.5x the capacity, so replaying all 2000 would take minutes per rate; run --workload serve "
+        "--requests 2000 for the full trace")
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
 def main():

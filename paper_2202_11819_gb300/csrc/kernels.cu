@@ -2264,6 +2264,23 @@ __global__ void k_pack6(const T* pool, const BlockDesc* desc, int b, int p, T* s
     }
 }
 
+// The exchange of one block's six packed faces (Fig. 1(b)): face f of block
+// b, packed at send_off[b][f] of the halo buffer, is copied to the receive
+// segment of the neighbour's opposite face, recv_off[n][f ^ 1]. One thread
+// per cell of the block's largest face, visiting the six faces in turn.
+template <typename T>
+__global__ void k_exchange6(const BlockDesc* desc, int b, T* halo, const int64_t* send_off, const int64_t* recv_off)
+{
+    const BlockDesc& d = desc[b];
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+        const int n = d.nbr[f];
+        if (n < 0 || q >= face_size(d, f)) continue;
+        halo[recv_off[(int64_t)n * 6 + opposite_face(f)] + q] = halo[send_off[(int64_t)b * 6 + f] + q];
+    }
+}
+
 template <typename T>
 __global__ void k_unpack6(T* pool, const BlockDesc* desc, int b, int p, const T* recv, const int64_t* faceoff)
 {
@@ -2572,6 +2589,15 @@ cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void*
     const int th = 128, g = (maxface + th - 1) / th;
     if (dtype_f32) k_pack6<float><<<g, th, 0, s>>>((const float*)a.pool, a.desc, b, p, (float*)send, faceoff);
     else k_pack6<double><<<g, th, 0, s>>>((const double*)a.pool, a.desc, b, p, (double*)send, faceoff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exchange6(const LaunchArgs& a, int dtype_f32, int b, void* halo, const int64_t* send_off,
+                             const int64_t* recv_off, int maxface, cudaStream_t s)
+{
+    const int th = 128, g = (maxface + th - 1) / th;
+    if (dtype_f32) k_exchange6<float><<<g, th, 0, s>>>(a.desc, b, (float*)halo, send_off, recv_off);
+    else k_exchange6<double><<<g, th, 0, s>>>(a.desc, b, (double*)halo, send_off, recv_off);
     return cudaGetLastError();
 }
 

@@ -63,6 +63,10 @@ cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void*
                          int maxface, cudaStream_t s);
 cudaError_t launch_unpack6(const LaunchArgs& a, int dtype_f32, int b, int p, const void* recv, const int64_t* faceoff,
                            int maxface, cudaStream_t s);
+// the six-face exchange of block b: its packed faces into the neighbours'
+// receive segments of the same halo buffer
+cudaError_t launch_exchange6(const LaunchArgs& a, int dtype_f32, int b, void* halo, const int64_t* send_off,
+                             const int64_t* recv_off, int maxface, cudaStream_t s);
 cudaError_t launch_scatter(const LaunchArgs& a, int dtype_f32, int src_f32, const void* dense, int b0, int nb,
                            int64_t dense_base, int p, cudaStream_t s);
 cudaError_t launch_gather(const LaunchArgs& a, int dtype_f32, int dst_f32, void* dense, int b0, int nb,

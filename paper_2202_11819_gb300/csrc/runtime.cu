@@ -704,14 +704,24 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
                 h->launches += 1;
             }
         }
-        for (int f = 0; f < 6; ++f) {
-            const int n = d.nbr[f];
-            if (n < 0) continue;
-            if (!capture) CU(cudaStreamWaitEvent(s, E.unpacked[n], 0), "wait unpacked");
-            CU(cudaMemcpyAsync(send + h->recv_off[(int64_t)n * 6 + opposite_face(f)] * es,
-                               send + h->send_off[b * 6 + f] * es, (size_t)h->fsize[b * 6 + f] * es,
-                               cudaMemcpyDeviceToDevice, s),
-               "halo copy");
+        if (six) {
+            // the captured form: one exchange kernel per block instead of a
+            // copy node per face (a graph launch holds one iteration, so no
+            // neighbour's unpack of an earlier iteration can still be reading)
+            if (h->maxface[b] > 0) {
+                CU(launch_exchange6(a, f32, (int)b, send, dsend, drecv, h->maxface[b], s), "exchange6");
+                h->launches += 1;
+            }
+        } else {
+            for (int f = 0; f < 6; ++f) {
+                const int n = d.nbr[f];
+                if (n < 0) continue;
+                CU(cudaStreamWaitEvent(s, E.unpacked[n], 0), "wait unpacked");
+                CU(cudaMemcpyAsync(send + h->recv_off[(int64_t)n * 6 + opposite_face(f)] * es,
+                                   send + h->send_off[b * 6 + f] * es, (size_t)h->fsize[b * 6 + f] * es,
+                                   cudaMemcpyDeviceToDevice, s),
+                   "halo copy");
+            }
         }
         CU(cudaEventRecord(E.sent[b], s), "record sent");
     }
@@ -787,12 +797,12 @@ int ensure_graph(jac_ctx* h, int p)
     return JAC_OK;
 }
 
-// kernels per graph launch of the unfused flow (its six-face form: pack6
-// and unpack6 for a block with a neighbour, then the update)
+// kernels per graph launch of the unfused flow (its six-face form: pack6,
+// exchange6 and unpack6 for a block with a neighbour, then the update)
 int64_t unfused_kernels(const jac_ctx* h)
 {
     int64_t n = 0;
-    for (size_t b = 0; b < h->hdesc.size(); ++b) n += 1 + (h->maxface[b] > 0 ? 2 : 0);
+    for (size_t b = 0; b < h->hdesc.size(); ++b) n += 1 + (h->maxface[b] > 0 ? 3 : 0);
     return n;
 }
 
