@@ -39,6 +39,7 @@ struct BlockDesc {
     int64_t dense;    // start of the instance's interior in dense x-fastest arrays
     int32_t gdim[3];  // the instance's global dims
     int32_t ntiles;   // work units (tiles) of this block
+    int32_t u0;       // index of the block's first work unit (its units are contiguous)
     double bc[6];     // Dirichlet value per face (used where nbr[f] < 0)
     float bcf[6];     // the same rounded to binary32 (binary32 grids)
     int32_t pad;

@@ -1173,9 +1173,13 @@ __device__ __forceinline__ HaloSlot<double> halo_slot_pair(const double* pool, c
 // After the tile's loop: the cells recorded in the slow list (or, when it
 // overflowed, every cell of the tile) with the exact per-cell routine.
 // Slow-list entries of the two-column engine: (k << 10) | (tid << 1) | cell.
+// The exponent field of |v|.
+__device__ __forceinline__ int exp_field(double v) { return (int)((dbits(v) >> 52) & 0x7FFull); }
+
 template <bool PULL, bool CG, int TW>
 __device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* desc, const BlockDesc& d, int b, int p,
-                                              int x0, int y0, int z0, int z1, bool k1, int x, int y, SlowList* slow)
+                                              int x0, int y0, int z0, int z1, bool k1, int x, int y, SlowList* slow,
+                                              int eref, int& lzm)
 {
     constexpr int kTP = TW / 2;
     __syncthreads();
@@ -1187,13 +1191,17 @@ __device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* des
             const uint32_t c = slow->cell[i];
             const int kk = (int)(c >> 10), t = (int)((c >> 1) & 511u), cell = (int)(c & 1u);
             const int cx = x0 + 2 * (t % kTP) + cell, cy = y0 + t / kTP;
-            pool[cell_index<double>(d, p ^ 1, cx, cy, kk)] = exact_cell<double, PULL, CG, false>(pool, desc, b, p, cx, cy, kk);
+            const double v = exact_cell<double, PULL, CG, false>(pool, desc, b, p, cx, cy, kk);
+            pool[cell_index<double>(d, p ^ 1, cx, cy, kk)] = v;
+            lzm = min(lzm, eref - exp_field(v));
         }
     } else if (k1) {
         for (int kk = z0; kk < z1; ++kk)
-            for (int cell = 0; cell < 2; ++cell)
-                pool[cell_index<double>(d, p ^ 1, x + cell, y, kk)] =
-                    exact_cell<double, PULL, CG, false>(pool, desc, b, p, x + cell, y, kk);
+            for (int cell = 0; cell < 2; ++cell) {
+                const double v = exact_cell<double, PULL, CG, false>(pool, desc, b, p, x + cell, y, kk);
+                pool[cell_index<double>(d, p ^ 1, x + cell, y, kk)] = v;
+                lzm = min(lzm, eref - exp_field(v));
+            }
     }
 }
 
@@ -1207,10 +1215,18 @@ __device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* des
 // tile, the step after a fallback) falls back to the 96-bit frame itself. The
 // 96-bit path thus stays out of the hot loop, whose registers it would
 // otherwise take.
+// Unit exponent bounds (uin, uout; null: the grid's frame only): uin holds,
+// per work unit, an upper bound on the exponent field of the values that
+// unit wrote into the buffer read now (all ones where unknown); the tile's
+// frame is taken from the largest bound over the units of its block and of
+// its six neighbours (the only blocks whose values it reads) and the
+// block's Dirichlet values, and never above the grid's frame. At its end the
+// tile stores the bound of its own outputs in *uout. The frame only scales
+// the integers, so the results do not depend on it.
 template <bool PULL, bool CG, int TW>
 __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* __restrict__ desc,
                                     const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
-                                    unsigned char* smraw, SlowList* slow)
+                                    unsigned char* smraw, SlowList* slow, const uint32_t* uin, uint32_t* uout)
 {
     using T = double;
     using W = frame::W96;
@@ -1226,10 +1242,24 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     T* const re = rc + (RD + 1) * 2 * kN;                   // [RD][kEr]
     const BlockDesc& d = desc[b];
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
-    const int eref = frame_e[d.inst] + 1;
-    const bool nok = eref >= 13;  // else every step takes the 96-bit frame
-    const uint32_t elo = nframe::elo_hi(eref), nscale = nframe::scale_hi(eref);
     const int tid = threadIdx.x, tp = tid % kTP, ty = tid / kTP;
+    __shared__ uint32_t s_red[kN / 32];
+    if (uin) {
+        // the largest exponent bound of the blocks this tile reads
+        uint32_t emax = 0u;
+        for (int j = 0; j < 7; ++j) {
+            const int nb = j == 0 ? b : d.nbr[j - 1];
+            if (nb < 0) {
+                if (tid == 0) emax = max(emax, (uint32_t)exp_field(d.bc[j - 1]));
+                continue;
+            }
+            const BlockDesc& n = desc[nb];
+            const int u0 = n.u0, nt = n.ntiles;
+            for (int i = tid; i < nt; i += kN) emax = max(emax, __ldcg(uin + u0 + i));
+        }
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if ((tid & 31) == 0) s_red[tid >> 5] = emax;
+    }
     const int x = x0 + 2 * tp, y = y0 + ty;
     const int plane = (int)d.plane;  // below 2^31 elements for every block shape the runtime makes
     if (tid == 0) slow->n = 0;
@@ -1246,6 +1276,7 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     uint64_t zmA = 0u, zmB = 0u, cA = 0u, cB = 0u;
     bool gzm = true, gc = true;
     const uint32_t rz_s = (uint32_t)__cvta_generic_to_shared(rc + 2 * (RD * kN + tid));
+    double2 zl = make_double2(0.0, 0.0), c00 = make_double2(0.0, 0.0);  // planes z0 - 1, z0 (converted below)
     if (k1) {
         const T* col = pool + cell_index<T>(d, p, x, y, 0);
         osrc = col + (int64_t)(z0 + 1) * plane;
@@ -1253,16 +1284,8 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         out = pool + cell_index<T>(d, p ^ 1, x, y, z0);
         cp_async_if<16>(rz_s, z1 == bz ? z_pair_source<PULL>(pool, desc, d, p, x, y, 5) : col + (int64_t)z1 * plane,
                         true);
-        const double2 zl = ld_pair<CG>(z0 == 0 ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4)
-                                               : col + (int64_t)(z0 - 1) * plane);
-        const double2 c0 = ld_pair<CG>(col + (int64_t)z0 * plane);
-        bool g1, g2;
-        zmA = nframe::of0(zl.x, elo, g1);
-        zmB = nframe::of0(zl.y, elo, g2);
-        gzm = g1 && g2;
-        cA = nframe::of(c0.x, elo, g1);
-        cB = nframe::of(c0.y, elo, g2);
-        gc = g1 && g2;
+        zl = ld_pair<CG>(z0 == 0 ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4) : col + (int64_t)(z0 - 1) * plane);
+        c00 = ld_pair<CG>(col + (int64_t)z0 * plane);
     }
     constexpr bool kSplit = 2 * kEr <= kN;
     constexpr int kHT = kSplit ? 2 * kEr : kEr;
@@ -1318,7 +1341,26 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         osrc += 2 * oplane;
     };
     copy_r(0, z0);
-    __syncthreads();  // slow->n = 0 visible before any append
+    __syncthreads();  // slow->n = 0 visible before any append; the warps' exponent bounds
+    int eref = frame_e[d.inst] + 1;
+    if (uin) {
+        uint32_t emax = 0u;
+#pragma unroll
+        for (int w = 0; w < kN / 32; ++w) emax = max(emax, s_red[w]);
+        if (emax < 2047u) eref = min(eref, (int)emax + 1);
+    }
+    const bool nok = eref >= 13;  // else every step takes the 96-bit frame
+    const uint32_t elo = nframe::elo_hi(eref), nscale = nframe::scale_hi(eref);
+    int lzm = 64;  // the least leading-zero count of this thread's sums: its results' fields are <= eref - lzm
+    if (k1) {
+        bool g1, g2;
+        zmA = nframe::of0(zl.x, elo, g1);
+        zmB = nframe::of0(zl.y, elo, g2);
+        gzm = g1 && g2;
+        cA = nframe::of(c00.x, elo, g1);
+        cB = nframe::of(c00.y, elo, g2);
+        gc = g1 && g2;
+    }
 
     // the current step's two new own planes (k+1, k+2) as frame integers
     uint64_t c0A = 0u, c0B = 0u, c1A = 0u, c1B = 0u;
@@ -1331,14 +1373,20 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
             const uint64_t SA = uA + cB + n0[own - 1] + ym.x + yp.x + zmA;
             const uint64_t SB = uB + cA + n0[own + 2] + ym.y + yp.y + zmB;
             const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
-            if (k1) *(double2*)out = o;
+            if (k1) {
+                *(double2*)out = o;
+                lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+            }
         }
         if (two) {
             const ulonglong2 ym = *(const ulonglong2*)(n1 + own - kSW), yp = *(const ulonglong2*)(n1 + own + kSW);
             const uint64_t SA = uA + c0B + n1[own - 1] + ym.x + yp.x + c1A;
             const uint64_t SB = uB + c0A + n1[own + 2] + ym.y + yp.y + c1B;
             const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
-            if (k1) *(double2*)(out + plane) = o;
+            if (k1) {
+                *(double2*)(out + plane) = o;
+                lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+            }
         }
     };
     auto advance = [&](bool two) {
@@ -1489,6 +1537,7 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
                 frame::sum7(c, xm, xp, ym, yp, zm, zp, a0, a1, a2);
                 if (frame::mean7_of_sum(a0, a1, a2, eref, v)) {
                     *o = v;
+                    lzm = min(lzm, eref - exp_field(v));
                 } else {
                     const int i = atomicAdd(&slow->n, 1);
                     if (i < kSlowMax) slow->cell[i] = ((uint32_t)kk << 10) | ((uint32_t)tid << 1) | (uint32_t)cell;
@@ -1533,7 +1582,19 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         if (k >= z1) break;
     }
     cp_async_wait<0>();
-    n2_slow_cells<PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, slow);
+    n2_slow_cells<PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, slow, eref, lzm);
+    if (uout) {
+        // every output's exponent field is at most eref - (the tile's least count)
+        const int w = __reduce_min_sync(0xffffffffu, lzm);
+        if ((tid & 31) == 0) s_red[tid >> 5] = (uint32_t)w;
+        __syncthreads();
+        if (tid == 0) {
+            int m = 64;
+#pragma unroll
+            for (int i = 0; i < kN / 32; ++i) m = min(m, (int)s_red[i]);
+            *uout = (uint32_t)max(0, eref - m);
+        }
+    }
 }
 
 // One binary64 work unit (TW x 512/TW columns) of the exact mean: the
@@ -1541,11 +1602,13 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
 // engine on the unit's two halves.
 template <bool PULL, bool CG, int TW>
 __device__ __forceinline__ void exact_unit(double* pool, const BlockDesc* desc, const int32_t* frame_e, int b, int p,
-                                           int x0, int y0, int z0, int z1, SlowList* slow)
+                                           int x0, int y0, int z0, int z1, SlowList* slow, const uint32_t* uin,
+                                           uint32_t* uout)
 {
     if ((desc[b].ext[0] & 1) == 0) {
-        tile_engine_narrow2<PULL, CG, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow);
+        tile_engine_narrow2<PULL, CG, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow, uin, uout);
     } else {
+        // (the single-column form keeps the grid's frame; its units' bounds stay unknown)
         tile_engine_narrow<PULL, CG, kRing<double>, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow);
         const int y1 = y0 + kNT<double> / TW;
         if (y1 < desc[b].ext[1]) {
@@ -2013,7 +2076,7 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
     __shared__ SlowList slow;
     if constexpr (OP == OP_EXACT)
         exact_unit<false, false, TW>(pool, desc, frame_e, b, p, blockIdx.x * TW, blockIdx.y * (2 * kNT<T> / TW), 0,
-                                     desc[b].ext[2], &slow);
+                                     desc[b].ext[2], &slow, nullptr, nullptr);
     else
         tile_engine<T, OP, false, false, kRing<T>, TW>(pool, desc, b, p, blockIdx.x * TW, blockIdx.y * (kNT<T> / TW),
                                                        0, desc[b].ext[2], jac_dyn_sm);
@@ -2021,14 +2084,15 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
 
 template <typename T, int OP>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
-                                                            const TileUnit* units, int p)
+                                                            const TileUnit* units, int p, uint32_t* uexp, int ucap)
 {
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
         if constexpr (OP == OP_EXACT)
-            exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
+            exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow,
+                                        uexp + (int64_t)p * ucap, uexp + (int64_t)(p ^ 1) * ucap + blockIdx.x);
         else
             seq_unit<true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
     });
@@ -2067,7 +2131,7 @@ template <typename T, int OP, bool RING>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
-                 int hold_block, int64_t hold_after)
+                 int hold_block, int64_t hold_after, uint32_t* uexp, int ucap)
 {
     __shared__ SlowList slow;
     __shared__ long long s_next;
@@ -2120,7 +2184,9 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
                 // barrier above order them after the neighbours' releases
                 f32_unit<true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             } else if constexpr (OP == OP_EXACT) {
-                exact_unit<true, true, TW>(pool, desc, frame_e, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1, &slow);
+                const int pt = (p0 + t) & 1;
+                exact_unit<true, true, TW>(pool, desc, frame_e, u.block, pt, u.x0, u.y0, u.z0, u.z1, &slow,
+                                           uexp + (int64_t)pt * ucap, uexp + (int64_t)(pt ^ 1) * ucap + w % nunits);
             } else {
                 seq_unit<true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             }
@@ -2458,10 +2524,10 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
         k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
         k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap);
     else
         k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap);
     return cudaGetLastError();
 }
 
@@ -2524,15 +2590,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
     if (dtype_f32)
         k_persistent<float, OP_SEQ, true><<<ctas, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap);
     else if (arith == 1)
         k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap);
     else
         k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,9 @@ struct LaunchArgs {
     const BlockDesc* desc;   // device block table
     const TileUnit* units;   // device tile table
     int32_t* frame;          // per instance: largest exponent field (grid frame)
+    uint32_t* uexp;          // [2][units_cap]: per buffer parity and work unit, a bound on the
+                             // exponent field of the unit's values there (all ones: unknown)
+    int units_cap;
     int nblocks;
     int nunits;
     int tile_w;              // tile width of the update engine: 16, 32 or 64

@@ -228,6 +228,7 @@ struct jac_ctx {
 
     // residual and I/O staging
     double* partials = nullptr;
+    uint32_t* uexp = nullptr;  // [2][partials_cap] unit exponent bounds (see LaunchArgs)
     double* dres = nullptr;
     void* dense = nullptr;
     size_t dense_bytes = 0;
@@ -239,6 +240,8 @@ struct jac_ctx {
         a.desc = ddesc;
         a.units = dunits;
         a.frame = frame;
+        a.uexp = uexp;
+        a.units_cap = (int)partials_cap;
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
         a.tile_w = tile_w;
@@ -342,6 +345,16 @@ int class_tile_width(const jac_ctx* h, int32_t bx)
     return h->tile_w;
 }
 
+// Mark every unit's exponent bound unknown (all ones), so the next
+// iteration of the exact mean takes the grid's frame: after anything that
+// changes the grids other than the kernels that maintain the bounds.
+int forget_unit_frames(jac_ctx* h)
+{
+    if (h->uexp && h->partials_cap)
+        CU(cudaMemsetAsync(h->uexp, 0xFF, 2 * h->partials_cap * sizeof(uint32_t), h->stream), "forget unit frames");
+    return JAC_OK;
+}
+
 int build_units(jac_ctx* h)
 {
     const int64_t nblocks = (int64_t)h->hdesc.size();
@@ -428,12 +441,19 @@ int build_units(jac_ctx* h)
         }
     }
     seg.push_back((int32_t)h->hunits.size());
+    // each block's first unit (units of a block are contiguous)
+    for (int32_t b = 0; b < (int32_t)nblocks; ++b) h->hdesc[b].u0 = -1;
+    for (size_t i = 0; i < h->hunits.size(); ++i) {
+        BlockDesc& d = h->hdesc[h->hunits[i].block];
+        if (d.u0 < 0) d.u0 = (int32_t)i;
+    }
     int rc;
     const size_t need = std::max<size_t>(1, h->hunits.size());
     if (need > h->partials_cap) {
         // earlier, smaller tables stay allocated until the context is destroyed
         if ((rc = dev_alloc(h, need * sizeof(TileUnit), (void**)&h->dunits))) return rc;
         if ((rc = dev_alloc(h, need * sizeof(double), (void**)&h->partials))) return rc;
+        if ((rc = dev_alloc(h, 2 * need * sizeof(uint32_t), (void**)&h->uexp))) return rc;
         h->partials_cap = need;
     }
     if (nblocks > 0)
@@ -448,6 +468,9 @@ int build_units(jac_ctx* h)
     if (!slot.empty())
         CU(cudaMemcpyAsync(h->dslot, slot.data(), slot.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
            "copy slot map");
+    // the unit exponent bounds describe the old tables: unknown until the
+    // next exact-mean iteration writes them
+    if ((rc = forget_unit_frames(h))) return rc;
     // the host tables must stay valid until the copies above have run
     CU(cudaStreamSynchronize(h->stream), "table sync");
     h->pctas = 0;
@@ -896,6 +919,10 @@ int write_dense(jac_ctx* h, int i0, int i1, const void* src, size_t n, int src_f
                       h->stream),
        "scatter");
     h->launches += 1;
+    {
+        const int rcf = forget_unit_frames(h);
+        if (rcf) return rcf;
+    }
     if (i0 == h->first_active() && i1 == h->last_active() + 1) h->iters = 0;
     if (!src_on_device) CU(cudaStreamSynchronize(h->stream), "write sync");
     return JAC_OK;
@@ -1238,6 +1265,11 @@ int jac_iterate(jac_ctx* h, int64_t n)
     if (n < 0) return fail(JAC_EINVAL, "n_iters must be >= 0");
     if (n == 0 || h->hunits.empty()) return JAC_OK;
     const int f32 = h->dtype == JAC_F32;
+    // only the fused and persistent forms of the exact mean keep the unit
+    // exponent bounds; after any other iteration they are unknown
+    const bool keeps = !f32 && h->arith == JAC_ARITH_EXACT &&
+                       (h->mode == JAC_MODE_FUSED || h->mode == JAC_MODE_GRAPH_FUSED || h->mode == JAC_MODE_PERSISTENT);
+    if (!keeps && (rc = forget_unit_frames(h))) return rc;
     switch (h->mode) {
         case JAC_MODE_FUSED:
             for (int64_t i = 0; i < n; ++i) {
@@ -1584,6 +1616,7 @@ int jac_autotune(jac_ctx* h, int32_t trial_iters, jac_tune_t* result)
     h->parity = parity0;
     h->iters = iters0;
     if (rc) return rc;
+    if ((rc = forget_unit_frames(h))) return rc;  // the bounds describe the trials' data
     CU(cudaStreamSynchronize(h->stream), "autotune sync");
     if (result) *result = best;
     return JAC_OK;

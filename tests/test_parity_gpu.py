@@ -433,3 +433,35 @@ def test_last_wave_split_in_z_gives_the_oracle_result():
             seen[split] += 1
             assert np.array_equal(got, want), (dims, mode, split)
     assert seen[True] > 0 and seen[False] > 0, seen
+
+
+@pytest.mark.parametrize("mode", ["fused", "persistent", "graph_fused"])
+def test_per_tile_frames_on_blocks_of_very_different_magnitude(mode):
+    """Each tile of the exact mean takes its fixed-point frame from the
+    largest exponent among the values of its block and neighbours (written by
+    the previous iteration), not from the grid's largest value. Blocks whose
+    values lie many binades apart, a boundary value far above them, and a
+    mode change and a rewrite in the middle, against the oracle bit for bit."""
+    dims, block = (128, 128, 64), (32, 64, 32)
+    u0 = grid(41, dims)
+    # scale the eight blocks by 2^0, 2^-6, ..., 2^-42
+    for bk in range(2):
+        for bj in range(2):
+            for bi in range(4):
+                s = 2.0 ** (-6 * (bi + 4 * (bj + 2 * bk)))
+                u0[bk * 32:(bk + 1) * 32, bj * 64:(bj + 1) * 64, bi * 32:(bi + 1) * 32] *= s
+    bc = (2.0 ** 10, 0.0, 2.0 ** -30, 0.0, 1e-3, 0.5)
+    want = oracle.jacobi(u0, bc, 12, oracle.RULE_EXACT)
+    with Jacobi3D(dims, block, bc=bc, mode=mode) as J:
+        J.write(u0)
+        J.iterate(5)
+        J.set_mode("unfused")  # a form that does not keep the per-unit bounds
+        J.iterate(1)
+        J.set_mode(mode)
+        J.iterate(6)
+        got = J.read()
+        J.write(u0)  # the bounds of the old state must not survive a write
+        J.iterate(12)
+        got2 = J.read()
+    assert np.array_equal(got, want)
+    assert np.array_equal(got2, want)
