@@ -401,19 +401,21 @@ def run_ours(a, rank, world, local, pg):
             del dev_tmp
             barrier(pg)
             torch.cuda.synchronize()
-            with ClockSampler(local) as e2e_clk:
-                t0 = time.perf_counter()
-                for _ in range(e2e_steps):
-                    t = time.perf_counter()
-                    host_write()
-                    t1 = time.perf_counter()
-                    J.iterate(a.iters)
-                    r = J.residual()
-                    t2 = time.perf_counter()
-                    host_read()
-                    parts.append((t1 - t, t2 - t1, time.perf_counter() - t2))
-                torch.cuda.synchronize()
-                e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
+            # no clock sampler here: nvidia-smi's queries stall host copies by
+            # about 10 ms at random (measured on GB300: a plain pinned copy of
+            # 1 GiB takes 5.1-5.6 ms alone and 10-20 ms while nvidia-smi polls)
+            t0 = time.perf_counter()
+            for _ in range(e2e_steps):
+                t = time.perf_counter()
+                host_write()
+                t1 = time.perf_counter()
+                J.iterate(a.iters)
+                r = J.residual()
+                t2 = time.perf_counter()
+                host_read()
+                parts.append((t1 - t, t2 - t1, time.perf_counter() - t2))
+            torch.cuda.synchronize()
+            e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
             tot = np.sum(np.array(parts), axis=0)
             e2e = {"value": world * ncell * a.iters * e2e_steps / e2e_wall, "unit": UNIT,
                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
@@ -423,8 +425,7 @@ def run_ours(a, rank, world, local, pg):
                    "write_read_ms_each_step": [[round(1e3 * w, 2), round(1e3 * rd, 2)] for w, _, rd in parts],
                    "host_buffers_pinned": bool(host_in.is_pinned() and host_out.is_pinned()),
                    "plain_copy_gb_per_s": {"h2d": round(nbytes / (tc1 - tc) / 1e9, 1),
-                                           "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)},
-                   "clocks": e2e_clk.summary()}
+                                           "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)}}
 
         # ---- other issue forms on the same grid (fewer iterations)
         forms = None
