@@ -32,7 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-MODE_NAMES = {0: "unfused", 1: "fused", 2: "graph", 3: "persistent", 4: "graph_fused"}
+MODE_NAMES = {0: "unfused", 1: "fused", 2: "graph", 3: "persistent", 4: "graph_fused", 5: "split"}
 METRIC = "Jacobi3D cell-updates/s"
 UNIT = "cell-updates/s"
 BYTES_PER_UPDATE = {"f64": 16, "f32": 8}  # read + write of one cell at ideal neighbour reuse
@@ -431,7 +431,7 @@ def run_ours(a, rank, world, local, pg):
         forms = None
         if a.forms:
             forms = {}
-            for mode, n in (("unfused", 10), ("graph", 10), ("fused", 100), ("graph_fused", 100),
+            for mode, n in (("unfused", 10), ("split", 10), ("graph", 10), ("fused", 100), ("graph_fused", 100),
                             ("persistent", 100)):
                 J.set_mode(mode)
                 J.iterate(2)  # builds graphs / streams outside the timing

@@ -66,13 +66,22 @@ typedef enum { JAC_F64 = 0, JAC_F32 = 1 } jac_dtype;
  *             block waits only for its six neighbours to finish the previous
  *             iteration (per-block iteration counters, the device form of
  *             the reference numbers of Section II-A), with bounded waits.
- *  GRAPH_FUSED the FUSED kernel captured as two alternating graphs.       */
+ *  GRAPH_FUSED the FUSED kernel captured as two alternating graphs.
+ *  SPLIT      the UNFUSED flow with the manual overlap of Section II-A
+ *             (Fig. 1): per block the interior update (cells 1 .. b-2 on
+ *             every axis, which read no halo) runs on the low-priority
+ *             compute stream while the high-priority communication stream
+ *             packs, exchanges and unpacks the halos (the priorities of
+ *             Section III-A); the exterior layer is updated after the
+ *             unpack. A comparison form: per-cell updates, not the tile
+ *             engines.                                                    */
 typedef enum {
     JAC_MODE_UNFUSED = 0,
     JAC_MODE_FUSED = 1,
     JAC_MODE_GRAPH = 2,
     JAC_MODE_PERSISTENT = 3,
-    JAC_MODE_GRAPH_FUSED = 4
+    JAC_MODE_GRAPH_FUSED = 4,
+    JAC_MODE_SPLIT = 5
 } jac_mode;
 
 /* Rounding of the binary64 mean (binary32 contexts always use SEQ):

@@ -30,6 +30,7 @@ JAC_MODE_FUSED = 1
 JAC_MODE_GRAPH = 2
 JAC_MODE_PERSISTENT = 3
 JAC_MODE_GRAPH_FUSED = 4
+JAC_MODE_SPLIT = 5
 
 JAC_ARITH_SEQ = 0
 JAC_ARITH_EXACT = 1
@@ -40,6 +41,7 @@ MODES = {
     "graph": JAC_MODE_GRAPH,
     "persistent": JAC_MODE_PERSISTENT,
     "graph_fused": JAC_MODE_GRAPH_FUSED,
+    "split": JAC_MODE_SPLIT,
 }
 
 

@@ -2264,6 +2264,51 @@ __global__ void k_sum_partials(const double* partials, int n, double* out)
     if (threadIdx.x == 0) out[0] = sqrt(red[0]);
 }
 
+// The interior/exterior split of the update (the manual overlap of Section
+// II-A, Fig. 1): the interior region (cells 1 .. b-2 on every axis) reads
+// only the block's own values, so it can run while the halos are exchanged;
+// the exterior region (the outermost layer of cells) reads the ghost layer
+// and runs after the unpack. One thread per (x, y) column marching in z, the
+// z neighbours carried in registers, the per-cell mean of the context's rule.
+template <typename T, int OP>
+__device__ __forceinline__ T region_mean(T c, T xm, T xp, T ym, T yp, T zm, T zp)
+{
+    if constexpr (OP == OP_EXACT) return (T)mean7_exact((double)c, (double)xm, (double)xp, (double)ym, (double)yp,
+                                                        (double)zm, (double)zp);
+    else return mean7<T, 0>(c, xm, xp, ym, yp, zm, zp);
+}
+
+template <typename T, int OP>
+__global__ void k_update_region(T* pool, const BlockDesc* desc, int b, int p, int exterior)
+{
+    const BlockDesc& d = desc[b];
+    const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= bx || y >= by) return;
+    const bool ring = x == 0 || y == 0 || x == bx - 1 || y == by - 1;
+    int k0, k1, kstep;
+    if (!exterior) {
+        if (ring) return;
+        k0 = 1;
+        k1 = bz - 1;  // planes 1 .. bz-2
+        kstep = 1;
+    } else if (ring) {
+        k0 = 0;
+        k1 = bz;
+        kstep = 1;
+    } else {
+        k0 = 0;  // planes 0 and bz-1 of an inner column
+        k1 = bz;
+        kstep = bz > 1 ? bz - 1 : 1;
+    }
+    auto at = [&](int xx, int yy, int kk) { return load_cell<T, false, false>(pool, desc, d, p, xx, yy, kk); };
+    for (int k = k0; k < k1; k += kstep) {
+        const T o = region_mean<T, OP>(at(x, y, k), at(x - 1, y, k), at(x + 1, y, k), at(x, y - 1, k),
+                                        at(x, y + 1, k), at(x, y, k - 1), at(x, y, k + 1));
+        pool[cell_index<T>(d, p ^ 1, x, y, k)] = o;
+    }
+}
+
 // Face f of block d: the cells of the plane, first axis fastest.
 __device__ __forceinline__ int face_size(const BlockDesc& d, int f)
 {
@@ -2655,6 +2700,16 @@ cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void*
     const int th = 128, g = (maxface + th - 1) / th;
     if (dtype_f32) k_pack6<float><<<g, th, 0, s>>>((const float*)a.pool, a.desc, b, p, (float*)send, faceoff);
     else k_pack6<double><<<g, th, 0, s>>>((const double*)a.pool, a.desc, b, p, (double*)send, faceoff);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_region(const LaunchArgs& a, int dtype_f32, int arith, int b, int bx, int by, int p,
+                                 int exterior, cudaStream_t s)
+{
+    const dim3 th(32, 8, 1), g((bx + 31) / 32, (by + 7) / 8, 1);
+    if (dtype_f32) k_update_region<float, OP_SEQ><<<g, th, 0, s>>>((float*)a.pool, a.desc, b, p, exterior);
+    else if (arith == 1) k_update_region<double, OP_EXACT><<<g, th, 0, s>>>((double*)a.pool, a.desc, b, p, exterior);
+    else k_update_region<double, OP_SEQ><<<g, th, 0, s>>>((double*)a.pool, a.desc, b, p, exterior);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,10 @@ cudaError_t launch_pack6(const LaunchArgs& a, int dtype_f32, int b, int p, void*
                          int maxface, cudaStream_t s);
 cudaError_t launch_unpack6(const LaunchArgs& a, int dtype_f32, int b, int p, const void* recv, const int64_t* faceoff,
                            int maxface, cudaStream_t s);
+// the interior (exterior == 0: cells 1 .. b-2 on every axis) or the
+// exterior (the outermost layer) of block b's update, from its ghost layer
+cudaError_t launch_update_region(const LaunchArgs& a, int dtype_f32, int arith, int b, int bx, int by, int p,
+                                 int exterior, cudaStream_t s);
 // the six-face exchange of block b: its packed faces into the neighbours'
 // receive segments of the same halo buffer
 cudaError_t launch_exchange6(const LaunchArgs& a, int dtype_f32, int b, void* halo, const int64_t* send_off,

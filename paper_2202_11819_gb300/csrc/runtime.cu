@@ -210,7 +210,7 @@ struct jac_ctx {
     // Two event sets: one for eager issue and one used only while capturing a
     // graph (a wait may not name an event whose last record was captured).
     struct Events {
-        std::vector<cudaEvent_t> sent, unpacked, updated;
+        std::vector<cudaEvent_t> sent, unpacked, updated, interior;
         cudaEvent_t fork = nullptr;
     } ev[2];
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -677,10 +677,12 @@ int ensure_halo(jac_ctx* h)
         E.sent.resize(nblocks);
         E.unpacked.resize(nblocks);
         E.updated.resize(nblocks);
+        E.interior.resize(nblocks);
         for (int64_t b = 0; b < nblocks; ++b) {
             CU(cudaEventCreateWithFlags(&E.sent[b], cudaEventDisableTiming), "create event");
             CU(cudaEventCreateWithFlags(&E.unpacked[b], cudaEventDisableTiming), "create event");
             CU(cudaEventCreateWithFlags(&E.updated[b], cudaEventDisableTiming), "create event");
+            CU(cudaEventCreateWithFlags(&E.interior[b], cudaEventDisableTiming), "create event");
         }
         CU(cudaEventCreateWithFlags(&E.fork, cudaEventDisableTiming), "create event");
     }
@@ -772,6 +774,74 @@ int issue_unfused(jac_ctx* h, int p, bool capture)
         CU(launch_stencil_block(a, f32, h->arith, (int)b, h->ntx[b], h->nty[b], p, h->comp[b]), "update");
         h->launches += 1;
         CU(cudaEventRecord(E.updated[b], h->comp[b]), "record updated");
+    }
+    return JAC_OK;
+}
+
+// One iteration of the unfused flow with the interior/exterior split (the
+// manual overlap of Section II-A, Fig. 1, on the stream priorities of
+// Section III-A): per block, the interior update on the low-priority compute
+// stream starts as soon as the block's previous iteration is done, while the
+// high-priority communication stream packs the faces, copies them to the
+// neighbours and, once the neighbours' faces have arrived, unpacks them and
+// updates the exterior layer. Interior and exterior write disjoint cells of
+// buffer p^1; the exterior waits for the interior, whose results it reads in
+// the next iteration only through the stream order, so each block's
+// iteration ends with its exterior (event `updated`).
+int issue_split(jac_ctx* h, int p)
+{
+    const LaunchArgs a = h->args();
+    const int f32 = h->dtype == JAC_F32;
+    const int64_t nblocks = (int64_t)h->hdesc.size();
+    char* send = (char*)h->halo;
+    const size_t es = (size_t)h->esize;
+    auto& E = h->ev[0];
+    auto inner = [&](const BlockDesc& d) { return d.ext[0] > 2 && d.ext[1] > 2 && d.ext[2] > 2; };
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        if (!inner(d)) continue;
+        CU(cudaStreamWaitEvent(h->comp[b], E.updated[b], 0), "wait updated (interior)");
+        CU(launch_update_region(a, f32, h->arith, (int)b, d.ext[0], d.ext[1], p, 0, h->comp[b]), "interior");
+        h->launches += 1;
+        CU(cudaEventRecord(E.interior[b], h->comp[b]), "record interior");
+    }
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        cudaStream_t s = h->comm[b];
+        CU(cudaStreamWaitEvent(s, E.updated[b], 0), "wait updated");
+        for (int f = 0; f < 6; ++f) {
+            if (d.nbr[f] < 0) continue;
+            CU(launch_pack_face(a, f32, (int)b, f, p, send + h->send_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
+               "pack");
+            h->launches += 1;
+        }
+        for (int f = 0; f < 6; ++f) {
+            const int n = d.nbr[f];
+            if (n < 0) continue;
+            CU(cudaStreamWaitEvent(s, E.unpacked[n], 0), "wait unpacked");
+            CU(cudaMemcpyAsync(send + h->recv_off[(int64_t)n * 6 + opposite_face(f)] * es,
+                               send + h->send_off[b * 6 + f] * es, (size_t)h->fsize[b * 6 + f] * es,
+                               cudaMemcpyDeviceToDevice, s),
+               "halo copy");
+        }
+        CU(cudaEventRecord(E.sent[b], s), "record sent");
+    }
+    for (int64_t b = 0; b < nblocks; ++b) {
+        const BlockDesc& d = h->hdesc[b];
+        cudaStream_t s = h->comm[b];
+        for (int f = 0; f < 6; ++f)
+            if (d.nbr[f] >= 0) CU(cudaStreamWaitEvent(s, E.sent[d.nbr[f]], 0), "wait sent");
+        for (int f = 0; f < 6; ++f) {
+            if (d.nbr[f] < 0) continue;
+            CU(launch_unpack_face(a, f32, (int)b, f, p, send + h->recv_off[b * 6 + f] * es, h->fsize[b * 6 + f], s),
+               "unpack");
+            h->launches += 1;
+        }
+        CU(cudaEventRecord(E.unpacked[b], s), "record unpacked");
+        if (inner(d)) CU(cudaStreamWaitEvent(s, E.interior[b], 0), "wait interior");
+        CU(launch_update_region(a, f32, h->arith, (int)b, d.ext[0], d.ext[1], p, 1, s), "exterior");
+        h->launches += 1;
+        CU(cudaEventRecord(E.updated[b], s), "record updated");
     }
     return JAC_OK;
 }
@@ -1178,8 +1248,8 @@ int jac_set_mode(jac_ctx* h, int32_t mode)
 {
     int rc = check_ctx(h);
     if (rc) return rc;
-    if (mode < JAC_MODE_UNFUSED || mode > JAC_MODE_GRAPH_FUSED) return fail(JAC_EINVAL, "unknown mode %d", mode);
-    if (h->is_pool && (mode == JAC_MODE_UNFUSED || mode == JAC_MODE_GRAPH))
+    if (mode < JAC_MODE_UNFUSED || mode > JAC_MODE_SPLIT) return fail(JAC_EINVAL, "unknown mode %d", mode);
+    if (h->is_pool && (mode == JAC_MODE_UNFUSED || mode == JAC_MODE_GRAPH || mode == JAC_MODE_SPLIT))
         return fail(JAC_EINVAL, "pools run the fused or persistent forms only");
     h->mode = mode;
     return JAC_OK;
@@ -1298,6 +1368,15 @@ int jac_iterate(jac_ctx* h, int64_t n)
             if ((rc = fork_blocks(h, false))) return rc;
             for (int64_t i = 0; i < n; ++i) {
                 if ((rc = issue_unfused(h, h->parity, false))) return rc;
+                h->parity ^= 1;
+            }
+            if ((rc = join_blocks(h, false))) return rc;
+            break;
+        case JAC_MODE_SPLIT:
+            if ((rc = ensure_halo(h))) return rc;
+            if ((rc = fork_blocks(h, false))) return rc;
+            for (int64_t i = 0; i < n; ++i) {
+                if ((rc = issue_split(h, h->parity))) return rc;
                 h->parity ^= 1;
             }
             if ((rc = join_blocks(h, false))) return rc;

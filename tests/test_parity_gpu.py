@@ -20,7 +20,7 @@ from paper_2202_11819_gb300 import Jacobi3D, _lib
 
 pytestmark = pytest.mark.gpu
 
-MODES = ["unfused", "fused", "graph", "persistent", "graph_fused"]
+MODES = ["unfused", "fused", "graph", "persistent", "graph_fused", "split"]
 BC_MIXED = (1.0, 0.25, 0.0, 0.5, 0.125, 0.75)
 ORACLE_RULE = {"seq": oracle.RULE_SEQ, "exact": oracle.RULE_EXACT}
 
