@@ -1262,7 +1262,13 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     }
     const int x = x0 + 2 * tp, y = y0 + ty;
     const int plane = (int)d.plane;  // below 2^31 elements for every block shape the runtime makes
-    if (tid == 0) slow->n = 0;
+    if (tid == 0) {
+        slow->n = 0;
+        // this unit's bound of the buffer written now: its readers (the
+        // previous iteration's tiles of this block and its neighbours) have
+        // all finished; the warps fold their bounds into it at the end
+        if (uout) *uout = 0u;
+    }
 
     // own pair stream: planes z0+1 .. z1-1 through the ring, plane z1 into its
     // own slot at the start; the two current planes carried as frame integers
@@ -1584,16 +1590,11 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     cp_async_wait<0>();
     n2_slow_cells<PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, slow, eref, lzm);
     if (uout) {
-        // every output's exponent field is at most eref - (the tile's least count)
+        // every output's exponent field is at most eref - (the least count);
+        // published with the tile's results (the barrier and fence before the
+        // block's completion counter, or the end of the launch)
         const int w = __reduce_min_sync(0xffffffffu, lzm);
-        if ((tid & 31) == 0) s_red[tid >> 5] = (uint32_t)w;
-        __syncthreads();
-        if (tid == 0) {
-            int m = 64;
-#pragma unroll
-            for (int i = 0; i < kN / 32; ++i) m = min(m, (int)s_red[i]);
-            *uout = (uint32_t)max(0, eref - m);
-        }
+        if ((tid & 31) == 0) atomicMax(uout, (uint32_t)max(0, eref - w));
     }
 }
 
