@@ -50,7 +50,11 @@ constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
 template <typename T>
 constexpr int kMinCTAs = 1024 / kNT<T>;
 // The exact mean's two-column engine keeps four cells' values live per
-// thread: three 256-thread CTAs per SM (85 registers each) instead of four.
+// thread: three 256-thread CTAs per SM (80 registers each) instead of four.
+// Four at 64 registers (1.8 KB of spill stores in the compiled kernel)
+// measured the same on an aged field (0.461 against 0.462 ms per 512^3
+// iteration, 64-wide tiles) but slower with 32-wide tiles (0.482 against
+// 0.474).
 template <typename T, int OP>
 constexpr int kMinCTAsOp = (sizeof(T) == 8 && OP == 1) ? 3 : kMinCTAs<T>;
 
@@ -1261,7 +1265,7 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         if ((tid & 31) == 0) s_red[tid >> 5] = emax;
     }
     const int x = x0 + 2 * tp, y = y0 + ty;
-    const int plane = (int)d.plane;  // below 2^31 elements for every block shape the runtime makes
+    const int plane = (int)d.plane;  // block dims are at most 256: a plane holds fewer than 2^17 elements
     if (tid == 0) {
         slow->n = 0;
         // this unit's bound of the buffer written now: its readers (the
