@@ -237,9 +237,12 @@ int jac_iterate(jac_ctx *h, int64_t n_iters);
 /* rho(u) = sqrt( sum over interior cells of L^2 ),
  * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly. Binary64 grids:
  * L is rounded once to binary64 and accumulated in binary64 by fused
- * multiply-adds (acc = fma(L, L, acc)). Binary32 grids: L^2 is summed
- * exactly per thread and rounded once. The per-thread sums are combined by
- * a fixed tree per work unit, and the units' partials in unit order. That
+ * multiply-adds (acc = fma(L, L, acc)), per-thread sums combined by a fixed
+ * tree per work unit. Binary32 grids: L^2 is summed exactly per work unit
+ * and rounded once (a unit with a value more than 21 binades below the
+ * grid's largest, or of odd x extent, sums it exactly per thread and combines
+ * the rounded thread sums by a fixed tree). The units' partials are summed in
+ * unit order. That
  * order is fixed by the grid, the block dims, the tile width and z depth, and
  * the unit split the runtime derives from the device's SM count and
  * occupancy: repeated calls on one device and configuration give the same
@@ -253,6 +256,19 @@ int jac_residual(jac_ctx *h, double *out);
  * `dev_out` (one double). Stream-ordered, no host sync. For a batch context
  * rho covers all grids: sqrt of the sum over every grid's cells. */
 int jac_residual_device(jac_ctx *h, double *dev_out);
+
+/* Enqueue n_iters >= 0 iterations as jac_iterate does, together with the
+ * residual of the grid before every `every`-th of them (every >= 1):
+ * dev_out[j] = rho(u^(k0 + j * every)) for j = 0 .. ceil(n_iters / every) - 1,
+ * k0 the iteration count at the call; dev_out is device memory of that many
+ * doubles (unused when n_iters = 0). Binary32 contexts in the fused and
+ * graph-fused modes compute each residual inside the update launch that reads
+ * that grid (kernel fusion, Section III-D1: one launch, no second pass over
+ * the grid); other modes and binary64 contexts enqueue jac_residual_device
+ * before the iteration. Either way dev_out[j] has the bits jac_residual gives
+ * for that grid. Stream-ordered, no host sync; JAC_EINVAL for n_iters < 0,
+ * every < 1 or a null dev_out, JAC_ESTATE without a resident grid. */
+int jac_iterate_residual(jac_ctx *h, int64_t n_iters, int64_t every, double *dev_out);
 
 /* Per-grid residuals of a batch context: out[i] = rho of grid i, same
  * definition as jac_residual. The host form synchronises; the device form

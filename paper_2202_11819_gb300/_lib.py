@@ -133,6 +133,7 @@ _SIGS = {
     "jac_iterate": ([ctypes.c_void_p, ctypes.c_int64], ctypes.c_int),
     "jac_residual": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "jac_residual_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "jac_iterate_residual": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "jac_sync": ([ctypes.c_void_p], ctypes.c_int),
     "jac_info": ([ctypes.c_void_p, ctypes.POINTER(jac_info_t)], ctypes.c_int),
     "jac_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -298,6 +299,11 @@ def jac_residual(h) -> float:
 
 def jac_residual_device(h, dev_ptr: int) -> None:
     _check(load().jac_residual_device(h, ctypes.c_void_p(dev_ptr)), "jac_residual_device")
+
+
+def jac_iterate_residual(h, n_iters: int, every: int, dev_ptr: int) -> None:
+    _check(load().jac_iterate_residual(h, int(n_iters), int(every), ctypes.c_void_p(dev_ptr)),
+           "jac_iterate_residual")
 
 
 def jac_sync(h) -> None:

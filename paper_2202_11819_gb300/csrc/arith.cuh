@@ -1035,4 +1035,138 @@ JAC_HD inline double mean7(uint64_t S, uint32_t scale_hi)
 
 }  // namespace nframe
 
+// ------------------------------------------------------------------------
+// The binary32 residual in 32-bit words (the residual term of the update
+// launch, kernel fusion of Section III-D1).
+// Let every value of a binary32 grid satisfy |v| < 2^(E - 1) (E = the grid's
+// largest binary32 exponent field - 125). Two additions of constants split v
+// exactly into v = H q1 + r, q1 = 2^(E - 22), and r = G q2 when r is a
+// multiple of q2 = 2^(E - 45):
+//   t1 = RN(v + C1), C1 = 1.5 * 2^(E + 1): t1 lies in [2^(E + 1), 2^(E + 2)],
+//        where the binary32 numbers are spaced q1 apart, so t1 - C1 = H q1 is
+//        v rounded to a multiple of q1 (|H| <= 2^21) and the bit pattern of t1
+//        is bits(C1) + H (the patterns of one binade are consecutive
+//        integers, and 2^(E + 2) continues the count).
+//   r  = v - (t1 - C1), exact (|r| <= q1 / 2, a multiple of v's spacing).
+//   t2 = RN(r + C2), C2 = 1.5 * 2^(E - 22): t2 lies in [q1, 2 q1], spaced q2
+//        apart, and its bit pattern is bits(C2) + G, G = r rounded to a
+//        multiple of q2 (|G| <= 2^22). G q2 = r exactly iff RN(t2 - C2) == r
+//        (a subtraction that is itself exact): true for 0 and for every
+//        |v| >= 2^(E - 22), whose spacing is at least q2.
+// In a sum of bit patterns whose integer weights add up to zero the offsets
+// bits(C1), bits(C2) cancel, so the Laplacian term's two parts are 32-bit
+// integer sums of the raw patterns (wrapping arithmetic, exact results):
+//   LH = sum_6 bits(t1_n) - 6 bits(t1_c),  |LH| <= 12 * 2^21,
+//   LG = sum_6 bits(t2_n) - 6 bits(t2_c),  |LG| <= 12 * 2^22,
+// and L = (LH 2^23 + LG) q2 exactly. L^2 / q2^2 = LH^2 2^46 + 2 LH LG 2^23 +
+// LG^2: three 64-bit sums of 32 x 32-bit products, each term below 2^51.2,
+// so up to 2^11 cells per sum stay below 2^63; their combination
+// S = A 2^46 + B 2^24 + C is exact in 128 bits, and the sum of squares is
+// S q2^2 = S 2^(2 E - 90).
+// ------------------------------------------------------------------------
+namespace r32 {
+
+JAC_HD inline float fadd(float a, float b)
+{
+#if defined(__CUDA_ARCH__)
+    return __fadd_rn(a, b);
+#else
+    return a + b;  // binary32 arithmetic on the host (SSE / NEON): rounded to nearest even
+#endif
+}
+
+JAC_HD inline float fsub(float a, float b)
+{
+#if defined(__CUDA_ARCH__)
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+
+JAC_HD inline uint32_t fbits(float v)
+{
+    uint32_t b;
+    memcpy(&b, &v, 4);
+    return b;
+}
+
+// 1.5 * 2^e as a binary32 number (e in [-126, 127]).
+JAC_HD inline float c15(int e)
+{
+    const uint32_t b = ((uint32_t)(e + 127) << 23) | 0x400000u;
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+// E for a grid whose largest binary32 exponent field is f (|v| < 2^(f - 126)).
+JAC_HD inline int frame_E(int f) { return f - 125; }
+
+// C1 and C2 are normal binary32 numbers and the result's scale is a normal
+// binary64 one.
+JAC_HD inline bool frame_ok(int E) { return E >= -100 && E <= 125; }
+
+struct Split {
+    uint32_t h, g;  // bit patterns of t1 and t2
+};
+
+// The split of v (c1 = C1, c2 = C2); `inexact` is set when r is not a
+// multiple of q2.
+JAC_HD inline Split split(float v, float c1, float c2, bool& inexact)
+{
+    const float t1 = fadd(v, c1);
+    const float r = fsub(v, fsub(t1, c1));
+    const float t2 = fadd(r, c2);
+    inexact |= fsub(t2, c2) != r;
+    return {fbits(t1), fbits(t2)};
+}
+
+// The split without the check (for a value another lane checks).
+JAC_HD inline Split split_nc(float v, float c1, float c2)
+{
+    const float t1 = fadd(v, c1);
+    const float r = fsub(v, fsub(t1, c1));
+    return {fbits(t1), fbits(fadd(r, c2))};
+}
+
+// One part of L: n0 + ... + n5 - 6 c over bit patterns.
+JAC_HD inline int32_t lpart(uint32_t c, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t n3, uint32_t n4, uint32_t n5)
+{
+    return (int32_t)(n0 + n1 + n2 + n3 + n4 + n5 - 6u * c);
+}
+
+struct Acc {
+    int64_t a, b, c;  // sums of LH^2, LH LG, LG^2
+};
+
+JAC_HD inline void add_square(int32_t lh, int32_t lg, Acc& s)
+{
+    s.a += (int64_t)lh * lh;
+    s.b += (int64_t)lh * lg;
+    s.c += (int64_t)lg * lg;
+}
+
+// (lo, hi) += x 2^sh as 128-bit two's complement (0 <= sh < 64).
+JAC_HD inline void add_i128(uint64_t& lo, uint64_t& hi, int64_t x, int sh)
+{
+    const uint64_t xl = (uint64_t)x << sh;
+    const uint64_t xh = sh ? (uint64_t)(x >> (64 - sh)) : (x < 0 ? ~0ull : 0ull);
+    const uint64_t nl = lo + xl;
+    hi += xh + (nl < xl ? 1u : 0u);
+    lo = nl;
+}
+
+// S = a 2^46 + b 2^24 + c (nonnegative: a sum of squares) as 128 bits.
+JAC_HD inline void combine(const Acc& s, uint64_t& lo, uint64_t& hi)
+{
+    lo = 0u;
+    hi = 0u;
+    add_i128(lo, hi, s.c, 0);
+    add_i128(lo, hi, s.b, 24);
+    add_i128(lo, hi, s.a, 46);
+}
+
+}  // namespace r32
+
 }  // namespace jac

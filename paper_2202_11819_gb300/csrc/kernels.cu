@@ -1845,9 +1845,20 @@ __device__ __forceinline__ Src<float> pair_source(const float* pool, const Block
 __device__ __forceinline__ float2 ld2(const float* p) { return *(const float2*)p; }
 __device__ __forceinline__ float2 ldcg2(const float* p) { return __ldcg((const float2*)p); }
 
-template <bool CG, int TW>
-__device__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __restrict__ desc, int b, int p, int x0,
-                                  int y0, int z0, int z1, unsigned char* smraw)
+// What the engine's residual modes return per thread: the exact sums of the
+// split Laplacian terms of its interior cells, and whether a value it read
+// lies outside the split's exact range (or the grid's frame is out of range).
+struct R32Out {
+    r32::Acc acc;
+    bool bad;
+};
+
+// RM (residual mode): 0 the update only; 1 the update and, from the same
+// values, the residual terms of the grid it reads; 2 the residual terms only.
+template <bool CG, int TW, int RM = 0>
+__device__ __forceinline__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __restrict__ desc, int b,
+                                                  int p, int x0, int y0, int z0, int z1, unsigned char* smraw,
+                                                  const int32_t* frame_e = nullptr, R32Out* ro = nullptr)
 {
     using T = float;
     constexpr int kB = kR2Batch, kP = kR2Ahead, RD = kR2Ring, kNB = RD / kB;
@@ -1979,6 +1990,31 @@ __device__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __r
     cp_async_wait<kP>();
     __syncthreads();
     float2 c = ld2(rd);
+    // residual modes: the split constants of the block's grid, the own pair's
+    // splits at planes k (rc*) and k - 1 (rz*), and the exact sums. Every value
+    // a cell reads is checked by one lane at least: its own tile's values by
+    // their owners (the pair entering as zp, the first plane, the plane below
+    // the range), the x halo by the lanes reading xm0 and xp1, the y halo rows
+    // by the warps holding the tile's first and last rows, the row at the
+    // block's y edge by its k2p owners.
+    [[maybe_unused]] float c1 = 0.f, c2 = 0.f;
+    [[maybe_unused]] bool rbad = false;
+    [[maybe_unused]] r32::Acc racc{0, 0, 0};
+    [[maybe_unused]] r32::Split rc0{}, rc1{}, rz0{}, rz1{};
+    [[maybe_unused]] const bool ylo_warp = (tid >> 5) == 0, yhi_warp = (tid >> 5) == kNT<T> / 32 - 1;
+    if constexpr (RM != 0) {
+        const int E = r32::frame_E(frame_e[d.inst] - 896);
+        rbad = !r32::frame_ok(E);
+        const int Ec = rbad ? 0 : E;  // finite constants either way
+        c1 = r32::c15(Ec + 1);
+        c2 = r32::c15(Ec - 22);
+        bool eo = false, ez = false;
+        rc0 = r32::split(c.x, c1, c2, eo);
+        rc1 = r32::split(c.y, c1, c2, eo);
+        rz0 = r32::split(zm.x, c1, c2, ez);
+        rz1 = r32::split(zm.y, c1, c2, ez);
+        rbad |= ((k1 || k2p) && eo) || (k1 && ez);
+    }
     // Batch j computes planes k0 .. k0+kB-1 (slots q0 ..) and reads plane
     // k0+kB too; it first issues copy batch j + kP + 1 into slots sb ..
     int q0 = 0, sb = (kP + 1) * kB;
@@ -1998,25 +2034,61 @@ __device__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __r
                 const float2 zp = (FULL || k + 1 < z1) ? ld2(pn) : zhiv;
                 const float xm0 = pl[-1], xp1 = pl[2];
                 const float2 ym = ld2(pl - kSW), yp = ld2(pl + kSW);
-                float s0 = __fadd_rn(c.x, xm0);
-                s0 = __fadd_rn(s0, c.y);
-                s0 = __fadd_rn(s0, ym.x);
-                s0 = __fadd_rn(s0, yp.x);
-                s0 = __fadd_rn(s0, zm.x);
-                s0 = __fadd_rn(s0, zp.x);
-                float s1 = __fadd_rn(c.y, c.x);
-                s1 = __fadd_rn(s1, xp1);
-                s1 = __fadd_rn(s1, ym.y);
-                s1 = __fadd_rn(s1, yp.y);
-                s1 = __fadd_rn(s1, zm.y);
-                s1 = __fadd_rn(s1, zp.y);
-                float2 o = make_float2(div7f_fast(s0), div7f_fast(s1));
-                // the exact small-value path, for the warp only when a lane needs it
-                if (__any_sync(0xffffffffu, k1 && (div7f_needs_exact(s0) || div7f_needs_exact(s1)))) {
-                    o.x = div7f(s0);
-                    o.y = div7f(s1);
+                if constexpr (RM != 2) {
+                    float s0 = __fadd_rn(c.x, xm0);
+                    s0 = __fadd_rn(s0, c.y);
+                    s0 = __fadd_rn(s0, ym.x);
+                    s0 = __fadd_rn(s0, yp.x);
+                    s0 = __fadd_rn(s0, zm.x);
+                    s0 = __fadd_rn(s0, zp.x);
+                    float s1 = __fadd_rn(c.y, c.x);
+                    s1 = __fadd_rn(s1, xp1);
+                    s1 = __fadd_rn(s1, ym.y);
+                    s1 = __fadd_rn(s1, yp.y);
+                    s1 = __fadd_rn(s1, zm.y);
+                    s1 = __fadd_rn(s1, zp.y);
+                    float2 o = make_float2(div7f_fast(s0), div7f_fast(s1));
+                    // the exact small-value path, for the warp only when a lane needs it
+                    if (__any_sync(0xffffffffu, k1 && (div7f_needs_exact(s0) || div7f_needs_exact(s1)))) {
+                        o.x = div7f(s0);
+                        o.y = div7f(s1);
+                    }
+                    if (k1) *(float2*)out = o;
                 }
-                if (k1) *(float2*)out = o;
+                if constexpr (RM != 0) {
+                    // L of the pair's cells at plane k, in the split words
+                    bool eo = false, ex = false, ey = false;
+                    const r32::Split n0 = r32::split(zp.x, c1, c2, eo), n1 = r32::split(zp.y, c1, c2, eo);
+                    const r32::Split sxm = r32::split(xm0, c1, c2, ex), sxp = r32::split(xp1, c1, c2, ex);
+                    r32::Split sym0, sym1, syp0, syp1;
+                    if (ylo_warp) {
+                        sym0 = r32::split(ym.x, c1, c2, ey);
+                        sym1 = r32::split(ym.y, c1, c2, ey);
+                    } else {
+                        sym0 = r32::split_nc(ym.x, c1, c2);
+                        sym1 = r32::split_nc(ym.y, c1, c2);
+                    }
+                    if (yhi_warp) {
+                        syp0 = r32::split(yp.x, c1, c2, ey);
+                        syp1 = r32::split(yp.y, c1, c2, ey);
+                    } else {
+                        syp0 = r32::split_nc(yp.x, c1, c2);
+                        syp1 = r32::split_nc(yp.y, c1, c2);
+                    }
+                    rbad |= ((k1 || k2p) && eo) || (k1 && (ex || ey));
+                    const int32_t h0 = r32::lpart(rc0.h, sxm.h, rc1.h, sym0.h, syp0.h, rz0.h, n0.h);
+                    const int32_t g0 = r32::lpart(rc0.g, sxm.g, rc1.g, sym0.g, syp0.g, rz0.g, n0.g);
+                    const int32_t h1 = r32::lpart(rc1.h, rc0.h, sxp.h, sym1.h, syp1.h, rz1.h, n1.h);
+                    const int32_t g1 = r32::lpart(rc1.g, rc0.g, sxp.g, sym1.g, syp1.g, rz1.g, n1.g);
+                    if (k1) {
+                        r32::add_square(h0, g0, racc);
+                        r32::add_square(h1, g1, racc);
+                    }
+                    rz0 = rc0;
+                    rz1 = rc1;
+                    rc0 = n0;
+                    rc1 = n1;
+                }
                 out += plane;
                 zm = c;
                 c = zp;
@@ -2032,6 +2104,10 @@ __device__ void tile_engine_ring2(float* __restrict__ pool, const BlockDesc* __r
     for (; k0 < z1; k0 += kB) batch(std::false_type{}, k0);
     cp_async_wait<0>();
     __syncthreads();  // the ring is free for the next unit
+    if constexpr (RM != 0) {
+        ro->acc = racc;
+        ro->bad = rbad;
+    }
 }
 
 // A binary32 unit (TW x 1024/TW cells): the two-column engine when the
@@ -2236,6 +2312,135 @@ __global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_residual(const T* pool,
         __syncthreads();
     }
     if (tid == 0) partials[blockIdx.x] = red[0];
+}
+
+// ------------------------------------------------ binary32 residual in the ring
+// The binary32 residual from the two-column ring engine (residual modes): per
+// work unit the exact sum of L^2 (split words, 128-bit combination, one
+// rounding to binary64). Units the split cannot take (odd x extent, a value
+// outside its exact range, a grid frame out of range) take the 64-bit-frame
+// engine of k_residual, whose per-unit partial is rounded per thread and
+// summed by a fixed tree. The partials are summed by the last unit to finish,
+// in k_sum_partials' order, so the grid's rho is the same bits in every form
+// that produces it.
+
+// The unit's partial from the threads' exact sums (valid in thread 0).
+__device__ double r32_unit_partial(const r32::Acc& a, int E, unsigned char* smraw)
+{
+    uint64_t lo, hi;
+    r32::combine(a, lo, hi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t ol = __shfl_down_sync(0xffffffffu, lo, o), oh = __shfl_down_sync(0xffffffffu, hi, o);
+        const uint64_t nl = lo + ol;
+        hi += oh + (nl < ol ? 1u : 0u);
+        lo = nl;
+    }
+    uint64_t* const w = (uint64_t*)smraw;  // [warps][2]
+    const int tid = threadIdx.x;
+    if ((tid & 31) == 0) {
+        w[2 * (tid >> 5)] = lo;
+        w[2 * (tid >> 5) + 1] = hi;
+    }
+    __syncthreads();
+    double part = 0.0;
+    if (tid == 0) {
+        uint64_t sl = 0u, sh = 0u;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            const uint64_t nl = sl + w[2 * i];
+            sh += w[2 * i + 1] + (nl < w[2 * i] ? 1u : 0u);
+            sl = nl;
+        }
+        part = frame::u192_to_double_scaled(sl, sh, 0u, 2 * E - 90);
+    }
+    __syncthreads();
+    return part;
+}
+
+// The 64-bit-frame engine's partial of a unit (valid in thread 0): the two
+// engine tiles, then a fixed tree over the threads.
+template <int TW>
+__device__ __noinline__ double r32_fallback_partial(float* pool, const BlockDesc* desc, const int32_t* frame_e, int b, int p,
+                                       int x0, int y0, int z0, int z1, SlowList* slow)
+{
+    using T = float;
+    double acc = tile_engine_pair<T, OP_RES32, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1,
+                                                                          jac_dyn_sm, slow);
+    __syncthreads();
+    acc += tile_engine_pair<T, OP_RES32, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0 + kNT<T> / TW,
+                                                                    z0, z1, jac_dyn_sm, slow);
+    __syncthreads();
+    double* const red = (double*)jac_dyn_sm;
+    const int tid = threadIdx.x;
+    red[tid] = acc;
+    __syncthreads();
+    for (int s = kNT<T> / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = red[tid] + red[tid + s];
+        __syncthreads();
+    }
+    const double part = red[0];
+    __syncthreads();
+    return part;
+}
+
+// RM 1: one binary32 update iteration (as k_fused_ring) that also returns the
+// residual of the grid it reads; RM 2: the residual only. partials[unit] gets
+// the unit's partial; with `out` set, the last unit to finish writes
+// sqrt(sum of partials) there and clears *count (zero at every launch).
+template <int RM>
+__global__ void __launch_bounds__(kNT<float>, kMinCTAs<float>)
+    k_ring_residual(float* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits,
+                    int p, double* partials, unsigned* count, double* out)
+{
+    __shared__ SlowList slow;
+    __shared__ int s_last;
+    const TileUnit u = units[blockIdx.x];
+    const BlockDesc& d = desc[u.block];
+    const int tid = threadIdx.x;
+    double part = 0.0;
+    with_tw(u.tw, [&](auto tw_c) {
+        constexpr int TW = decltype(tw_c)::value;
+        bool fall = true;
+        if ((d.ext[0] & 1) == 0) {
+            R32Out ro;
+            tile_engine_ring2<false, TW, RM>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, frame_e,
+                                             &ro);
+            fall = __syncthreads_or(ro.bad);
+            if (!fall) part = r32_unit_partial(ro.acc, r32::frame_E(frame_e[d.inst] - 896), jac_dyn_sm);
+        } else if constexpr (RM == 1) {
+            tile_engine_ring<float, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1, jac_dyn_sm);
+            tile_engine_ring<float, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0 + kNT<float> / TW, u.z0,
+                                                     u.z1, jac_dyn_sm);
+        }
+        if (fall) part = r32_fallback_partial<TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
+    });
+    if (tid == 0) {
+        partials[blockIdx.x] = part;
+        if (out) {
+            __threadfence();
+            s_last = atomicAdd(count, 1u) == (unsigned)(nunits - 1);
+        }
+    }
+    if (!out) return;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // k_sum_partials' order: 256 strided sums, then a fixed tree
+    double* const red = (double*)jac_dyn_sm;
+    if (tid < 256) {
+        double acc = 0.0;
+        for (int i = tid; i < nunits; i += 256) acc = acc + __ldcg(partials + i);
+        red[tid] = acc;
+    }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] = red[tid] + red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        out[0] = sqrt(red[0]);
+        *count = 0u;
+    }
 }
 
 // Per-grid residuals: resident grid i (slot slot[i]) owns partials
@@ -2568,6 +2773,31 @@ static int residual_bytes(int tw_mask)
     return n;
 }
 
+template <int TW>
+static constexpr int ring_res_bytes_tw()
+{
+    constexpr int a = f32_unit_bytes<TW>(), b = pair_engine_bytes<float, OP_RES32, TW, kRingRes>();
+    constexpr int m = a > b ? a : b;
+    return m > 256 * (int)sizeof(double) ? m : 256 * (int)sizeof(double);
+}
+
+static int ring_res_bytes(int tw_mask)
+{
+    if (tw_mask == 0) tw_mask = 7;
+    int n = 0;
+    if (tw_mask & 1) n = std::max(n, ring_res_bytes_tw<16>());
+    if (tw_mask & 2) n = std::max(n, ring_res_bytes_tw<32>());
+    if (tw_mask & 4) n = std::max(n, ring_res_bytes_tw<64>());
+    return n;
+}
+
+cudaError_t launch_fused_residual_f32(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s)
+{
+    k_ring_residual<1><<<a.nunits, kNT<float>, ring_res_bytes(a.tw_mask), s>>>(
+        (float*)a.pool, a.desc, a.frame, a.units, a.nunits, p, partials, a.rcount, dev_out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s)
 {
     if (dtype_f32)
@@ -2629,7 +2859,8 @@ cudaError_t prepare_kernels()
     JAC_ALLOW((k_persistent<double, OP_SEQ, false>), (unit_bytes_max<double, OP_SEQ>()));
     JAC_ALLOW((k_persistent<float, OP_SEQ, true>), (unit_bytes_max<float, OP_SEQ>()));
     JAC_ALLOW((k_residual<double>), (residual_bytes<double>(7)));
-    JAC_ALLOW((k_residual<float>), (residual_bytes<float>(7)));
+    JAC_ALLOW((k_ring_residual<1>), (ring_res_bytes(7)));
+    JAC_ALLOW((k_ring_residual<2>), (ring_res_bytes(7)));
 #undef JAC_ALLOW
     return e;
 }
@@ -2655,8 +2886,8 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
 cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, double* partials, cudaStream_t s)
 {
     if (dtype_f32)
-        k_residual<float><<<a.nunits, kNT<float>, residual_bytes<float>(a.tw_mask), s>>>((const float*)a.pool, a.desc, a.frame,
-                                                                             a.units, p, partials);
+        k_ring_residual<2><<<a.nunits, kNT<float>, ring_res_bytes(a.tw_mask), s>>>(
+            (float*)a.pool, a.desc, a.frame, a.units, a.nunits, p, partials, a.rcount, nullptr);
     else
         k_residual<double><<<a.nunits, kNT<double>, residual_bytes<double>(a.tw_mask), s>>>((const double*)a.pool, a.desc,
                                                                                a.frame, a.units, p, partials);
@@ -2666,6 +2897,11 @@ cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, 
 cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
                             cudaStream_t s)
 {
+    if (dtype_f32) {  // one launch: the last unit sums the partials
+        k_ring_residual<2><<<a.nunits, kNT<float>, ring_res_bytes(a.tw_mask), s>>>(
+            (float*)a.pool, a.desc, a.frame, a.units, a.nunits, p, partials, a.rcount, out);
+        return cudaGetLastError();
+    }
     cudaError_t e = launch_residual_partials(a, dtype_f32, p, partials, s);
     if (e != cudaSuccess) return e;
     k_sum_partials<<<1, 256, 0, s>>>(partials, a.nunits, out);

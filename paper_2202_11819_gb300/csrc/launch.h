@@ -18,6 +18,7 @@ struct LaunchArgs {
     uint32_t* uexp;          // [2][units_cap]: per buffer parity and work unit, a bound on the
                              // exponent field of the unit's values there (all ones: unknown)
     int units_cap;
+    uint32_t* rcount;        // zero between launches: the last-unit counter of the binary32 residual
     int nblocks;
     int nunits;
     int tile_w;              // tile width of the update engine: 16, 32 or 64
@@ -51,6 +52,9 @@ cudaError_t prepare_kernels();
 
 cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, int b, int nx_tiles, int ny_tiles,
                                  int p, cudaStream_t s);
+// One binary32 update iteration (k_fused_ring's result) that also writes
+// rho of the grid it reads to dev_out (one launch).
+cudaError_t launch_fused_residual_f32(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s);
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s);
 cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int dtype_f32, int arith, int ctas,
                               cudaStream_t s);

@@ -230,6 +230,7 @@ struct jac_ctx {
     double* partials = nullptr;
     uint32_t* uexp = nullptr;  // [2][partials_cap] unit exponent bounds (see LaunchArgs)
     double* dres = nullptr;
+    uint32_t* rcount = nullptr;  // the binary32 residual's last-unit counter (zero between launches)
     void* dense = nullptr;
     size_t dense_bytes = 0;
 
@@ -242,6 +243,7 @@ struct jac_ctx {
         a.frame = frame;
         a.uexp = uexp;
         a.units_cap = (int)partials_cap;
+        a.rcount = rcount;
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
         a.tile_w = tile_w;
@@ -1065,11 +1067,13 @@ int open_ctx(jac_ctx* h, void* stream)
     if ((rc = dev_alloc(h, sizeof(DeviceStatus), (void**)&h->status))) return rc;
     if ((rc = dev_alloc(h, sizeof(unsigned long long), (void**)&h->dbad))) return rc;
     if ((rc = dev_alloc(h, sizeof(double), (void**)&h->dres))) return rc;
+    if ((rc = dev_alloc(h, sizeof(uint32_t), (void**)&h->rcount))) return rc;
     if ((rc = dev_alloc(h, ns * sizeof(double), (void**)&h->dres_inst))) return rc;
     if ((rc = dev_alloc(h, ns * sizeof(int32_t), (void**)&h->frame))) return rc;
     if ((rc = dev_alloc(h, (ns + 1) * sizeof(int32_t), (void**)&h->dseg))) return rc;
     if ((rc = dev_alloc(h, ns * sizeof(int32_t), (void**)&h->dslot))) return rc;
     CU(cudaMemsetAsync(h->status, 0, sizeof(DeviceStatus), h->stream), "clear status");
+    CU(cudaMemsetAsync(h->rcount, 0, sizeof(uint32_t), h->stream), "clear residual counter");
     return JAC_OK;
 }
 
@@ -1438,7 +1442,35 @@ int jac_residual_device(jac_ctx* h, double* dev_out)
     if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
     if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
     CU(launch_residual(h->args(), h->dtype == JAC_F32, h->parity, h->partials, dev_out, h->stream), "residual");
-    h->launches += 2;
+    h->launches += h->dtype == JAC_F32 ? 1 : 2;
+    return JAC_OK;
+}
+
+int jac_iterate_residual(jac_ctx* h, int64_t n, int64_t every, double* dev_out)
+{
+    int rc = check_ready(h);
+    if (rc) return rc;
+    if (n < 0) return fail(JAC_EINVAL, "n_iters must be >= 0");
+    if (every < 1) return fail(JAC_EINVAL, "every must be >= 1");
+    if (n == 0) return JAC_OK;
+    if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
+    if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
+    // binary32 in the fused forms: the residual of u^k comes from the launch
+    // that computes u^(k+1); elsewhere the residual launch precedes the chunk
+    const bool fuse = h->dtype == JAC_F32 && (h->mode == JAC_MODE_FUSED || h->mode == JAC_MODE_GRAPH_FUSED);
+    for (int64_t i = 0, j = 0; i < n; i += every, ++j) {
+        const int64_t m = std::min(every, n - i);
+        if (fuse) {
+            CU(launch_fused_residual_f32(h->args(), h->parity, h->partials, dev_out + j, h->stream), "fused residual");
+            h->launches += 1;
+            h->parity ^= 1;
+            h->iters += 1;
+            if (m > 1 && (rc = jac_iterate(h, m - 1))) return rc;
+        } else {
+            if ((rc = jac_residual_device(h, dev_out + j))) return rc;
+            if ((rc = jac_iterate(h, m))) return rc;
+        }
+    }
     return JAC_OK;
 }
 

@@ -133,6 +133,16 @@ class Jacobi3D:
         _lib.jac_residual_device(self.h, out_tensor.data_ptr())
         return out_tensor
 
+    def iterate_residual(self, n: int, every: int, out_tensor):
+        """n iterations and rho of the grid before every `every`-th of them:
+        out_tensor (device float64, at least ceil(n / every) values) gets
+        rho(u^(k0 + j * every)), j = 0, 1, ..."""
+        need = -(-int(n) // int(every)) if n > 0 and every > 0 else 0
+        if out_tensor.numel() < need:
+            raise ValueError(f"out_tensor holds {out_tensor.numel()} values, {need} needed")
+        _lib.jac_iterate_residual(self.h, n, every, out_tensor.data_ptr())
+        return out_tensor
+
     def sync(self):
         _lib.jac_sync(self.h)
 

@@ -131,3 +131,70 @@ extern "C" int host_nframe_mean7(const double* v, int eref, double* out)
     *out = mean7(S, scale_hi(eref));
     return 1;
 }
+
+// ---- binary32 residual in split words (r32), for a grid whose largest
+// binary32 exponent field is f.
+
+// The split of v: 1 when exact; hg = (H, G), the offsets of the two bit
+// patterns from those of C1 and C2. -1 when the frame is out of range.
+extern "C" int host_r32_split(float v, int f, int32_t* hg)
+{
+    using namespace jac::r32;
+    const int E = frame_E(f);
+    if (!frame_ok(E)) return -1;
+    const float c1 = c15(E + 1), c2 = c15(E - 22);
+    bool inexact = false;
+    const Split s = split(v, c1, c2, inexact);
+    hg[0] = (int32_t)(s.h - fbits(c1));
+    hg[1] = (int32_t)(s.g - fbits(c2));
+    return inexact ? 0 : 1;
+}
+
+// The two parts of L for one cell (v = c, xm, xp, ym, yp, zm, zp):
+// L = (LH 2^23 + LG) 2^(E - 45). Returns as host_r32_split.
+extern "C" int host_r32_laplacian(const float* v, int f, int32_t* lhg)
+{
+    using namespace jac::r32;
+    const int E = frame_E(f);
+    if (!frame_ok(E)) return -1;
+    const float c1 = c15(E + 1), c2 = c15(E - 22);
+    bool inexact = false;
+    Split s[7];
+    for (int j = 0; j < 7; ++j) s[j] = split(v[j], c1, c2, inexact);
+    lhg[0] = lpart(s[0].h, s[1].h, s[2].h, s[3].h, s[4].h, s[5].h, s[6].h);
+    lhg[1] = lpart(s[0].g, s[1].g, s[2].g, s[3].g, s[4].g, s[5].g, s[6].g);
+    return inexact ? 0 : 1;
+}
+
+// The sum of L^2 over n cells as one engine thread forms it (the three
+// 64-bit sums in acc3), combined in 128 bits and rounded once (out).
+// Returns as host_r32_split.
+extern "C" int host_r32_sum_squares(const float* v, int n, int f, int64_t* acc3, double* out)
+{
+    using namespace jac::r32;
+    const int E = frame_E(f);
+    if (!frame_ok(E)) return -1;
+    const float c1 = c15(E + 1), c2 = c15(E - 22);
+    bool inexact = false;
+    Acc a{0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+        Split s[7];
+        for (int j = 0; j < 7; ++j) s[j] = split(v[7 * i + j], c1, c2, inexact);
+        add_square(lpart(s[0].h, s[1].h, s[2].h, s[3].h, s[4].h, s[5].h, s[6].h),
+                   lpart(s[0].g, s[1].g, s[2].g, s[3].g, s[4].g, s[5].g, s[6].g), a);
+    }
+    acc3[0] = a.a;
+    acc3[1] = a.b;
+    acc3[2] = a.c;
+    uint64_t lo, hi;
+    combine(a, lo, hi);
+    *out = jac::frame::u192_to_double_scaled(lo, hi, 0u, 2 * E - 90);
+    return inexact ? 0 : 1;
+}
+
+// S = a 2^46 + b 2^24 + c in 128 bits (lohi = low word, high word).
+extern "C" void host_r32_combine(const int64_t* abc, uint64_t* lohi)
+{
+    jac::r32::Acc a{abc[0], abc[1], abc[2]};
+    jac::r32::combine(a, lohi[0], lohi[1]);
+}

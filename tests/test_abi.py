@@ -53,6 +53,7 @@ def test_strerror_and_invalid_arguments_without_gpu():
     assert e.value.code == _lib.JAC_EINVAL
     lib = _lib.load()
     assert lib.jac_iterate(None, 1) == _lib.JAC_EINVAL
+    assert lib.jac_iterate_residual(None, 1, 1, None) == _lib.JAC_EINVAL
     assert lib.jac_destroy(None) == _lib.JAC_OK
 
 

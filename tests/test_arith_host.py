@@ -573,3 +573,134 @@ def test_narrow_frame_mean7_ties_and_near_ties(host_lib):
             assert np.float64(out.value).tobytes() == np.float64(want).tobytes(), vals
             n += 1
     assert n == 4000
+
+
+# ---- binary32 residual in split words (the update launch's residual term)
+
+def _r32_bind(lib):
+    lib.host_r32_split.argtypes = [ctypes.c_float, ctypes.c_int, ctypes.c_void_p]
+    lib.host_r32_split.restype = ctypes.c_int
+    lib.host_r32_laplacian.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    lib.host_r32_laplacian.restype = ctypes.c_int
+    lib.host_r32_sum_squares.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p]
+    lib.host_r32_sum_squares.restype = ctypes.c_int
+    lib.host_r32_combine.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    lib.host_r32_combine.restype = None
+    return lib
+
+
+def _f32_cases(rng, f, n):
+    """binary32 values below 2^(E - 1) (E = f - 125): random magnitudes over
+    40 binades below the top, zeros, the extremes and the split's boundaries."""
+    E = f - 125
+    top = np.nextafter(np.float32(2.0 ** (E - 1)), np.float32(0))
+    q1 = 2.0 ** (E - 22)
+    special = [0.0, -0.0, top, -top, q1, -q1, q1 / 2, 1.5 * q1, 2.5 * q1, np.nextafter(np.float32(q1), np.float32(0)),
+               2.0 ** (E - 45), 3 * 2.0 ** (E - 45), 2.0 ** (E - 46), 2.0 ** (E - 23) * 1.25]
+    e = rng.uniform(E - 41, E - 1, n)
+    v = (2.0 ** e) * rng.choice([-1.0, 1.0], n)
+    out = np.concatenate([np.array(special, dtype=np.float64), v]).astype(np.float32)
+    return out[np.abs(out.astype(np.float64)) < 2.0 ** (E - 1)]
+
+
+@pytest.mark.parametrize("f", [127, 150, 40, 230])
+def test_r32_split_is_exact_exactly_where_it_reports_so(host_lib, f):
+    lib = _r32_bind(host_lib)
+    E = f - 125
+    q1, q2 = Fraction(2) ** (E - 22), Fraction(2) ** (E - 45)
+    hg = (ctypes.c_int32 * 2)()
+    n_exact = n_inexact = 0
+    for v in _f32_cases(np.random.default_rng(f), f, 3000):
+        rc = lib.host_r32_split(float(v), f, hg)
+        fv = Fraction(float(v))
+        exact = (fv / q2).denominator == 1
+        assert rc == (1 if exact else 0), (v, rc)
+        if abs(fv) >= q1:
+            assert rc == 1, v  # the window: every value within 21 binades of the top
+        if rc == 1:
+            n_exact += 1
+            assert hg[0] * q1 + hg[1] * q2 == fv, v
+            assert abs(hg[0]) <= 2 ** 21 and abs(hg[1]) <= 2 ** 22
+        else:
+            n_inexact += 1
+    assert n_exact > 1000 and n_inexact > 100
+
+
+def test_r32_split_declines_frames_out_of_range(host_lib):
+    lib = _r32_bind(host_lib)
+    hg = (ctypes.c_int32 * 2)()
+    assert lib.host_r32_split(1.0, 251, hg) == -1  # E = 126: C1 = 1.5 * 2^127 would overflow
+    assert lib.host_r32_split(0.0, 24, hg) == -1  # E = -101: C2 would be subnormal
+    assert lib.host_r32_split(1.0, 250, hg) != -1 and lib.host_r32_split(0.0, 25, hg) != -1
+
+
+@pytest.mark.parametrize("f", [127, 100])
+def test_r32_laplacian_parts_are_the_exact_term(host_lib, f):
+    lib = _r32_bind(host_lib)
+    E = f - 125
+    q2 = Fraction(2) ** (E - 45)
+    rng = np.random.default_rng(7 + f)
+    top = np.nextafter(np.float32(2.0 ** (E - 1)), np.float32(0))
+    lhg = (ctypes.c_int32 * 2)()
+    cases = [np.array([-top] + [top] * 6, dtype=np.float32), np.array([top] + [-top] * 6, dtype=np.float32),
+             np.zeros(7, dtype=np.float32), np.array([top] * 7, dtype=np.float32)]
+    for _ in range(3000):
+        e = rng.uniform(E - 22, E - 1, 7)
+        s = rng.choice([-1.0, 1.0], 7) if rng.random() < 0.5 else np.ones(7)
+        v = (2.0 ** e * s).astype(np.float32)
+        v[rng.random(7) < 0.1] = 0.0
+        cases.append(v)
+    for v in cases:
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        assert lib.host_r32_laplacian(v.ctypes.data, f, lhg) == 1
+        fr = [Fraction(float(x)) for x in v]
+        L = sum(fr[1:]) - 6 * fr[0]
+        assert (lhg[0] * 2 ** 23 + lhg[1]) * q2 == L, v
+        assert abs(lhg[0]) <= 12 * 2 ** 21 and abs(lhg[1]) <= 12 * 2 ** 22
+
+
+def test_r32_sum_of_squares_is_exact_then_rounded_once(host_lib):
+    lib = _r32_bind(host_lib)
+    f = 127
+    E = f - 125
+    q2 = Fraction(2) ** (E - 45)
+    rng = np.random.default_rng(11)
+    top = np.nextafter(np.float32(2.0 ** (E - 1)), np.float32(0))
+    # 2048 cells (the most one thread sums): extreme terms, near-cancelling
+    # ones and random ones
+    n = 2048
+    v = (2.0 ** rng.uniform(E - 22, E - 1, (n, 7)) * rng.choice([-1.0, 1.0], (n, 7))).astype(np.float32)
+    v[:512, 0] = -top
+    v[:512, 1:] = top
+    v[512:1024, 1:] = v[512:1024, :1]  # L = 0
+    v[1024:1100, 1] = np.nextafter(v[1024:1100, 1], np.float32(0))  # L = one spacing
+    v = np.ascontiguousarray(v)
+    acc3 = (ctypes.c_int64 * 3)()
+    out = ctypes.c_double()
+    assert lib.host_r32_sum_squares(v.ctypes.data, n, f, acc3, ctypes.byref(out)) == 1
+    exact = Fraction(0)
+    for row in v:
+        fr = [Fraction(float(x)) for x in row]
+        exact += (sum(fr[1:]) - 6 * fr[0]) ** 2
+    assert out.value == float(exact)
+    assert (acc3[0] * 2 ** 46 + acc3[1] * 2 ** 24 + acc3[2]) * q2 * q2 == exact
+    assert max(abs(acc3[0]), abs(acc3[1]), abs(acc3[2])) < 2 ** 63
+    # a value outside the window makes the sum report itself inexact
+    v[5, 3] = np.float32(2.0 ** (E - 30) * 1.3)
+    assert lib.host_r32_sum_squares(v.ctypes.data, n, f, acc3, ctypes.byref(out)) == 0
+
+
+def test_r32_combine_is_the_128_bit_sum(host_lib):
+    lib = _r32_bind(host_lib)
+    rng = np.random.default_rng(3)
+    abc = (ctypes.c_int64 * 3)()
+    lohi = (ctypes.c_uint64 * 2)()
+    for _ in range(2000):
+        vals = [int(rng.integers(-2 ** 62, 2 ** 62)) for _ in range(3)]
+        if rng.random() < 0.3:
+            vals[int(rng.integers(0, 3))] = int(rng.choice([2 ** 63 - 1, -2 ** 63, 0, -1]))
+        abc[0], abc[1], abc[2] = vals
+        lib.host_r32_combine(abc, lohi)
+        s = (vals[0] * 2 ** 46 + vals[1] * 2 ** 24 + vals[2]) % 2 ** 128
+        assert lohi[0] + 2 ** 64 * lohi[1] == s, vals
