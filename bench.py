@@ -310,8 +310,12 @@ def run_ours(a, rank, world, local, pg):
     u0 = synth.grid_uniform01(0, *g)
     if a.dtype == "f32":
         u0 = u0.astype(np.float32)
-    host_in = torch.from_numpy(u0.reshape(-1)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
+    # host buffers from the library's allocator (huge-page backed, registered);
+    # base-page pinned buffers (torch) for the comparison leg
+    h_in = _lib.host_array(ncell, np_dt)
+    h_in[:] = u0.reshape(-1)
+    host_in = torch.from_numpy(h_in)
+    host_out = torch.from_numpy(_lib.host_array(ncell, np_dt))
     dev_u0 = host_in.to(f"cuda:{local}")
     rho = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
 
@@ -369,63 +373,78 @@ def run_ours(a, rank, world, local, pg):
         e2e = None
         if not a.no_e2e:
             e2e_steps = max(1, min(a.steps, 3))
-            parts = []  # host seconds per step: write (copy in, check, scatter), iterate + residual, read
-
-            def host_write():
-                if a.dtype == "f32":
-                    _lib.jac_write_f32(J.h, host_in.numpy())
-                else:
-                    _lib.jac_write(J.h, host_in.numpy())
-
-            def host_read():
-                if a.dtype == "f32":
-                    _lib.jac_read_f32(J.h, host_out.numpy())
-                else:
-                    _lib.jac_read(J.h, host_out.numpy())
-
-            # set-up, as a caller would do it once: the library's staging
-            # buffer for host copies is allocated by the first host write
-            host_write()
-            host_read()
             nbytes = ncell * np.dtype(np_dt).itemsize
-            # the link's own rate for the same pinned buffers (a plain copy)
-            dev_tmp = torch.empty_like(dev_u0)
-            torch.cuda.synchronize()
-            tc = time.perf_counter()
-            dev_tmp.copy_(host_in, non_blocking=True)
-            torch.cuda.synchronize()
-            tc1 = time.perf_counter()
-            host_out.copy_(dev_tmp, non_blocking=True)
-            torch.cuda.synchronize()
-            tc2 = time.perf_counter()
-            del dev_tmp
-            barrier(pg)
-            torch.cuda.synchronize()
-            # no clock sampler here: nvidia-smi's queries stall host copies by
-            # about 10 ms at random (measured on GB300: a plain pinned copy of
-            # 1 GiB takes 5.1-5.6 ms alone and 10-20 ms while nvidia-smi polls)
-            t0 = time.perf_counter()
-            for _ in range(e2e_steps):
-                t = time.perf_counter()
+
+            def e2e_leg(hin, hout):
+                parts = []  # host seconds per step: write (copy in, check, scatter), iterate + residual, read
+
+                def host_write():
+                    if a.dtype == "f32":
+                        _lib.jac_write_f32(J.h, hin.numpy())
+                    else:
+                        _lib.jac_write(J.h, hin.numpy())
+
+                def host_read():
+                    if a.dtype == "f32":
+                        _lib.jac_read_f32(J.h, hout.numpy())
+                    else:
+                        _lib.jac_read(J.h, hout.numpy())
+
+                # set-up, as a caller would do it once: the library's staging
+                # buffer for host copies is allocated by the first host write
                 host_write()
-                t1 = time.perf_counter()
-                J.iterate(a.iters)
-                r = J.residual()
-                t2 = time.perf_counter()
                 host_read()
-                parts.append((t1 - t, t2 - t1, time.perf_counter() - t2))
-            torch.cuda.synchronize()
-            e2e_wall = max_over_ranks(pg, time.perf_counter() - t0)
-            tot = np.sum(np.array(parts), axis=0)
-            e2e = {"value": world * ncell * a.iters * e2e_steps / e2e_wall, "unit": UNIT,
-                   "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
-                   "residual": r,
-                   "ms_per_step": {k: round(1e3 * v / e2e_steps, 2)
-                                   for k, v in zip(("write", "iterate_and_residual", "read"), tot)},
-                   "write_read_ms_each_step": [[round(1e3 * w, 2), round(1e3 * rd, 2)] for w, _, rd in parts],
-                   "host_buffers_pinned": bool(host_in.is_pinned() and host_out.is_pinned()),
-                   "plain_copy_gb_per_s": {"h2d": round(nbytes / (tc1 - tc) / 1e9, 1),
-                                           "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)}}
+                # the link's own rate for the same pinned buffers (a plain copy)
+                dev_tmp = torch.empty_like(dev_u0)
+                torch.cuda.synchronize()
+                tc = time.perf_counter()
+                dev_tmp.copy_(hin, non_blocking=True)
+                torch.cuda.synchronize()
+                tc1 = time.perf_counter()
+                hout.copy_(dev_tmp, non_blocking=True)
+                torch.cuda.synchronize()
+                tc2 = time.perf_counter()
+                del dev_tmp
+                barrier(pg)
+                torch.cuda.synchronize()
+                # no clock sampler here: nvidia-smi's queries stall host copies
+                # by about 10 ms at random (measured on GB300: a plain pinned
+                # copy of 1 GiB takes 5.1-5.6 ms alone and 10-20 ms while
+                # nvidia-smi polls)
+                t0 = time.perf_counter()
+                for _ in range(e2e_steps):
+                    t = time.perf_counter()
+                    host_write()
+                    t1 = time.perf_counter()
+                    J.iterate(a.iters)
+                    r = J.residual()
+                    t2 = time.perf_counter()
+                    host_read()
+                    parts.append((t1 - t, t2 - t1, time.perf_counter() - t2))
+                torch.cuda.synchronize()
+                wall = max_over_ranks(pg, time.perf_counter() - t0)
+                tot = np.sum(np.array(parts), axis=0)
+                return {"value": world * ncell * a.iters * e2e_steps / wall, "unit": UNIT,
+                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes + 8, "steps": e2e_steps,
+                        "residual": r,
+                        "ms_per_step": {k: round(1e3 * v / e2e_steps, 2)
+                                        for k, v in zip(("write", "iterate_and_residual", "read"), tot)},
+                        "write_read_ms_each_step": [[round(1e3 * w, 2), round(1e3 * rd, 2)] for w, _, rd in parts],
+                        "host_buffers_pinned": bool(hin.is_pinned() and hout.is_pinned()),
+                        "plain_copy_gb_per_s": {"h2d": round(nbytes / (tc1 - tc) / 1e9, 1),
+                                                "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)}}
+
+            e2e = e2e_leg(host_in, host_out)
+            e2e["host_buffers"] = "jac_host_alloc (transparent huge pages, registered)"
+            # the same with base-page pinned buffers: each copy after a long
+            # launch then repeats its page translations (one per 64 KiB page)
+            base_in = host_in.clone().pin_memory()
+            base_out = torch.empty_like(base_in).pin_memory()
+            b_leg = e2e_leg(base_in, base_out)
+            e2e["base_page_pinned_buffers"] = {k: b_leg[k] for k in ("value", "ms_per_step",
+                                                                     "write_read_ms_each_step",
+                                                                     "plain_copy_gb_per_s")}
+            del base_in, base_out
 
         # ---- other issue forms on the same grid (fewer iterations)
         forms = None

@@ -9,6 +9,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -134,6 +135,8 @@ _SIGS = {
     "jac_residual": ([ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "jac_residual_device": ([ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "jac_iterate_residual": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
+    "jac_host_alloc": ([ctypes.c_size_t], ctypes.c_void_p),
+    "jac_host_free": ([ctypes.c_void_p], ctypes.c_int),
     "jac_sync": ([ctypes.c_void_p], ctypes.c_int),
     "jac_info": ([ctypes.c_void_p, ctypes.POINTER(jac_info_t)], ctypes.c_int),
     "jac_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -299,6 +302,28 @@ def jac_residual(h) -> float:
 
 def jac_residual_device(h, dev_ptr: int) -> None:
     _check(load().jac_residual_device(h, ctypes.c_void_p(dev_ptr)), "jac_residual_device")
+
+
+def jac_host_alloc(nbytes: int) -> int:
+    p = load().jac_host_alloc(int(nbytes))
+    if not p:
+        raise JacError(JAC_ENOMEM, "jac_host_alloc", jac_last_error())
+    return p
+
+
+def jac_host_free(ptr: int) -> None:
+    _check(load().jac_host_free(ctypes.c_void_p(ptr)), "jac_host_free")
+
+
+def host_array(n: int, dtype=np.float64) -> np.ndarray:
+    """A numpy array of n values in jac_host_alloc memory (freed with the
+    last array or tensor viewing it)."""
+    dt = np.dtype(dtype)
+    nbytes = max(1, n * dt.itemsize)
+    ptr = jac_host_alloc(nbytes)
+    buf = (ctypes.c_char * nbytes).from_address(ptr)
+    weakref.finalize(buf, jac_host_free, ptr)
+    return np.frombuffer(buf, dtype=dt, count=n)
 
 
 def jac_iterate_residual(h, n_iters: int, every: int, dev_ptr: int) -> None:

@@ -10,6 +10,7 @@
 // high-priority streams, the update on a low-priority stream, one set per
 // block).
 #include <cuda_runtime.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <cmath>
@@ -1201,6 +1202,105 @@ const char* jac_strerror(int code)
 }
 
 const char* jac_last_error(void) { return g_last_error.c_str(); }
+
+// ---- host buffers
+namespace {
+
+std::mutex g_host_mu;
+struct HostBuf {
+    size_t len;
+    bool mapped;  // huge-page mapping (munmap) rather than cudaHostAlloc
+};
+std::map<void*, HostBuf> g_host;
+
+// The transparent huge page size when the kernel offers them on request
+// (mode "always" or "madvise"), else 0.
+size_t thp_bytes()
+{
+    static const size_t hp = [] {
+        size_t v = 0;
+        if (FILE* f = fopen("/sys/kernel/mm/transparent_hugepage/enabled", "r")) {
+            char buf[128] = {0};
+            const bool on = fgets(buf, sizeof buf, f) && (strstr(buf, "[always]") || strstr(buf, "[madvise]"));
+            fclose(f);
+            if (on) {
+                if (FILE* g = fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+                    unsigned long long x = 0;
+                    if (fscanf(g, "%llu", &x) == 1) v = (size_t)x;
+                    fclose(g);
+                }
+            }
+        }
+        return v;
+    }();
+    return hp;
+}
+
+constexpr size_t kHostHugeMin = size_t(64) << 20;  // smaller requests get base pages
+
+}  // namespace
+
+void* jac_host_alloc(size_t bytes)
+{
+    if (bytes == 0) {
+        fail(JAC_EINVAL, "jac_host_alloc: zero bytes");
+        return nullptr;
+    }
+    const size_t hp = thp_bytes();
+    if (hp && bytes >= kHostHugeMin) {
+        const size_t len = (bytes + hp - 1) / hp * hp;
+        void* raw = mmap(nullptr, len + hp, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+        if (raw != MAP_FAILED) {
+            // keep the huge-page-aligned part
+            const uintptr_t r = (uintptr_t)raw, a = (r + hp - 1) / hp * hp;
+            if (a > r) munmap(raw, a - r);
+            if (r + len + hp > a + len) munmap((void*)(a + len), r + len + hp - (a + len));
+            void* p = (void*)a;
+            madvise(p, len, MADV_HUGEPAGE);
+            memset(p, 0, len);  // fault the pages in (as huge pages) before they are pinned
+            const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
+            if (e == cudaSuccess) {
+                std::lock_guard<std::mutex> lock(g_host_mu);
+                g_host[p] = HostBuf{len, true};
+                return p;
+            }
+            munmap(p, len);
+            cuda_fail(e, "jac_host_alloc: cudaHostRegister");
+            return nullptr;
+        }
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        cuda_fail(e, "jac_host_alloc: cudaHostAlloc");
+        return nullptr;
+    }
+    memset(p, 0, bytes);
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    g_host[p] = HostBuf{bytes, false};
+    return p;
+}
+
+int jac_host_free(void* p)
+{
+    if (!p) return JAC_OK;
+    HostBuf b;
+    {
+        std::lock_guard<std::mutex> lock(g_host_mu);
+        auto it = g_host.find(p);
+        if (it == g_host.end()) return fail(JAC_EINVAL, "jac_host_free: not a pointer from jac_host_alloc");
+        b = it->second;
+        g_host.erase(it);
+    }
+    if (b.mapped) {
+        const cudaError_t e = cudaHostUnregister(p);
+        munmap(p, b.len);
+        if (e != cudaSuccess) return cuda_fail(e, "jac_host_free: cudaHostUnregister");
+        return JAC_OK;
+    }
+    CU(cudaFreeHost(p), "jac_host_free: cudaFreeHost");
+    return JAC_OK;
+}
 
 int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void* user)
 {

@@ -55,6 +55,9 @@ def test_strerror_and_invalid_arguments_without_gpu():
     assert lib.jac_iterate(None, 1) == _lib.JAC_EINVAL
     assert lib.jac_iterate_residual(None, 1, 1, None) == _lib.JAC_EINVAL
     assert lib.jac_destroy(None) == _lib.JAC_OK
+    assert lib.jac_host_free(None) == _lib.JAC_OK
+    assert lib.jac_host_free(ctypes.c_void_p(4096)) == _lib.JAC_EINVAL
+    assert not lib.jac_host_alloc(0)
 
 
 def test_allocator_hook_requires_both_functions():
