@@ -260,14 +260,16 @@ int jac_read_device(jac_ctx *h, void *dev, size_t n_cells, int32_t dtype);
 int jac_iterate(jac_ctx *h, int64_t n_iters);
 
 /* rho(u) = sqrt( sum over interior cells of L^2 ),
- * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly. Binary64 grids:
- * L is rounded once to binary64 and accumulated in binary64 by fused
- * multiply-adds (acc = fma(L, L, acc)), per-thread sums combined by a fixed
- * tree per work unit. Binary32 grids: L^2 is summed exactly per work unit
- * and rounded once (a unit with a value more than 21 binades below the
- * grid's largest, or of odd x extent, sums it exactly per thread and combines
- * the rounded thread sums by a fixed tree). The units' partials are summed in
- * unit order. That
+ * L = xm + xp + ym + yp + zm + zp - 6c evaluated exactly. Per work unit,
+ * L^2 is summed exactly and rounded once to binary64 when every value the
+ * unit reads lies within the exact range of the integer form: binary64
+ * grids, positive values within nine binades of the grid's largest
+ * exponent, the grid's largest value between 2^-440 and 2^460 or so;
+ * binary32 grids, values within 21 binades of the grid's largest, that
+ * largest between 2^-100 and 2^125. Other units (and blocks of odd x extent)
+ * round L once to binary64 and sum the squares per thread (binary64: fused
+ * multiply-adds; binary32: exactly, then rounded), combining the thread
+ * sums by a fixed tree. The units' partials are summed in unit order. That
  * order is fixed by the grid, the block dims, the tile width and z depth, and
  * the unit split the runtime derives from the device's SM count and
  * occupancy: repeated calls on one device and configuration give the same
@@ -286,12 +288,13 @@ int jac_residual_device(jac_ctx *h, double *dev_out);
  * residual of the grid before every `every`-th of them (every >= 1):
  * dev_out[j] = rho(u^(k0 + j * every)) for j = 0 .. ceil(n_iters / every) - 1,
  * k0 the iteration count at the call; dev_out is device memory of that many
- * doubles (unused when n_iters = 0). Binary32 contexts in the fused and
- * graph-fused modes compute each residual inside the update launch that reads
- * that grid (kernel fusion, Section III-D1: one launch, no second pass over
- * the grid); other modes and binary64 contexts enqueue jac_residual_device
- * before the iteration. Either way dev_out[j] has the bits jac_residual gives
- * for that grid. Stream-ordered, no host sync; JAC_EINVAL for n_iters < 0,
+ * doubles (unused when n_iters = 0). In the fused and graph-fused modes
+ * (binary32, or binary64 with JAC_ARITH_EXACT) each residual comes from the
+ * update launch that reads that grid (kernel fusion, Section III-D1: one
+ * launch, no second pass over the grid); other modes and the sequential rule
+ * enqueue jac_residual_device before the iteration. Either way dev_out[j] has
+ * the bits jac_residual gives for that grid. Stream-ordered, no host sync;
+ * JAC_EINVAL for n_iters < 0,
  * every < 1 or a null dev_out, JAC_ESTATE without a resident grid. */
 int jac_iterate_residual(jac_ctx *h, int64_t n_iters, int64_t every, double *dev_out);
 

@@ -22,7 +22,9 @@
 //                                 iteration of its own and neighbouring blocks
 //                                 (the device form of the per-iteration
 //                                 reference numbers of Section II-A),
-//   k_residual / k_sum_partials   the residual norm, deterministic order,
+//   k_narrow_residual /           the residual norm (binary64 / binary32),
+//   k_ring_residual               alone or inside an update iteration,
+//                                 deterministic order,
 //   k_scatter / k_gather          dense x-fastest arrays <-> block storage.
 #include <cuda_runtime.h>
 
@@ -1227,10 +1229,24 @@ __device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* des
 // block's Dirichlet values, and never above the grid's frame. At its end the
 // tile stores the bound of its own outputs in *uout. The frame only scales
 // the integers, so the results do not depend on it.
-template <bool PULL, bool CG, int TW>
+// What the residual modes return per thread: the exact sum of L^2 of its
+// cells in units of 2^(2 (eref - 1084)) (192 bits), and whether a step of
+// the tile took the 96-bit frame (the unit's residual is then taken again by
+// the two-plane engine).
+struct R64Out {
+    uint64_t q0, q1, q2;
+    bool bad;
+};
+
+// RM (residual mode): 0 the update only; 1 the update and, from the same
+// 64-bit sums, L = S - 7c of the grid it reads; 2 the residual terms only
+// (nothing is written). The residual modes are called with the grid's frame
+// (uin null), so whether a unit falls back does not depend on the bounds.
+template <bool PULL, bool CG, int TW, int RM = 0>
 __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* __restrict__ desc,
                                     const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
-                                    unsigned char* smraw, SlowList* slow, const uint32_t* uin, uint32_t* uout)
+                                    unsigned char* smraw, SlowList* slow, const uint32_t* uin, uint32_t* uout,
+                                    R64Out* ro = nullptr)
 {
     using T = double;
     using W = frame::W96;
@@ -1375,6 +1391,13 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     // the current step's two new own planes (k+1, k+2) as frame integers
     uint64_t c0A = 0u, c0B = 0u, c1A = 0u, c1B = 0u;
     bool g0 = true, g1 = true;
+    // residual modes: this thread's sum of L^2 and whether a step fell back
+    [[maybe_unused]] uint64_t rq0 = 0u, rq1 = 0u, rq2 = 0u;
+    [[maybe_unused]] bool rbad = false;
+    // L = S - 7c: |L| < 6 * 2^61, exact in two's complement
+    [[maybe_unused]] auto lsq = [&](uint64_t S, uint64_t c) {
+        frame::add_square((int64_t)(S - 7u * c), rq0, rq1, rq2);
+    };
     // the 64-bit sums and means of planes k (buffer n0) and k+1 (n1)
     auto narrow = [&](const uint64_t* n0, const uint64_t* n1, bool two) {
         const uint64_t uA = cA + c0A, uB = cB + c0B;
@@ -1382,20 +1405,36 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
             const ulonglong2 ym = *(const ulonglong2*)(n0 + own - kSW), yp = *(const ulonglong2*)(n0 + own + kSW);
             const uint64_t SA = uA + cB + n0[own - 1] + ym.x + yp.x + zmA;
             const uint64_t SB = uB + cA + n0[own + 2] + ym.y + yp.y + zmB;
-            const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
-            if (k1) {
-                *(double2*)out = o;
-                lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+            if constexpr (RM != 2) {
+                const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
+                if (k1) {
+                    *(double2*)out = o;
+                    lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+                }
+            }
+            if constexpr (RM != 0) {
+                if (k1) {
+                    lsq(SA, cA);
+                    lsq(SB, cB);
+                }
             }
         }
         if (two) {
             const ulonglong2 ym = *(const ulonglong2*)(n1 + own - kSW), yp = *(const ulonglong2*)(n1 + own + kSW);
             const uint64_t SA = uA + c0B + n1[own - 1] + ym.x + yp.x + c1A;
             const uint64_t SB = uB + c0A + n1[own + 2] + ym.y + yp.y + c1B;
-            const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
-            if (k1) {
-                *(double2*)(out + plane) = o;
-                lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+            if constexpr (RM != 2) {
+                const double2 o = make_double2(nframe::mean7(SA, nscale), nframe::mean7(SB, nscale));
+                if (k1) {
+                    *(double2*)(out + plane) = o;
+                    lzm = min(lzm, min(clz32((uint32_t)(SA >> 32)), clz32((uint32_t)(SB >> 32))));
+                }
+            }
+            if constexpr (RM != 0) {
+                if (k1) {
+                    lsq(SA, c0A);
+                    lsq(SB, c0B);
+                }
             }
         }
     };
@@ -1498,7 +1537,8 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
                 fall = false;
             }
         }
-        if (fall) {
+        if constexpr (RM != 0) rbad |= fall;
+        if (RM != 2 && fall) {
             // the step in the 96-bit frame from the raw values: plane k in the
             // first pair of 64-bit planes, plane k+1 in the second (every
             // thread has passed the step's barrier, so no 64-bit plane is read
@@ -1592,6 +1632,16 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         if (k >= z1) break;
     }
     cp_async_wait<0>();
+    if constexpr (RM != 0) {
+        ro->q0 = rq0;
+        ro->q1 = rq1;
+        ro->q2 = rq2;
+        ro->bad = rbad;
+    }
+    if constexpr (RM == 2) {
+        __syncthreads();  // the shared memory is free for the caller
+        return;
+    }
     n2_slow_cells<PULL, CG, TW>(pool, desc, d, b, p, x0, y0, z0, z1, k1, x, y, slow, eref, lzm);
     if (uout) {
         // every output's exponent field is at most eref - (the least count);
@@ -2280,49 +2330,50 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
     }
 }
 
-// Residual: per CTA the sum over its tile of L^2 (L the exact Laplacian term
-// rounded once), in a fixed order (per thread over k, then a fixed tree).
-template <typename T>
-__global__ void __launch_bounds__(kNT<T>, kMinCTAs<T>) k_residual(const T* pool, const BlockDesc* desc,
-                                                          const int32_t* frame_e, const TileUnit* units, int p,
-                                                          double* partials)
+// ------------------------------------------------------------ residual
+// The residual from the two-column engines' residual modes: per work unit
+// the exact sum of L^2 (binary32: split words, 128-bit combination; binary64:
+// the 64-bit frame's S - 7c, 192-bit squares), rounded once to binary64.
+// Units these cannot take (odd x extent, a value outside the exact range, a
+// frame out of range) take the two-plane engine (tile_engine_pair's residual
+// ops), whose per-unit partial is rounded per thread and summed by a fixed
+// tree. The partials are summed by the last unit to finish in a fixed order,
+// so the grid's rho is the same bits in every form that produces it.
+
+// partials[unit] = part (thread 0's); with `out` set, the last unit to
+// finish (a fence, then an atomic count) writes sqrt of the sum of the
+// partials there (256 strided sums in unit order, then a fixed tree) and
+// clears *count, which is zero at every launch.
+__device__ void finish_residual(double part, double* partials, int nunits, unsigned* count, double* out, int* s_last)
 {
-    __shared__ SlowList slow;
-    __shared__ double red[kNT<T>];
-    const TileUnit u = units[blockIdx.x];
-    double acc = 0.0;
-    with_tw(u.tw, [&](auto tw_c) {
-        constexpr int TW = decltype(tw_c)::value;
-        constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
-        acc = tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block, p,
-                                                                  u.x0, u.y0, u.z0, u.z1, jac_dyn_sm, &slow);
-        {
-            // a unit is two engine tiles tall
-            __syncthreads();
-            acc += tile_engine_pair<T, OPR, true, false, kRingRes, TW>(const_cast<T*>(pool), desc, frame_e, u.block,
-                                                                       p, u.x0, u.y0 + kNT<T> / TW, u.z0, u.z1,
-                                                                       jac_dyn_sm, &slow);
-        }
-    });
     const int tid = threadIdx.x;
-    red[tid] = acc;
+    if (tid == 0) {
+        partials[blockIdx.x] = part;
+        if (out) {
+            __threadfence();
+            *s_last = atomicAdd(count, 1u) == (unsigned)(nunits - 1);
+        }
+    }
+    if (!out) return;
     __syncthreads();
-    for (int s = kNT<T> / 2; s > 0; s >>= 1) {
+    if (!*s_last) return;
+    __threadfence();
+    double* const red = (double*)jac_dyn_sm;
+    if (tid < 256) {
+        double acc = 0.0;
+        for (int i = tid; i < nunits; i += 256) acc = acc + __ldcg(partials + i);
+        red[tid] = acc;
+    }
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
         if (tid < s) red[tid] = red[tid] + red[tid + s];
         __syncthreads();
     }
-    if (tid == 0) partials[blockIdx.x] = red[0];
+    if (tid == 0) {
+        out[0] = sqrt(red[0]);
+        *count = 0u;
+    }
 }
-
-// ------------------------------------------------ binary32 residual in the ring
-// The binary32 residual from the two-column ring engine (residual modes): per
-// work unit the exact sum of L^2 (split words, 128-bit combination, one
-// rounding to binary64). Units the split cannot take (odd x extent, a value
-// outside its exact range, a grid frame out of range) take the 64-bit-frame
-// engine of k_residual, whose per-unit partial is rounded per thread and
-// summed by a fixed tree. The partials are summed by the last unit to finish,
-// in k_sum_partials' order, so the grid's rho is the same bits in every form
-// that produces it.
 
 // The unit's partial from the threads' exact sums (valid in thread 0).
 __device__ double r32_unit_partial(const r32::Acc& a, int E, unsigned char* smraw)
@@ -2357,18 +2408,20 @@ __device__ double r32_unit_partial(const r32::Acc& a, int E, unsigned char* smra
     return part;
 }
 
-// The 64-bit-frame engine's partial of a unit (valid in thread 0): the two
-// engine tiles, then a fixed tree over the threads.
-template <int TW>
-__device__ __noinline__ double r32_fallback_partial(float* pool, const BlockDesc* desc, const int32_t* frame_e, int b, int p,
-                                       int x0, int y0, int z0, int z1, SlowList* slow)
+// The two-plane engine's partial of a unit (valid in thread 0): the two
+// engine tiles, then a fixed tree over the threads (binary32 grids: L^2
+// summed exactly per thread in a 64-bit frame; binary64: L rounded once,
+// fused multiply-adds).
+template <typename T, int TW>
+__device__ __noinline__ double res_fallback_partial(T* pool, const BlockDesc* desc, const int32_t* frame_e, int b,
+                                                    int p, int x0, int y0, int z0, int z1, SlowList* slow)
 {
-    using T = float;
-    double acc = tile_engine_pair<T, OP_RES32, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1,
-                                                                          jac_dyn_sm, slow);
+    constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
+    double acc = tile_engine_pair<T, OPR, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1,
+                                                                     jac_dyn_sm, slow);
     __syncthreads();
-    acc += tile_engine_pair<T, OP_RES32, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0 + kNT<T> / TW,
-                                                                    z0, z1, jac_dyn_sm, slow);
+    acc += tile_engine_pair<T, OPR, true, false, kRingRes, TW>(pool, desc, frame_e, b, p, x0, y0 + kNT<T> / TW, z0,
+                                                               z1, jac_dyn_sm, slow);
     __syncthreads();
     double* const red = (double*)jac_dyn_sm;
     const int tid = threadIdx.x;
@@ -2396,7 +2449,6 @@ __global__ void __launch_bounds__(kNT<float>, kMinCTAs<float>)
     __shared__ int s_last;
     const TileUnit u = units[blockIdx.x];
     const BlockDesc& d = desc[u.block];
-    const int tid = threadIdx.x;
     double part = 0.0;
     with_tw(u.tw, [&](auto tw_c) {
         constexpr int TW = decltype(tw_c)::value;
@@ -2412,35 +2464,90 @@ __global__ void __launch_bounds__(kNT<float>, kMinCTAs<float>)
             tile_engine_ring<float, true, false, TW>(pool, desc, u.block, p, u.x0, u.y0 + kNT<float> / TW, u.z0,
                                                      u.z1, jac_dyn_sm);
         }
-        if (fall) part = r32_fallback_partial<TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
+        if (fall)
+            part = res_fallback_partial<float, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
     });
+    finish_residual(part, partials, nunits, count, out, &s_last);
+}
+
+// The exact partial of a binary64 unit from the threads' 192-bit sums of
+// L^2 (units of 2^scale), rounded once (valid in thread 0).
+__device__ double r64_unit_partial(const R64Out& r, int scale, unsigned char* smraw)
+{
+    uint64_t a0 = r.q0, a1 = r.q1, a2 = r.q2;
+    auto add3 = [](uint64_t& x0, uint64_t& x1, uint64_t& x2, uint64_t y0, uint64_t y1, uint64_t y2) {
+        const uint64_t s0 = x0 + y0;
+        const uint64_t c0 = s0 < y0 ? 1u : 0u;
+        const uint64_t t1 = x1 + y1;
+        const uint64_t c1 = t1 < y1 ? 1u : 0u;
+        const uint64_t s1 = t1 + c0;
+        const uint64_t c2 = s1 < t1 ? 1u : 0u;
+        x0 = s0;
+        x1 = s1;
+        x2 += y2 + c1 + c2;
+    };
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t b0 = __shfl_down_sync(0xffffffffu, a0, o), b1 = __shfl_down_sync(0xffffffffu, a1, o),
+                       b2 = __shfl_down_sync(0xffffffffu, a2, o);
+        add3(a0, a1, a2, b0, b1, b2);
+    }
+    uint64_t* const w = (uint64_t*)smraw;  // [warps][3]
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if ((tid & 31) == 0) {
+        w[3 * (tid >> 5)] = a0;
+        w[3 * (tid >> 5) + 1] = a1;
+        w[3 * (tid >> 5) + 2] = a2;
+    }
+    __syncthreads();
+    double part = 0.0;
     if (tid == 0) {
-        partials[blockIdx.x] = part;
-        if (out) {
-            __threadfence();
-            s_last = atomicAdd(count, 1u) == (unsigned)(nunits - 1);
+        uint64_t s0 = 0u, s1 = 0u, s2 = 0u;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) add3(s0, s1, s2, w[3 * i], w[3 * i + 1], w[3 * i + 2]);
+        part = frame::u192_to_double_scaled(s0, s1, s2, scale);
+    }
+    __syncthreads();
+    return part;
+}
+
+// RM 1: one binary64 iteration of the correctly rounded mean (the bits of
+// k_fused_step, which it replaces, unit bounds included) that also returns
+// the residual of the grid it reads; RM 2: the residual only. The 64-bit
+// frame is the grid's: a unit with a step outside it, of odd x extent, or
+// whose sum of squares could leave the normal range (scale outside
+// [-1000, 800]) takes the two-plane engine. Partials and the grid's sum as in
+// k_ring_residual.
+template <int RM>
+__global__ void __launch_bounds__(kNT<double>, 2)
+    k_narrow_residual(double* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits,
+                      int p, uint32_t* uexp, int ucap, double* partials, unsigned* count, double* out)
+{
+    __shared__ SlowList slow;
+    __shared__ int s_last;
+    const TileUnit u = units[blockIdx.x];
+    const BlockDesc& d = desc[u.block];
+    double part = 0.0;
+    with_tw(u.tw, [&](auto tw_c) {
+        constexpr int TW = decltype(tw_c)::value;
+        uint32_t* const uout = RM == 1 ? uexp + (int64_t)(p ^ 1) * ucap + blockIdx.x : nullptr;
+        bool fall = true;
+        if ((d.ext[0] & 1) == 0) {
+            R64Out ro;
+            tile_engine_narrow2<true, false, TW, RM>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1,
+                                                     jac_dyn_sm, &slow, nullptr, uout, &ro);
+            const int scale = 2 * (frame_e[d.inst] + 1 - 1084);
+            fall = __syncthreads_or(ro.bad) || scale < -1000 || scale > 800;
+            if (!fall) part = r64_unit_partial(ro, scale, jac_dyn_sm);
+        } else if constexpr (RM == 1) {
+            exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow, nullptr,
+                                        uout);
+            __syncthreads();
         }
-    }
-    if (!out) return;
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // k_sum_partials' order: 256 strided sums, then a fixed tree
-    double* const red = (double*)jac_dyn_sm;
-    if (tid < 256) {
-        double acc = 0.0;
-        for (int i = tid; i < nunits; i += 256) acc = acc + __ldcg(partials + i);
-        red[tid] = acc;
-    }
-    __syncthreads();
-    for (int s = 128; s > 0; s >>= 1) {
-        if (tid < s) red[tid] = red[tid] + red[tid + s];
-        __syncthreads();
-    }
-    if (tid == 0) {
-        out[0] = sqrt(red[0]);
-        *count = 0u;
-    }
+        if (fall)
+            part = res_fallback_partial<double, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow);
+    });
+    finish_residual(part, partials, nunits, count, out, &s_last);
 }
 
 // Per-grid residuals: resident grid i (slot slot[i]) owns partials
@@ -2460,19 +2567,6 @@ __global__ void k_sum_segments(const double* partials, const int32_t* seg, const
     if (threadIdx.x == 0) out[slot[i]] = sqrt(red[0]);
 }
 
-__global__ void k_sum_partials(const double* partials, int n, double* out)
-{
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc = acc + partials[i];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) red[threadIdx.x] = red[threadIdx.x] + red[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = sqrt(red[0]);
-}
 
 // The interior/exterior split of the update (the manual overlap of Section
 // II-A, Fig. 1): the interior region (cells 1 .. b-2 on every axis) reads
@@ -2761,18 +2855,6 @@ static int unit_bytes_max()
     return unit_bytes<T, OP>(7);
 }
 
-template <typename T>
-static int residual_bytes(int tw_mask)
-{
-    if (tw_mask == 0) tw_mask = 7;
-    constexpr int OPR = sizeof(T) == 4 ? OP_RES32 : OP_RES;
-    int n = 0;
-    if (tw_mask & 1) n = std::max(n, pair_engine_bytes<T, OPR, 16, kRingRes>());
-    if (tw_mask & 2) n = std::max(n, pair_engine_bytes<T, OPR, 32, kRingRes>());
-    if (tw_mask & 4) n = std::max(n, pair_engine_bytes<T, OPR, 64, kRingRes>());
-    return n;
-}
-
 template <int TW>
 static constexpr int ring_res_bytes_tw()
 {
@@ -2789,6 +2871,31 @@ static int ring_res_bytes(int tw_mask)
     if (tw_mask & 2) n = std::max(n, ring_res_bytes_tw<32>());
     if (tw_mask & 4) n = std::max(n, ring_res_bytes_tw<64>());
     return n;
+}
+
+template <int TW>
+static constexpr int narrow_res_bytes_tw()
+{
+    constexpr int a = kernel_bytes<double, OP_EXACT, TW>(), b = pair_engine_bytes<double, OP_RES, TW, kRingRes>();
+    constexpr int m = a > b ? a : b;
+    return m > 256 * (int)sizeof(double) ? m : 256 * (int)sizeof(double);
+}
+
+static int narrow_res_bytes(int tw_mask)
+{
+    if (tw_mask == 0) tw_mask = 7;
+    int n = 0;
+    if (tw_mask & 1) n = std::max(n, narrow_res_bytes_tw<16>());
+    if (tw_mask & 2) n = std::max(n, narrow_res_bytes_tw<32>());
+    if (tw_mask & 4) n = std::max(n, narrow_res_bytes_tw<64>());
+    return n;
+}
+
+cudaError_t launch_fused_residual_f64(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s)
+{
+    k_narrow_residual<1><<<a.nunits, kNT<double>, narrow_res_bytes(a.tw_mask), s>>>(
+        (double*)a.pool, a.desc, a.frame, a.units, a.nunits, p, a.uexp, a.units_cap, partials, a.rcount, dev_out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fused_residual_f32(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s)
@@ -2858,7 +2965,8 @@ cudaError_t prepare_kernels()
     JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes_max<double, OP_EXACT>()));
     JAC_ALLOW((k_persistent<double, OP_SEQ, false>), (unit_bytes_max<double, OP_SEQ>()));
     JAC_ALLOW((k_persistent<float, OP_SEQ, true>), (unit_bytes_max<float, OP_SEQ>()));
-    JAC_ALLOW((k_residual<double>), (residual_bytes<double>(7)));
+    JAC_ALLOW((k_narrow_residual<1>), (narrow_res_bytes(7)));
+    JAC_ALLOW((k_narrow_residual<2>), (narrow_res_bytes(7)));
     JAC_ALLOW((k_ring_residual<1>), (ring_res_bytes(7)));
     JAC_ALLOW((k_ring_residual<2>), (ring_res_bytes(7)));
 #undef JAC_ALLOW
@@ -2889,22 +2997,21 @@ cudaError_t launch_residual_partials(const LaunchArgs& a, int dtype_f32, int p, 
         k_ring_residual<2><<<a.nunits, kNT<float>, ring_res_bytes(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, p, partials, a.rcount, nullptr);
     else
-        k_residual<double><<<a.nunits, kNT<double>, residual_bytes<double>(a.tw_mask), s>>>((const double*)a.pool, a.desc,
-                                                                               a.frame, a.units, p, partials);
+        k_narrow_residual<2><<<a.nunits, kNT<double>, narrow_res_bytes(a.tw_mask), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, a.nunits, p, a.uexp, a.units_cap, partials, a.rcount, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const LaunchArgs& a, int dtype_f32, int p, double* partials, double* out,
                             cudaStream_t s)
 {
-    if (dtype_f32) {  // one launch: the last unit sums the partials
+    // one launch: the last unit sums the partials
+    if (dtype_f32)
         k_ring_residual<2><<<a.nunits, kNT<float>, ring_res_bytes(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, p, partials, a.rcount, out);
-        return cudaGetLastError();
-    }
-    cudaError_t e = launch_residual_partials(a, dtype_f32, p, partials, s);
-    if (e != cudaSuccess) return e;
-    k_sum_partials<<<1, 256, 0, s>>>(partials, a.nunits, out);
+    else
+        k_narrow_residual<2><<<a.nunits, kNT<double>, narrow_res_bytes(a.tw_mask), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, a.nunits, p, a.uexp, a.units_cap, partials, a.rcount, out);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,9 @@ cudaError_t launch_stencil_block(const LaunchArgs& a, int dtype_f32, int arith, 
 // One binary32 update iteration (k_fused_ring's result) that also writes
 // rho of the grid it reads to dev_out (one launch).
 cudaError_t launch_fused_residual_f32(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s);
+// One binary64 iteration of the correctly rounded mean (k_fused_step's result)
+// that also writes rho of the grid it reads to dev_out (one launch).
+cudaError_t launch_fused_residual_f64(const LaunchArgs& a, int p, double* partials, double* dev_out, cudaStream_t s);
 cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int p, cudaStream_t s);
 cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int dtype_f32, int arith, int ctas,
                               cudaStream_t s);

@@ -1542,7 +1542,7 @@ int jac_residual_device(jac_ctx* h, double* dev_out)
     if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
     if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
     CU(launch_residual(h->args(), h->dtype == JAC_F32, h->parity, h->partials, dev_out, h->stream), "residual");
-    h->launches += h->dtype == JAC_F32 ? 1 : 2;
+    h->launches += 1;
     return JAC_OK;
 }
 
@@ -1555,13 +1555,18 @@ int jac_iterate_residual(jac_ctx* h, int64_t n, int64_t every, double* dev_out)
     if (n == 0) return JAC_OK;
     if (!dev_out) return fail(JAC_EINVAL, "null output pointer");
     if (h->hunits.empty()) return fail(JAC_ESTATE, "no resident grid");
-    // binary32 in the fused forms: the residual of u^k comes from the launch
-    // that computes u^(k+1); elsewhere the residual launch precedes the chunk
-    const bool fuse = h->dtype == JAC_F32 && (h->mode == JAC_MODE_FUSED || h->mode == JAC_MODE_GRAPH_FUSED);
+    // the fused forms (binary32, or binary64 with the correctly rounded mean):
+    // the residual of u^k comes from the launch that computes u^(k+1);
+    // elsewhere the residual launch precedes the chunk
+    const bool fused_form = h->mode == JAC_MODE_FUSED || h->mode == JAC_MODE_GRAPH_FUSED;
+    const bool f32 = h->dtype == JAC_F32;
+    const bool fuse = fused_form && (f32 || h->arith == JAC_ARITH_EXACT);
     for (int64_t i = 0, j = 0; i < n; i += every, ++j) {
         const int64_t m = std::min(every, n - i);
         if (fuse) {
-            CU(launch_fused_residual_f32(h->args(), h->parity, h->partials, dev_out + j, h->stream), "fused residual");
+            CU(f32 ? launch_fused_residual_f32(h->args(), h->parity, h->partials, dev_out + j, h->stream)
+                   : launch_fused_residual_f64(h->args(), h->parity, h->partials, dev_out + j, h->stream),
+               "fused residual");
             h->launches += 1;
             h->parity ^= 1;
             h->iters += 1;

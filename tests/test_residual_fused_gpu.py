@@ -1,16 +1,17 @@
-"""The binary32 residual inside the update launch (jac_iterate_residual) and
-the binary32 residual launch that shares its arithmetic, against the oracle.
+"""The residual inside the update launch (jac_iterate_residual) and the
+residual launch that shares its arithmetic, binary32 and binary64, against
+the oracle.
 
-- The grid after the iterations: bit-exact against the binary32 oracle (the
-  update is k_fused_ring's arithmetic).
+- The grid after the iterations: bit-exact against the oracle (binary32; the
+  correctly rounded mean or the left-to-right rule for binary64).
 - rho(u^k): within 1e-12 relative of oracle.residual of the oracle's u^k
   (both are the exact sum of L^2 rounded once, then the per-unit partials
   summed in binary64: a few units of 2^-53 apart).
 - rho(u^k) has the same bits as jac_residual on the same grid in the same
   configuration (one per-unit arithmetic, one summation order).
 Cases: several blocks with ragged tiles, blocks of odd x extent (the
-64-bit-frame fallback engine), values outside the split's exact range,
-frames out of its range, mixed signs.
+two-plane fallback engine), values outside the exact range, frames out of
+it, mixed signs.
 """
 
 import numpy as np
@@ -36,20 +37,24 @@ def _cuda():
     yield
 
 
-def iterate_residual(u0, dims, block, n, every, mode, bc):
+def ctx(dims, block, bc, mode, dtype, arith):
+    return Jacobi3D(dims, block, dtype=dtype, bc=bc, mode=mode, arith=arith if dtype == "f64" else "seq")
+
+
+def iterate_residual(u0, dims, block, n, every, mode, bc, dtype="f32", arith="exact"):
     import torch
 
-    with Jacobi3D(dims, block, dtype="f32", bc=bc, mode=mode) as J:
+    with ctx(dims, block, bc, mode, dtype, arith) as J:
         J.write(u0)
         out = torch.full((max(1, -(-n // every)),), float("nan"), dtype=torch.float64, device="cuda")
         J.iterate_residual(n, every, out)
         J.sync()
-        return J.read(np.float32), out.cpu().numpy()
+        return J.read(np.float32 if dtype == "f32" else np.float64), out.cpu().numpy()
 
 
-def standalone_residuals(u0, dims, block, n, every, mode, bc):
+def standalone_residuals(u0, dims, block, n, every, mode, bc, dtype="f32", arith="exact"):
     rhos = []
-    with Jacobi3D(dims, block, dtype="f32", bc=bc, mode=mode) as J:
+    with ctx(dims, block, bc, mode, dtype, arith) as J:
         J.write(u0)
         for k in range(0, n, every):
             if k:
@@ -58,18 +63,24 @@ def standalone_residuals(u0, dims, block, n, every, mode, bc):
     return np.array(rhos)
 
 
-def check(u0, dims, block, n, every, mode, bc):
-    got, rho = iterate_residual(u0, dims, block, n, every, mode, bc)
-    assert np.array_equal(got, oracle.jacobi_f32(u0, bc, n))
+def oracle_iterate(u, bc, n, dtype, arith):
+    if dtype == "f32":
+        return oracle.jacobi_f32(u, bc, n)
+    return oracle.jacobi(u, bc, n, oracle.RULE_EXACT if arith == "exact" else oracle.RULE_SEQ)
+
+
+def check(u0, dims, block, n, every, mode, bc, dtype="f32", arith="exact"):
+    got, rho = iterate_residual(u0, dims, block, n, every, mode, bc, dtype, arith)
+    assert np.array_equal(got, oracle_iterate(u0, bc, n, dtype, arith))
     ks = list(range(0, n, every))
     assert len(rho) == len(ks)
     uk = u0
     for j, k in enumerate(ks):
         if k:
-            uk = oracle.jacobi_f32(uk, bc, every)
+            uk = oracle_iterate(uk, bc, every, dtype, arith)
         want = oracle.residual(uk, bc)
         assert abs(rho[j] - want) <= 1e-12 * want, (j, k, rho[j], want)
-    assert np.array_equal(rho, standalone_residuals(u0, dims, block, n, every, mode, bc))
+    assert np.array_equal(rho, standalone_residuals(u0, dims, block, n, every, mode, bc, dtype, arith))
     return rho
 
 
@@ -86,6 +97,41 @@ CASES = [
 def test_iterate_residual_matches_oracle_and_standalone(dims, block, mode):
     u0 = synth.grid_uniform01(31, *dims).astype(np.float32)
     check(u0, dims, block, 11, 4, mode, BC_MIXED)  # rho of u^0, u^4, u^8
+
+
+@pytest.mark.parametrize("arith", ["exact", "seq"])
+@pytest.mark.parametrize("mode", FUSED + OTHER)
+@pytest.mark.parametrize("dims,block", CASES)
+def test_iterate_residual_binary64(dims, block, mode, arith):
+    u0 = synth.grid_uniform01(37, *dims)
+    check(u0, dims, block, 11, 4, mode, BC_MIXED, "f64", arith)
+
+
+@pytest.mark.parametrize("mode", FUSED)
+@pytest.mark.parametrize("case", ["spread", "mixed_signs", "huge_frame", "tiny_frame", "zeros"])
+def test_iterate_residual_binary64_outside_the_frame(mode, case):
+    """Binary64 units whose steps take the 96-bit frame (values more than
+    nine binades apart, negative values), and grids whose sum of squares the
+    integer form could not scale, go to the two-plane engine."""
+    dims, block = (48, 20, 14), (24, 10, 7)
+    rng = np.random.default_rng(8)
+    u0 = rng.random(dims[::-1]) + 0.5
+    bc = BC_MIXED
+    if case == "spread":
+        u0.reshape(-1)[::89] = 3e-7
+    elif case == "mixed_signs":
+        u0 = u0 - 1.0
+        bc = (1.0, -0.25, 0.0, 0.5, -0.125, 0.75)
+    elif case == "huge_frame":  # squares scaled by 2^810: beyond the integer form's range, finite in binary64
+        u0 = u0 * 1e140
+        bc = tuple(b * 1e140 for b in BC_MIXED)
+    elif case == "tiny_frame":  # squares scaled by 2^-1050
+        u0 = u0 * 1e-140
+        bc = tuple(b * 1e-140 for b in BC_MIXED)
+    else:
+        u0.reshape(-1)[::3] = 0.0
+        bc = (0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
+    check(u0, dims, block, 5, 2, mode, bc, "f64", "exact")
 
 
 @pytest.mark.parametrize("mode", FUSED)
