@@ -1242,11 +1242,27 @@ struct R64Out {
 // 64-bit sums, L = S - 7c of the grid it reads; 2 the residual terms only
 // (nothing is written). The residual modes are called with the grid's frame
 // (uin null), so whether a unit falls back does not depend on the bounds.
+// The frame sources of unit u (LaunchArgs): its list in fs, or n = -1 where
+// it has none.
+struct FrameSources {
+    const int32_t* list;
+    int n;
+};
+
+__device__ __forceinline__ FrameSources frame_sources(const int32_t* fs_off, const int32_t* fs, int u)
+{
+    if (!fs_off) return {nullptr, -1};
+    const int a = fs_off[u], e = fs_off[u + 1];
+    const int start = a < 0 ? -a - 1 : a;
+    if (e < 0) return {nullptr, -1};
+    return {fs + start, e - start};
+}
+
 template <bool PULL, bool CG, int TW, int RM = 0>
 __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* __restrict__ desc,
                                     const int32_t* __restrict__ frame_e, int b, int p, int x0, int y0, int z0, int z1,
                                     unsigned char* smraw, SlowList* slow, const uint32_t* uin, uint32_t* uout,
-                                    R64Out* ro = nullptr)
+                                    R64Out* ro = nullptr, FrameSources fsrc = {nullptr, -1})
 {
     using T = double;
     using W = frame::W96;
@@ -1265,17 +1281,28 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     const int tid = threadIdx.x, tp = tid % kTP, ty = tid / kTP;
     __shared__ uint32_t s_red[kN / 32];
     if (uin) {
-        // the largest exponent bound of the blocks this tile reads
         uint32_t emax = 0u;
-        for (int j = 0; j < 7; ++j) {
-            const int nb = j == 0 ? b : d.nbr[j - 1];
-            if (nb < 0) {
-                if (tid == 0) emax = max(emax, (uint32_t)exp_field(d.bc[j - 1]));
-                continue;
+        if (fsrc.n >= 0) {
+            // the largest exponent bound of the units this tile reads, and the
+            // Dirichlet values of the faces it touches
+            for (int i = tid; i < fsrc.n; i += kN) emax = max(emax, __ldcg(uin + fsrc.list[i]));
+            if (tid == 0) {
+                const bool touch[6] = {x0 == 0, x0 + TW >= bx, y0 == 0, y0 + n2_rows<TW>() >= by, z0 == 0, z1 >= bz};
+                for (int j = 0; j < 6; ++j)
+                    if (d.nbr[j] < 0 && touch[j]) emax = max(emax, (uint32_t)exp_field(d.bc[j]));
             }
-            const BlockDesc& n = desc[nb];
-            const int u0 = n.u0, nt = n.ntiles;
-            for (int i = tid; i < nt; i += kN) emax = max(emax, __ldcg(uin + u0 + i));
+        } else {
+            // the largest exponent bound of the blocks this tile reads
+            for (int j = 0; j < 7; ++j) {
+                const int nb = j == 0 ? b : d.nbr[j - 1];
+                if (nb < 0) {
+                    if (tid == 0) emax = max(emax, (uint32_t)exp_field(d.bc[j - 1]));
+                    continue;
+                }
+                const BlockDesc& n = desc[nb];
+                const int u0 = n.u0, nt = n.ntiles;
+                for (int i = tid; i < nt; i += kN) emax = max(emax, __ldcg(uin + u0 + i));
+            }
         }
         emax = __reduce_max_sync(0xffffffffu, emax);
         if ((tid & 31) == 0) s_red[tid >> 5] = emax;
@@ -1658,10 +1685,11 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
 template <bool PULL, bool CG, int TW>
 __device__ __forceinline__ void exact_unit(double* pool, const BlockDesc* desc, const int32_t* frame_e, int b, int p,
                                            int x0, int y0, int z0, int z1, SlowList* slow, const uint32_t* uin,
-                                           uint32_t* uout)
+                                           uint32_t* uout, FrameSources fsrc = {nullptr, -1})
 {
     if ((desc[b].ext[0] & 1) == 0) {
-        tile_engine_narrow2<PULL, CG, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow, uin, uout);
+        tile_engine_narrow2<PULL, CG, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow, uin, uout,
+                                          nullptr, fsrc);
     } else {
         // (the single-column form keeps the grid's frame; its units' bounds stay unknown)
         tile_engine_narrow<PULL, CG, kRing<double>, TW>(pool, desc, frame_e, b, p, x0, y0, z0, z1, jac_dyn_sm, slow);
@@ -2215,7 +2243,8 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
 
 template <typename T, int OP>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
-                                                            const TileUnit* units, int p, uint32_t* uexp, int ucap)
+                                                            const TileUnit* units, int p, uint32_t* uexp, int ucap,
+                                                            const int32_t* fs_off, const int32_t* fs)
 {
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
@@ -2223,7 +2252,8 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* p
         constexpr int TW = decltype(tw_c)::value;
         if constexpr (OP == OP_EXACT)
             exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow,
-                                        uexp + (int64_t)p * ucap, uexp + (int64_t)(p ^ 1) * ucap + blockIdx.x);
+                                        uexp + (int64_t)p * ucap, uexp + (int64_t)(p ^ 1) * ucap + blockIdx.x,
+                                        frame_sources(fs_off, fs, blockIdx.x));
         else
             seq_unit<true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
     });
@@ -2262,7 +2292,8 @@ template <typename T, int OP, bool RING>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
-                 int hold_block, int64_t hold_after, uint32_t* uexp, int ucap)
+                 int hold_block, int64_t hold_after, uint32_t* uexp, int ucap, const int32_t* fs_off,
+                 const int32_t* fs)
 {
     __shared__ SlowList slow;
     __shared__ long long s_next;
@@ -2317,7 +2348,8 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
             } else if constexpr (OP == OP_EXACT) {
                 const int pt = (p0 + t) & 1;
                 exact_unit<true, true, TW>(pool, desc, frame_e, u.block, pt, u.x0, u.y0, u.z0, u.z1, &slow,
-                                           uexp + (int64_t)pt * ucap, uexp + (int64_t)(pt ^ 1) * ucap + w % nunits);
+                                           uexp + (int64_t)pt * ucap, uexp + (int64_t)(pt ^ 1) * ucap + w % nunits,
+                                           frame_sources(fs_off, fs, (int)(w % nunits)));
             } else {
                 seq_unit<true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             }
@@ -2911,10 +2943,10 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
         k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
         k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs_off, a.fs);
     else
         k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs_off, a.fs);
     return cudaGetLastError();
 }
 
@@ -2979,15 +3011,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
     if (dtype_f32)
         k_persistent<float, OP_SEQ, true><<<ctas, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
     else if (arith == 1)
         k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
     else
         k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
     return cudaGetLastError();
 }
 

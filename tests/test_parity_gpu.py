@@ -465,3 +465,28 @@ def test_per_tile_frames_on_blocks_of_very_different_magnitude(mode):
         got2 = J.read()
     assert np.array_equal(got, want)
     assert np.array_equal(got2, want)
+
+
+@pytest.mark.parametrize("mode", ["fused", "persistent"])
+@pytest.mark.parametrize("tile_w,zdepth", [(64, 0), (32, 0), (16, 0), (32, 12), (64, 7)])
+def test_unit_frames_with_magnitudes_varying_inside_blocks(mode, tile_w, zdepth):
+    """Each tile's frame comes from the exponent bounds of the units whose
+    values it reads (its own, the adjacent units of its block, the face
+    units of the neighbouring blocks) and the Dirichlet faces it touches.
+    Magnitudes that change by 2^10 from one tile row, tile column or z slab
+    to the next, inside blocks and across them, with several tile widths and
+    z depths (units split in z), against the oracle bit for bit: a source
+    left out of a list would put a value above its tile's frame."""
+    dims, block = (96, 80, 60), (48, 40, 30)
+    u0 = grid(43, dims)
+    z, y, x = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    expo = -10 * ((x // 16) % 3 + (y // 4) % 3 + (z // 6) % 3)
+    u0 = u0 * 2.0 ** expo
+    bc = (2.0 ** 8, 0.0, 2.0 ** -40, 0.25, 0.0, 1e-20)
+    want = oracle.jacobi(u0, bc, 9, oracle.RULE_EXACT)
+    with Jacobi3D(dims, block, bc=bc, mode=mode) as J:
+        _lib.jac_set_tile(J.h, tile_w, zdepth)
+        J.write(u0)
+        J.iterate(9)
+        got = J.read()
+    assert np.array_equal(got, want)
