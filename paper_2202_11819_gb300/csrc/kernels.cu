@@ -51,14 +51,15 @@ template <typename T>
 constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
 template <typename T>
 constexpr int kMinCTAs = 1024 / kNT<T>;
-// The exact mean's two-column engine keeps four cells' values live per
-// thread: three 256-thread CTAs per SM (80 registers each) instead of four.
-// Four at 64 registers (1.8 KB of spill stores in the compiled kernel)
-// measured the same on an aged field (0.461 against 0.462 ms per 512^3
-// iteration, 64-wide tiles) but slower with 32-wide tiles (0.482 against
-// 0.474).
+// Minimum resident CTAs per SM of the update kernels (it sets their register
+// budget). The exact mean's two-column engine runs four 256-thread CTAs per
+// SM at 64 registers: the 96-bit step spills (1.8 KB of spill stores), but
+// with frames from each unit's sources few steps take it, and the extra CTA
+// hides the units' prologue latency (512^3, 64-wide tiles: 0.425 ms per
+// iteration young and 0.449 aged, against 0.436 and 0.451 at three CTAs of
+// 80 registers; 32-wide tiles lose: 0.469 against 0.462 aged).
 template <typename T, int OP>
-constexpr int kMinCTAsOp = (sizeof(T) == 8 && OP == 1) ? 3 : kMinCTAs<T>;
+constexpr int kMinCTAsOp = kMinCTAs<T>;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
