@@ -55,6 +55,8 @@ struct TileUnit {
     int16_t z0, z1;
     int16_t tw;   // tile width: 16, 32 or 64 columns
     int16_t pad;
+    int32_t fs0;  // its frame sources (the units whose outputs its tile reads) are fs[fs0 .. fs0 + fsn)
+    int32_t fsn;  // -1: no list (the bounds of every unit of its block and neighbours are taken)
 };
 
 // Error word values written by kernels (read back by the host at syncs).

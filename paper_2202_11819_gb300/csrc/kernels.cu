@@ -1243,20 +1243,16 @@ struct R64Out {
 // 64-bit sums, L = S - 7c of the grid it reads; 2 the residual terms only
 // (nothing is written). The residual modes are called with the grid's frame
 // (uin null), so whether a unit falls back does not depend on the bounds.
-// The frame sources of unit u (LaunchArgs): its list in fs, or n = -1 where
-// it has none.
+// The frame sources of a unit: its list in fs, or n = -1 where it has none.
 struct FrameSources {
     const int32_t* list;
     int n;
 };
 
-__device__ __forceinline__ FrameSources frame_sources(const int32_t* fs_off, const int32_t* fs, int u)
+__device__ __forceinline__ FrameSources frame_sources(const int32_t* fs, const TileUnit& u)
 {
-    if (!fs_off) return {nullptr, -1};
-    const int a = fs_off[u], e = fs_off[u + 1];
-    const int start = a < 0 ? -a - 1 : a;
-    if (e < 0) return {nullptr, -1};
-    return {fs + start, e - start};
+    if (!fs || u.fsn < 0) return {nullptr, -1};
+    return {fs + u.fs0, u.fsn};
 }
 
 template <bool PULL, bool CG, int TW, int RM = 0>
@@ -1281,33 +1277,6 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2];
     const int tid = threadIdx.x, tp = tid % kTP, ty = tid / kTP;
     __shared__ uint32_t s_red[kN / 32];
-    if (uin) {
-        uint32_t emax = 0u;
-        if (fsrc.n >= 0) {
-            // the largest exponent bound of the units this tile reads, and the
-            // Dirichlet values of the faces it touches
-            for (int i = tid; i < fsrc.n; i += kN) emax = max(emax, __ldcg(uin + fsrc.list[i]));
-            if (tid == 0) {
-                const bool touch[6] = {x0 == 0, x0 + TW >= bx, y0 == 0, y0 + n2_rows<TW>() >= by, z0 == 0, z1 >= bz};
-                for (int j = 0; j < 6; ++j)
-                    if (d.nbr[j] < 0 && touch[j]) emax = max(emax, (uint32_t)exp_field(d.bc[j]));
-            }
-        } else {
-            // the largest exponent bound of the blocks this tile reads
-            for (int j = 0; j < 7; ++j) {
-                const int nb = j == 0 ? b : d.nbr[j - 1];
-                if (nb < 0) {
-                    if (tid == 0) emax = max(emax, (uint32_t)exp_field(d.bc[j - 1]));
-                    continue;
-                }
-                const BlockDesc& n = desc[nb];
-                const int u0 = n.u0, nt = n.ntiles;
-                for (int i = tid; i < nt; i += kN) emax = max(emax, __ldcg(uin + u0 + i));
-            }
-        }
-        emax = __reduce_max_sync(0xffffffffu, emax);
-        if ((tid & 31) == 0) s_red[tid >> 5] = emax;
-    }
     const int x = x0 + 2 * tp, y = y0 + ty;
     const int plane = (int)d.plane;  // block dims are at most 256: a plane holds fewer than 2^17 elements
     if (tid == 0) {
@@ -1395,6 +1364,35 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
         osrc += 2 * oplane;
     };
     copy_r(0, z0);
+    // the tile's frame from the exponent bounds (after the first copies and
+    // loads are in flight, so their latencies overlap)
+    if (uin) {
+        uint32_t emax = 0u;
+        if (fsrc.n >= 0) {
+            // the largest exponent bound of the units this tile reads, and the
+            // Dirichlet values of the faces it touches
+            for (int i = tid; i < fsrc.n; i += kN) emax = max(emax, __ldcg(uin + fsrc.list[i]));
+            if (tid == 0) {
+                const bool touch[6] = {x0 == 0, x0 + TW >= bx, y0 == 0, y0 + n2_rows<TW>() >= by, z0 == 0, z1 >= bz};
+                for (int j = 0; j < 6; ++j)
+                    if (d.nbr[j] < 0 && touch[j]) emax = max(emax, (uint32_t)exp_field(d.bc[j]));
+            }
+        } else {
+            // the largest exponent bound of the blocks this tile reads
+            for (int j = 0; j < 7; ++j) {
+                const int nb = j == 0 ? b : d.nbr[j - 1];
+                if (nb < 0) {
+                    if (tid == 0) emax = max(emax, (uint32_t)exp_field(d.bc[j - 1]));
+                    continue;
+                }
+                const BlockDesc& n = desc[nb];
+                const int u0 = n.u0, nt = n.ntiles;
+                for (int i = tid; i < nt; i += kN) emax = max(emax, __ldcg(uin + u0 + i));
+            }
+        }
+        emax = __reduce_max_sync(0xffffffffu, emax);
+        if ((tid & 31) == 0) s_red[tid >> 5] = emax;
+    }
     __syncthreads();  // slow->n = 0 visible before any append; the warps' exponent bounds
     int eref = frame_e[d.inst] + 1;
     if (uin) {
@@ -2245,7 +2243,7 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
 template <typename T, int OP>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p, uint32_t* uexp, int ucap,
-                                                            const int32_t* fs_off, const int32_t* fs)
+                                                            const int32_t* fs)
 {
     __shared__ SlowList slow;
     const TileUnit u = units[blockIdx.x];
@@ -2254,7 +2252,7 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* p
         if constexpr (OP == OP_EXACT)
             exact_unit<true, false, TW>(pool, desc, frame_e, u.block, p, u.x0, u.y0, u.z0, u.z1, &slow,
                                         uexp + (int64_t)p * ucap, uexp + (int64_t)(p ^ 1) * ucap + blockIdx.x,
-                                        frame_sources(fs_off, fs, blockIdx.x));
+                                        frame_sources(fs, u));
         else
             seq_unit<true, false, TW>(pool, desc, u.block, p, u.x0, u.y0, u.z0, u.z1);
     });
@@ -2293,8 +2291,7 @@ template <typename T, int OP, bool RING>
 __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
-                 int hold_block, int64_t hold_after, uint32_t* uexp, int ucap, const int32_t* fs_off,
-                 const int32_t* fs)
+                 int hold_block, int64_t hold_after, uint32_t* uexp, int ucap, const int32_t* fs)
 {
     __shared__ SlowList slow;
     __shared__ long long s_next;
@@ -2350,7 +2347,7 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
                 const int pt = (p0 + t) & 1;
                 exact_unit<true, true, TW>(pool, desc, frame_e, u.block, pt, u.x0, u.y0, u.z0, u.z1, &slow,
                                            uexp + (int64_t)pt * ucap, uexp + (int64_t)(pt ^ 1) * ucap + w % nunits,
-                                           frame_sources(fs_off, fs, (int)(w % nunits)));
+                                           frame_sources(fs, u));
             } else {
                 seq_unit<true, true, TW>(pool, desc, u.block, (p0 + t) & 1, u.x0, u.y0, u.z0, u.z1);
             }
@@ -2944,10 +2941,10 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
         k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
         k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs_off, a.fs);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
     else
         k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs_off, a.fs);
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
     return cudaGetLastError();
 }
 
@@ -3012,15 +3009,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
     if (dtype_f32)
         k_persistent<float, OP_SEQ, true><<<ctas, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>(
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else if (arith == 1)
         k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else
         k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs_off, a.fs);
+            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     return cudaGetLastError();
 }
 

@@ -18,11 +18,7 @@ struct LaunchArgs {
     uint32_t* uexp;          // [2][units_cap]: per buffer parity and work unit, a bound on the
                              // exponent field of the unit's values there (all ones: unknown)
     int units_cap;
-    // per unit u: the units whose outputs its tile reads (frame sources), at
-    // fs[start(u) .. start(u+1)), start(v) = fs_off[v] or -fs_off[v] - 1;
-    // a negative fs_off[u + 1] marks a unit without a list
-    const int32_t* fs_off;
-    const int32_t* fs;
+    const int32_t* fs;       // the units' frame-source lists (TileUnit::fs0, fsn)
     uint32_t* rcount;        // zero between launches: the last-unit counter of the binary32 residual
     int nblocks;
     int nunits;

@@ -230,8 +230,7 @@ struct jac_ctx {
     // residual and I/O staging
     double* partials = nullptr;
     uint32_t* uexp = nullptr;  // [2][partials_cap] unit exponent bounds (see LaunchArgs)
-    int32_t* fs_off = nullptr;  // [partials_cap + 1] per unit: its frame sources in fs (see LaunchArgs)
-    int32_t* fs = nullptr;
+    int32_t* fs = nullptr;  // the units' frame-source lists (TileUnit::fs0, fsn)
     size_t fs_cap = 0;
     double* dres = nullptr;
     uint32_t* rcount = nullptr;  // the binary32 residual's last-unit counter (zero between launches)
@@ -247,7 +246,6 @@ struct jac_ctx {
         a.frame = frame;
         a.uexp = uexp;
         a.units_cap = (int)partials_cap;
-        a.fs_off = fs_off;
         a.fs = fs;
         a.rcount = rcount;
         a.nblocks = (int)hdesc.size();
@@ -371,10 +369,9 @@ int forget_unit_frames(jac_ctx* h)
 // its neighbours).
 constexpr int kMaxFrameSources = 256;
 
-int build_frame_sources(jac_ctx* h, std::vector<int32_t>& off, std::vector<int32_t>& src)
+int build_frame_sources(jac_ctx* h, std::vector<int32_t>& src)
 {
     const bool f32 = h->dtype == JAC_F32;
-    off.assign(h->hunits.size() + 1, 0);
     src.clear();
     // units of block nb overlapping columns [xa, xb], rows [ya, yb], planes [za, zb] (inclusive)
     auto add = [&](int32_t nb, int xa, int xb, int ya, int yb, int za, int zb) {
@@ -389,7 +386,7 @@ int build_frame_sources(jac_ctx* h, std::vector<int32_t>& off, std::vector<int32
         }
     };
     for (size_t i = 0; i < h->hunits.size(); ++i) {
-        const TileUnit& u = h->hunits[i];
+        TileUnit& u = h->hunits[i];
         const BlockDesc& d = h->hdesc[u.block];
         const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2], th = tile_rows(u.tw, f32);
         const int x1 = std::min<int>(u.x0 + u.tw, bx) - 1, y1 = std::min<int>(u.y0 + th, by) - 1, z1 = u.z1 - 1;
@@ -402,11 +399,12 @@ int build_frame_sources(jac_ctx* h, std::vector<int32_t>& off, std::vector<int32
         if (y1 == by - 1 && d.nbr[3] >= 0) add(d.nbr[3], u.x0, x1, 0, 0, u.z0, z1);
         if (u.z0 == 0 && d.nbr[4] >= 0) add(d.nbr[4], u.x0, x1, u.y0, y1, h->hdesc[d.nbr[4]].ext[2] - 1, h->hdesc[d.nbr[4]].ext[2] - 1);
         if (z1 == bz - 1 && d.nbr[5] >= 0) add(d.nbr[5], u.x0, x1, u.y0, y1, 0, 0);
-        if (src.size() - start > (size_t)kMaxFrameSources) {
+        u.fs0 = (int32_t)start;
+        u.fsn = (int32_t)(src.size() - start);
+        if (u.fsn > kMaxFrameSources) {
             src.resize(start);
-            off[i + 1] = -1;  // marker, fixed below
+            u.fsn = -1;
         }
-        off[i + 1] = off[i + 1] < 0 ? -(int32_t)src.size() - 1 : (int32_t)src.size();
     }
     return JAC_OK;
 }
@@ -445,6 +443,8 @@ int build_units(jac_ctx* h)
                         u.z1 = (int16_t)std::min(d.ext[2], (zc + 1) * zd);
                         u.tw = (int16_t)TW;
                         u.pad = 0;
+                        u.fs0 = 0;
+                        u.fsn = -1;  // set by build_frame_sources
                         h->tw_mask |= TW == 16 ? 1 : (TW == 32 ? 2 : 4);
                         h->hunits.push_back(u);
                     }
@@ -510,18 +510,15 @@ int build_units(jac_ctx* h)
         if ((rc = dev_alloc(h, need * sizeof(TileUnit), (void**)&h->dunits))) return rc;
         if ((rc = dev_alloc(h, need * sizeof(double), (void**)&h->partials))) return rc;
         if ((rc = dev_alloc(h, 2 * need * sizeof(uint32_t), (void**)&h->uexp))) return rc;
-        if ((rc = dev_alloc(h, (need + 1) * sizeof(int32_t), (void**)&h->fs_off))) return rc;
         h->partials_cap = need;
     }
-    std::vector<int32_t> fso, fsl;
-    if ((rc = build_frame_sources(h, fso, fsl))) return rc;
+    std::vector<int32_t> fsl;
+    if ((rc = build_frame_sources(h, fsl))) return rc;  // sets the units' fs0, fsn before they are copied
     if (fsl.size() > h->fs_cap || !h->fs) {
         const size_t cap = std::max<size_t>(1, fsl.size());
         if ((rc = dev_alloc(h, cap * sizeof(int32_t), (void**)&h->fs))) return rc;
         h->fs_cap = cap;
     }
-    CU(cudaMemcpyAsync(h->fs_off, fso.data(), fso.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
-       "copy frame source offsets");
     if (!fsl.empty())
         CU(cudaMemcpyAsync(h->fs, fsl.data(), fsl.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream),
            "copy frame sources");
