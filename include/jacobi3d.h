@@ -150,9 +150,12 @@ int jac_set_allocator(jac_alloc_fn alloc, jac_free_fn free_fn, void *user);
  * host forms of jac_write / jac_read (and any other host<->device copy),
  * laid out for the host link. A request of 64 MiB or more is backed by the
  * kernel's transparent huge pages where it offers them on request: anonymous
- * memory aligned to the huge-page size, advised MADV_HUGEPAGE, touched, then
- * registered with cudaHostRegister. A copy then needs one address
- * translation per huge page instead of one per base page. On GB300 (64 KiB
+ * memory aligned to the huge-page size, advised MADV_HUGEPAGE, placed
+ * preferably on the current GPU's nearest host NUMA node, touched, then
+ * registered with cudaHostRegister, when the kernel gives (nearly) all of it
+ * huge pages (else the memory comes from cudaHostAlloc: registered base pages
+ * copy more slowly than the driver's pinned memory). A copy then needs one
+ * address translation per huge page instead of one per base page. On GB300 (64 KiB
  * base pages, 512 MiB huge pages) a pinned 1 GiB buffer of base pages that
  * has not been copied for a second or more takes 80-210 ms for its next
  * copy, about 7 us per page translation, and 5.1 ms for the copies after it;

@@ -1574,9 +1574,13 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
             W fc0{}, fc1{}, fz0{}, fz1{}, f00{}, f01{}, f10{}, f11{};
             if (k1) {
                 const T* pk = osrc - (RD + 1) * plane;  // osrc is at plane k + RD + 1
-                const double2 c = ld_pair<CG>(pk);
-                const double2 zm = ld_pair<CG>((k == z0 && z0 == 0) ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4)
-                                                                    : pk - plane);
+                // L1-allocating loads, like the ring's cp.async.ca copies, which
+                // brought these lines in: in the persistent form the dependency
+                // acquire and the barrier before the tile order them after the
+                // writers' releases
+                const double2 c = *(const double2*)pk;
+                const double2 zm = *(const double2*)((k == z0 && z0 == 0) ? z_pair_source<PULL>(pool, desc, d, p, x, y, 4)
+                                                                          : pk - plane);
                 const double2 zh = *(const double2*)(rc + (RD * kN + tid) * 2);
                 const double2 a = zfirst ? zh : *(const double2*)(rc + (S * kN + tid) * 2);
                 const double2 bb = zsecond ? zh : *(const double2*)(rc + ((S + 1) * kN + tid) * 2);

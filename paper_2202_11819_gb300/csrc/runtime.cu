@@ -11,6 +11,8 @@
 // block).
 #include <cuda_runtime.h>
 #include <sys/mman.h>
+#include <sys/syscall.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <cmath>
@@ -1301,6 +1303,43 @@ size_t thp_bytes()
 
 constexpr size_t kHostHugeMin = size_t(64) << 20;  // smaller requests get base pages
 
+// Bytes of [p, p + len) the kernel backs with transparent huge pages (the
+// AnonHugePages of the mappings it overlaps in /proc/self/smaps).
+size_t huge_bytes(const void* p, size_t len)
+{
+    FILE* f = fopen("/proc/self/smaps", "r");
+    if (!f) return 0;
+    char line[512];
+    bool in = false;
+    size_t kb = 0;
+    const uintptr_t a = (uintptr_t)p, e = a + len;
+    while (fgets(line, sizeof line, f)) {
+        unsigned long lo = 0, hi = 0;
+        if (sscanf(line, "%lx-%lx", &lo, &hi) == 2) {  // a mapping's header line
+            in = lo < e && hi > a;
+            continue;
+        }
+        unsigned long v = 0;
+        if (in && strncmp(line, "AnonHugePages:", 14) == 0 && sscanf(line + 14, "%lu", &v) == 1) kb += v;
+    }
+    fclose(f);
+    return kb * 1024;
+}
+
+// Prefer the current GPU's nearest host NUMA node for the pages of [p, p +
+// len), so that they are not faulted in on whichever node the calling thread
+// happens to run (a far node halves or worse the device's writes to them).
+// Best effort: nothing changes where the attribute or the call is missing.
+void prefer_gpu_numa_node(void* p, size_t len)
+{
+    int dev = 0, node = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    if (cudaDeviceGetAttribute(&node, cudaDevAttrHostNumaId, dev) != cudaSuccess || node < 0 || node >= 63) return;
+    unsigned long mask = 1ul << node;
+    constexpr long kMpolPreferred = 1;
+    syscall(SYS_mbind, p, len, kMpolPreferred, &mask, (unsigned long)(8 * sizeof mask), 0u);
+}
+
 }  // namespace
 
 void* jac_host_alloc(size_t bytes)
@@ -1320,16 +1359,24 @@ void* jac_host_alloc(size_t bytes)
             if (r + len + hp > a + len) munmap((void*)(a + len), r + len + hp - (a + len));
             void* p = (void*)a;
             madvise(p, len, MADV_HUGEPAGE);
-            memset(p, 0, len);  // fault the pages in (as huge pages) before they are pinned
-            const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
-            if (e == cudaSuccess) {
-                std::lock_guard<std::mutex> lock(g_host_mu);
-                g_host[p] = HostBuf{len, true};
-                return p;
+            prefer_gpu_numa_node(p, len);
+            memset(p, 0, len);  // fault the pages in (huge, on that node) before they are pinned
+            constexpr int kMadvCollapse = 25;  // synchronous collapse where the faults got base pages
+            if (huge_bytes(p, len) < len) madvise(p, len, kMadvCollapse);
+            // registered base pages are slower to copy than the driver's pinned memory: keep the
+            // mapping only when (nearly) all of it is on huge pages
+            if (huge_bytes(p, len) >= len - len / 16) {
+                const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterPortable);
+                if (e == cudaSuccess) {
+                    std::lock_guard<std::mutex> lock(g_host_mu);
+                    g_host[p] = HostBuf{len, true};
+                    return p;
+                }
+                munmap(p, len);
+                cuda_fail(e, "jac_host_alloc: cudaHostRegister");
+                return nullptr;
             }
             munmap(p, len);
-            cuda_fail(e, "jac_host_alloc: cudaHostRegister");
-            return nullptr;
         }
     }
     void* p = nullptr;

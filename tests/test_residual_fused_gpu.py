@@ -211,3 +211,30 @@ def test_fused_residual_at_full_size_equals_the_residual_launch():
     r = rho.cpu().numpy()
     assert r[0] == r[1] and r[0] > 0
     assert torch.equal(a, b)
+
+
+def test_binary64_fused_residual_at_full_size_equals_the_residual_launch():
+    """512^3 binary64 in 64^3 blocks, 64-wide tiles, the correctly rounded
+    mean in the fused form: the residual from the update launch has the
+    residual launch's bits, and the iteration the plain fused launch's."""
+    import torch
+
+    dims, block = (512, 512, 512), (64, 64, 64)
+    u0 = torch.from_numpy(synth.grid_uniform01(0, *dims).reshape(-1)).to("cuda")
+    with Jacobi3D(dims, block, bc=synth.DIRICHLET_X0, mode="fused", arith="exact") as J:
+        _lib.jac_set_tile(J.h, 64, 0)
+        J.write_device(u0)
+        J.iterate(60)
+        rho = torch.zeros(2, dtype=torch.float64, device="cuda")
+        J.residual_device(rho[0:1])
+        J.iterate_residual(1, 1, rho[1:2])
+        a = torch.empty_like(u0)
+        J.read_device(a)
+        J.write_device(u0)
+        J.iterate(61)
+        b = torch.empty_like(u0)
+        J.read_device(b)
+        J.sync()
+    r = rho.cpu().numpy()
+    assert r[0] == r[1] and r[0] > 0
+    assert torch.equal(a, b)
