@@ -60,6 +60,11 @@ constexpr int kMinCTAs = 1024 / kNT<T>;
 // 80 registers; 32-wide tiles lose: 0.469 against 0.462 aged).
 template <typename T, int OP>
 constexpr int kMinCTAsOp = kMinCTAs<T>;
+// The exact mean's fused and persistent kernels are also built for three
+// CTAs per SM (80 registers, the 96-bit step without spills), which grids too
+// small to fill the GPU take: each CTA then runs alone on its SM, so its own
+// speed counts (64^3 in one block: 0.039 ms per iteration against 0.052).
+constexpr int kMinCTAsSmall = 3;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
@@ -2244,8 +2249,8 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
                                                        0, desc[b].ext[2], jac_dyn_sm);
 }
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+template <typename T, int OP, int MINB = kMinCTAsOp<T, OP>>
+__global__ void __launch_bounds__(kNT<T>, MINB) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p, uint32_t* uexp, int ucap,
                                                             const int32_t* fs)
 {
@@ -2291,8 +2296,8 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p)
 // overwrites (buffer p^1 held iteration t-1). The seven counters are polled
 // by seven threads at once, and the next unit is taken while the current
 // one computes. Every wait is bounded.
-template <typename T, int OP, bool RING>
-__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>))
+template <typename T, int OP, bool RING, int MINB = kMinCTAsOp<T, OP>>
+__global__ void __launch_bounds__(kNT<T>, MINB)
     k_persistent(T* pool, const BlockDesc* desc, const int32_t* frame_e, const TileUnit* units, int nunits, int p0,
                  int64_t n_iters, uint32_t* done, unsigned long long* work, DeviceStatus* st, int64_t wait_ns,
                  int hold_block, int64_t hold_after, uint32_t* uexp, int ucap, const int32_t* fs)
@@ -2944,19 +2949,26 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
     if (dtype_f32)
         k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
-        k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
+        if (a.small)
+            k_fused_step<double, OP_EXACT, kMinCTAsSmall>
+                <<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+                    (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
+        else
+            k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+                (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
     else
         k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
     return cudaGetLastError();
 }
 
-const void* persistent_kernel(int dtype_f32, int arith)
+const void* persistent_kernel(int dtype_f32, int arith, int small)
 {
     if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, true>;
-    return arith == 1 ? (const void*)k_persistent<double, OP_EXACT, false>
-                      : (const void*)k_persistent<double, OP_SEQ, false>;
+    if (arith == 1)
+        return small ? (const void*)k_persistent<double, OP_EXACT, false, kMinCTAsSmall>
+                     : (const void*)k_persistent<double, OP_EXACT, false>;
+    return (const void*)k_persistent<double, OP_SEQ, false>;
 }
 
 int persistent_block_threads(int dtype_f32) { return dtype_f32 ? kNT<float> : kNT<double>; }
@@ -2994,6 +3006,8 @@ cudaError_t prepare_kernels()
 #define JAC_ALLOW(K, BYTES) \
     if (e == cudaSuccess) e = allow_smem(K, BYTES)
     JAC_ALLOW((k_fused_step<double, OP_EXACT>), (unit_bytes_max<double, OP_EXACT>()));
+    JAC_ALLOW((k_fused_step<double, OP_EXACT, kMinCTAsSmall>), (unit_bytes_max<double, OP_EXACT>()));
+    JAC_ALLOW((k_persistent<double, OP_EXACT, false, kMinCTAsSmall>), (unit_bytes_max<double, OP_EXACT>()));
     JAC_ALLOW((k_fused_step<double, OP_SEQ>), (unit_bytes_max<double, OP_SEQ>()));
     JAC_ALLOW((k_fused_ring<float>), (unit_bytes_max<float, OP_SEQ>()));
     JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes_max<double, OP_EXACT>()));
@@ -3015,9 +3029,15 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
             (float*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
             q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else if (arith == 1)
-        k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-            (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,
-            q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
+        if (a.small)
+            k_persistent<double, OP_EXACT, false, kMinCTAsSmall>
+                <<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+                    (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status,
+                    q.wait_ns, q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
+        else
+            k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+                (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status,
+                q.wait_ns, q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else
         k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,

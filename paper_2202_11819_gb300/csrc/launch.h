@@ -19,6 +19,7 @@ struct LaunchArgs {
                              // exponent field of the unit's values there (all ones: unknown)
     int units_cap;
     const int32_t* fs;       // the units' frame-source lists (TileUnit::fs0, fsn)
+    int small;               // the grid has fewer units than two waves of the exact mean's 4-CTA build
     uint32_t* rcount;        // zero between launches: the last-unit counter of the binary32 residual
     int nblocks;
     int nunits;
@@ -42,7 +43,9 @@ int tile_rows(int tw, bool f32);
 int engine_threads(bool f32);
 bool tile_width_supported(int tw);
 int persistent_block_threads(int dtype_f32);
-const void* persistent_kernel(int dtype_f32, int arith);
+// small: the exact mean's latency build (kMinCTAsSmall CTAs per SM), for
+// grids with too few units to fill the GPU (LaunchArgs::small)
+const void* persistent_kernel(int dtype_f32, int arith, int small);
 // dynamic shared memory of a unit-kernel (fused, persistent) CTA whose units
 // use the tile widths in tw_mask (bit 0 = 16, 1 = 32, 2 = 64): only as much
 // as those widths need, so the rest of the SM's memory stays L1 cache

@@ -233,6 +233,7 @@ struct jac_ctx {
     double* partials = nullptr;
     uint32_t* uexp = nullptr;  // [2][partials_cap] unit exponent bounds (see LaunchArgs)
     int32_t* fs = nullptr;  // the units' frame-source lists (TileUnit::fs0, fsn)
+    int small = 0;          // see LaunchArgs::small
     size_t fs_cap = 0;
     double* dres = nullptr;
     uint32_t* rcount = nullptr;  // the binary32 residual's last-unit counter (zero between launches)
@@ -249,6 +250,7 @@ struct jac_ctx {
         a.uexp = uexp;
         a.units_cap = (int)partials_cap;
         a.fs = fs;
+        a.small = small;
         a.rcount = rcount;
         a.nblocks = (int)hdesc.size();
         a.nunits = (int)hunits.size();
@@ -453,13 +455,25 @@ int build_units(jac_ctx* h)
         }
         I.u1 = (int32_t)h->hunits.size();
     }
+    // A grid with fewer units than two waves of the exact mean's four-CTA
+    // build takes its three-CTA latency build (LaunchArgs::small).
+    if (!h->hunits.empty()) {
+        int per_sm4 = 0, sms4 = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, persistent_kernel(h->dtype == JAC_F32, h->arith, 0),
+                                                         persistent_block_threads(h->dtype == JAC_F32),
+                                                         persistent_smem_bytes(h->dtype == JAC_F32, h->arith,
+                                                                               h->tw_mask)),
+           "occupancy");
+        CU(cudaDeviceGetAttribute(&sms4, cudaDevAttrMultiProcessorCount, h->device), "SM count");
+        h->small = (int64_t)h->hunits.size() < 2 * (int64_t)per_sm4 * sms4 ? 1 : 0;
+    }
     // The last wave: when the units leave it at most half full, split its
     // units in z (each in place, so every instance's units stay together),
     // so the wave holds twice as many units of half the work.
     if (!h->hunits.empty() && !h->inst.empty()) {
         const int f32 = h->dtype == JAC_F32;
         int per_sm = 0, sms = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith, h->small),
                                                          persistent_block_threads(f32),
                                                          persistent_smem_bytes(f32, h->arith, h->tw_mask)),
            "occupancy");
@@ -1606,7 +1620,7 @@ int jac_iterate(jac_ctx* h, int64_t n)
         case JAC_MODE_PERSISTENT: {
             if (h->pctas == 0) {
                 int per_sm = 0, sms = 0;
-                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith),
+                CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel(f32, h->arith, h->small),
                                                                  persistent_block_threads(f32),
                                                                  persistent_smem_bytes(f32, h->arith, h->tw_mask)),
                    "occupancy");
