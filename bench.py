@@ -310,13 +310,7 @@ def run_ours(a, rank, world, local, pg):
     u0 = synth.grid_uniform01(0, *g)
     if a.dtype == "f32":
         u0 = u0.astype(np.float32)
-    # host buffers from the library's allocator (huge-page backed, registered);
-    # base-page pinned buffers (torch) for the comparison leg
-    h_in = _lib.host_array(ncell, np_dt)
-    h_in[:] = u0.reshape(-1)
-    host_in = torch.from_numpy(h_in)
-    host_out = torch.from_numpy(_lib.host_array(ncell, np_dt))
-    dev_u0 = host_in.to(f"cuda:{local}")
+    dev_u0 = torch.from_numpy(u0.reshape(-1)).to(f"cuda:{local}")
     rho = torch.zeros(1, dtype=torch.float64, device=f"cuda:{local}")
 
     with torch.cuda.stream(stream):
@@ -434,11 +428,22 @@ def run_ours(a, rank, world, local, pg):
                         "plain_copy_gb_per_s": {"h2d": round(nbytes / (tc1 - tc) / 1e9, 1),
                                                 "d2h": round(nbytes / (tc2 - tc1) / 1e9, 1)}}
 
+            # host buffers from the library's allocator (huge pages where the
+            # kernel gives them), allocated just before the leg as the
+            # comparison leg's are
+            h_in = _lib.host_array(ncell, np_dt)
+            h_in[:] = u0.reshape(-1)
+            host_in = torch.from_numpy(h_in)
+            host_out = torch.from_numpy(_lib.host_array(ncell, np_dt))
+            kinds = {_lib.jac_host_alloc_kind(host_in.data_ptr()), _lib.jac_host_alloc_kind(host_out.data_ptr())}
             e2e = e2e_leg(host_in, host_out)
-            e2e["host_buffers"] = "jac_host_alloc (transparent huge pages, registered)"
+            e2e["host_buffers"] = ("jac_host_alloc: transparent huge pages, registered" if kinds == {1} else
+                                   "jac_host_alloc: cudaHostAlloc (the kernel gave no huge pages)" if kinds == {0}
+                                   else "jac_host_alloc: mixed")
+            del h_in, host_in, host_out
             # the same with base-page pinned buffers: each copy after a long
             # launch then repeats its page translations (one per 64 KiB page)
-            base_in = host_in.clone().pin_memory()
+            base_in = torch.from_numpy(u0.reshape(-1)).pin_memory()
             base_out = torch.empty_like(base_in).pin_memory()
             b_leg = e2e_leg(base_in, base_out)
             e2e["base_page_pinned_buffers"] = {k: b_leg[k] for k in ("value", "ms_per_step",

@@ -170,6 +170,10 @@ void *jac_host_alloc(size_t bytes);
  * jac_host_alloc did not return gives JAC_EINVAL. */
 int jac_host_free(void *p);
 
+/* What backs a pointer jac_host_alloc returned: 1 huge pages (registered),
+ * 0 cudaHostAlloc memory, -1 a pointer it did not return. */
+int jac_host_alloc_kind(const void *p);
+
 /* ------------------------------------------------------------------ */
 /* Context lifecycle                                                   */
 /* ------------------------------------------------------------------ */

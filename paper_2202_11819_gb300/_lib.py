@@ -137,6 +137,7 @@ _SIGS = {
     "jac_iterate_residual": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p], ctypes.c_int),
     "jac_host_alloc": ([ctypes.c_size_t], ctypes.c_void_p),
     "jac_host_free": ([ctypes.c_void_p], ctypes.c_int),
+    "jac_host_alloc_kind": ([ctypes.c_void_p], ctypes.c_int),
     "jac_sync": ([ctypes.c_void_p], ctypes.c_int),
     "jac_info": ([ctypes.c_void_p, ctypes.POINTER(jac_info_t)], ctypes.c_int),
     "jac_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -313,6 +314,10 @@ def jac_host_alloc(nbytes: int) -> int:
 
 def jac_host_free(ptr: int) -> None:
     _check(load().jac_host_free(ctypes.c_void_p(ptr)), "jac_host_free")
+
+
+def jac_host_alloc_kind(ptr: int) -> int:
+    return load().jac_host_alloc_kind(ctypes.c_void_p(ptr))
 
 
 def host_array(n: int, dtype=np.float64) -> np.ndarray:

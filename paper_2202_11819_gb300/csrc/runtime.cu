@@ -1405,6 +1405,14 @@ void* jac_host_alloc(size_t bytes)
     return p;
 }
 
+int jac_host_alloc_kind(const void* p)
+{
+    std::lock_guard<std::mutex> lock(g_host_mu);
+    auto it = g_host.find(const_cast<void*>(p));
+    if (it == g_host.end()) return -1;
+    return it->second.mapped ? 1 : 0;
+}
+
 int jac_host_free(void* p)
 {
     if (!p) return JAC_OK;

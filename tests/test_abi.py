@@ -58,6 +58,7 @@ def test_strerror_and_invalid_arguments_without_gpu():
     assert lib.jac_host_free(None) == _lib.JAC_OK
     assert lib.jac_host_free(ctypes.c_void_p(4096)) == _lib.JAC_EINVAL
     assert not lib.jac_host_alloc(0)
+    assert lib.jac_host_alloc_kind(ctypes.c_void_p(4096)) == -1
 
 
 def test_allocator_hook_requires_both_functions():

@@ -35,6 +35,8 @@ def test_host_alloc_is_pinned_zeroed_and_copies(nbytes):
     assert not a.any()
     t = torch.from_numpy(a)
     assert t.is_pinned()
+    kind = _lib.jac_host_alloc_kind(a.ctypes.data)
+    assert kind in (0, 1) and (kind == 0 or nbytes >= 64 << 20)
     a[:] = np.arange(n, dtype=np.float64)
     d = t.to("cuda", non_blocking=True)
     back = torch.from_numpy(_lib.host_array(n, np.float64))
