@@ -52,19 +52,19 @@ constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
 template <typename T>
 constexpr int kMinCTAs = 1024 / kNT<T>;
 // Minimum resident CTAs per SM of the update kernels (it sets their register
-// budget). The exact mean's two-column engine runs four 256-thread CTAs per
-// SM at 64 registers: the 96-bit step spills (1.8 KB of spill stores), but
-// with frames from each unit's sources few steps take it, and the extra CTA
-// hides the units' prologue latency (512^3, 64-wide tiles: 0.425 ms per
-// iteration young and 0.449 aged, against 0.436 and 0.451 at three CTAs of
-// 80 registers; 32-wide tiles lose: 0.469 against 0.462 aged).
+// budget). The exact mean's two-column engine keeps four cells' values live
+// per thread: three 256-thread CTAs per SM at 80 registers, the 96-bit step
+// without spills. The persistent kernel is also built for four CTAs at 64
+// registers (1.8 KB of spill stores, in the 96-bit step), which grids with at
+// least two waves of units take: there the fourth CTA hides the units'
+// prologue latency (512^3, 64-wide tiles: 0.425 ms per iteration young and
+// 0.447 aged against 0.436 and 0.451). Everywhere else three are faster: one
+// block of 64^3 (0.039 against 0.052 ms), the fused form at 512^3 aged (0.509
+// against 0.539), the batch of 256 small grids (1.89e11 against 1.66e11
+// cell-updates/s).
 template <typename T, int OP>
-constexpr int kMinCTAsOp = kMinCTAs<T>;
-// The exact mean's fused and persistent kernels are also built for three
-// CTAs per SM (80 registers, the 96-bit step without spills), which grids too
-// small to fill the GPU take: each CTA then runs alone on its SM, so its own
-// speed counts (64^3 in one block: 0.039 ms per iteration against 0.052).
-constexpr int kMinCTAsSmall = 3;
+constexpr int kMinCTAsOp = (sizeof(T) == 8 && OP == 1) ? 3 : kMinCTAs<T>;
+constexpr int kMinCTAsWide = 4;
 
 template <typename T>
 __device__ __forceinline__ int64_t cell_index(const BlockDesc& d, int p, int x, int y, int k)
@@ -2249,8 +2249,8 @@ __global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_stencil_block(T
                                                        0, desc[b].ext[2], jac_dyn_sm);
 }
 
-template <typename T, int OP, int MINB = kMinCTAsOp<T, OP>>
-__global__ void __launch_bounds__(kNT<T>, MINB) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
+template <typename T, int OP>
+__global__ void __launch_bounds__(kNT<T>, (kMinCTAsOp<T, OP>)) k_fused_step(T* pool, const BlockDesc* desc, const int32_t* frame_e,
                                                             const TileUnit* units, int p, uint32_t* uexp, int ucap,
                                                             const int32_t* fs)
 {
@@ -2949,13 +2949,8 @@ cudaError_t launch_fused_step(const LaunchArgs& a, int dtype_f32, int arith, int
     if (dtype_f32)
         k_fused_ring<float><<<a.nunits, kNT<float>, unit_bytes<float, OP_SEQ>(a.tw_mask), s>>>((float*)a.pool, a.desc, a.units, p);
     else if (arith == 1)
-        if (a.small)
-            k_fused_step<double, OP_EXACT, kMinCTAsSmall>
-                <<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-                    (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
-        else
-            k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-                (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
+        k_fused_step<double, OP_EXACT><<<a.nunits, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+            (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
     else
         k_fused_step<double, OP_SEQ><<<a.nunits, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, p, a.uexp, a.units_cap, a.fs);
@@ -2966,8 +2961,8 @@ const void* persistent_kernel(int dtype_f32, int arith, int small)
 {
     if (dtype_f32) return (const void*)k_persistent<float, OP_SEQ, true>;
     if (arith == 1)
-        return small ? (const void*)k_persistent<double, OP_EXACT, false, kMinCTAsSmall>
-                     : (const void*)k_persistent<double, OP_EXACT, false>;
+        return small ? (const void*)k_persistent<double, OP_EXACT, false>
+                     : (const void*)k_persistent<double, OP_EXACT, false, kMinCTAsWide>;
     return (const void*)k_persistent<double, OP_SEQ, false>;
 }
 
@@ -3006,8 +3001,7 @@ cudaError_t prepare_kernels()
 #define JAC_ALLOW(K, BYTES) \
     if (e == cudaSuccess) e = allow_smem(K, BYTES)
     JAC_ALLOW((k_fused_step<double, OP_EXACT>), (unit_bytes_max<double, OP_EXACT>()));
-    JAC_ALLOW((k_fused_step<double, OP_EXACT, kMinCTAsSmall>), (unit_bytes_max<double, OP_EXACT>()));
-    JAC_ALLOW((k_persistent<double, OP_EXACT, false, kMinCTAsSmall>), (unit_bytes_max<double, OP_EXACT>()));
+    JAC_ALLOW((k_persistent<double, OP_EXACT, false, kMinCTAsWide>), (unit_bytes_max<double, OP_EXACT>()));
     JAC_ALLOW((k_fused_step<double, OP_SEQ>), (unit_bytes_max<double, OP_SEQ>()));
     JAC_ALLOW((k_fused_ring<float>), (unit_bytes_max<float, OP_SEQ>()));
     JAC_ALLOW((k_persistent<double, OP_EXACT, false>), (unit_bytes_max<double, OP_EXACT>()));
@@ -3030,14 +3024,14 @@ cudaError_t launch_persistent(const LaunchArgs& a, const PersistentArgs& q, int 
             q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else if (arith == 1)
         if (a.small)
-            k_persistent<double, OP_EXACT, false, kMinCTAsSmall>
-                <<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
-                    (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status,
-                    q.wait_ns, q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
-        else
             k_persistent<double, OP_EXACT, false><<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
                 (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status,
                 q.wait_ns, q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
+        else
+            k_persistent<double, OP_EXACT, false, kMinCTAsWide>
+                <<<ctas, kNT<double>, unit_bytes<double, OP_EXACT>(a.tw_mask), s>>>(
+                    (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status,
+                    q.wait_ns, q.hold_block, q.hold_after, a.uexp, a.units_cap, a.fs);
     else
         k_persistent<double, OP_SEQ, false><<<ctas, kNT<double>, unit_bytes<double, OP_SEQ>(a.tw_mask), s>>>(
             (double*)a.pool, a.desc, a.frame, a.units, a.nunits, q.p0, q.n_iters, q.done, q.work, q.status, q.wait_ns,

@@ -19,7 +19,7 @@ struct LaunchArgs {
                              // exponent field of the unit's values there (all ones: unknown)
     int units_cap;
     const int32_t* fs;       // the units' frame-source lists (TileUnit::fs0, fsn)
-    int small;               // the grid has fewer units than two waves of the exact mean's 4-CTA build
+    int small;               // the grid has fewer units than two waves of the exact mean's 4-CTA persistent build
     uint32_t* rcount;        // zero between launches: the last-unit counter of the binary32 residual
     int nblocks;
     int nunits;
@@ -43,8 +43,8 @@ int tile_rows(int tw, bool f32);
 int engine_threads(bool f32);
 bool tile_width_supported(int tw);
 int persistent_block_threads(int dtype_f32);
-// small: the exact mean's latency build (kMinCTAsSmall CTAs per SM), for
-// grids with too few units to fill the GPU (LaunchArgs::small)
+// small: the exact mean's three-CTA build, for grids with fewer units than two
+// waves of its four-CTA one (LaunchArgs::small)
 const void* persistent_kernel(int dtype_f32, int arith, int small);
 // dynamic shared memory of a unit-kernel (fused, persistent) CTA whose units
 // use the tile widths in tw_mask (bit 0 = 16, 1 = 32, 2 = 64): only as much

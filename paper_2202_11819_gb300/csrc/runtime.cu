@@ -456,7 +456,7 @@ int build_units(jac_ctx* h)
         I.u1 = (int32_t)h->hunits.size();
     }
     // A grid with fewer units than two waves of the exact mean's four-CTA
-    // build takes its three-CTA latency build (LaunchArgs::small).
+    // persistent build takes the three-CTA one (LaunchArgs::small).
     if (!h->hunits.empty()) {
         int per_sm4 = 0, sms4 = 0;
         CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm4, persistent_kernel(h->dtype == JAC_F32, h->arith, 0),
