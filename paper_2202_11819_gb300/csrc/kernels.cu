@@ -51,6 +51,7 @@ template <typename T>
 constexpr int kNT = sizeof(T) == 8 ? 256 : 512;
 template <typename T>
 constexpr int kMinCTAs = 1024 / kNT<T>;
+static_assert(kNT<float> <= kThreads && kNT<double> <= kThreads, "the slow lists encode thread ids below kThreads");
 // Minimum resident CTAs per SM of the update kernels (it sets their register
 // budget). The exact mean's two-column engine keeps four cells' values live
 // per thread: three 256-thread CTAs per SM at 80 registers, the 96-bit step

@@ -138,6 +138,8 @@ class Jacobi3D:
         out_tensor (device float64, at least ceil(n / every) values) gets
         rho(u^(k0 + j * every)), j = 0, 1, ..."""
         need = -(-int(n) // int(every)) if n > 0 and every > 0 else 0
+        if str(out_tensor.dtype) != "torch.float64" or not out_tensor.is_cuda or not out_tensor.is_contiguous():
+            raise ValueError("out_tensor must be a contiguous float64 CUDA tensor")
         if out_tensor.numel() < need:
             raise ValueError(f"out_tensor holds {out_tensor.numel()} values, {need} needed")
         _lib.jac_iterate_residual(self.h, n, every, out_tensor.data_ptr())

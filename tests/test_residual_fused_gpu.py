@@ -183,6 +183,10 @@ def test_iterate_residual_counts_and_errors():
         assert e.value.code == _lib.JAC_EINVAL
         with pytest.raises(ValueError):
             J.iterate_residual(7, 2, out[:3])
+        with pytest.raises(ValueError):
+            J.iterate_residual(7, 2, torch.zeros(8, dtype=torch.float32, device="cuda"))
+        with pytest.raises(ValueError):
+            J.iterate_residual(7, 2, torch.zeros(8, dtype=torch.float64))
         assert np.array_equal(J.read(np.float32), oracle.jacobi_f32(u0, BC_MIXED, 7))
 
 
