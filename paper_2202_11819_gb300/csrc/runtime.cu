@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "jacobi3d.h"
+#include "frame_sources.h"
 #include "jac_common.cuh"
 #include "launch.h"
 
@@ -365,51 +366,11 @@ int forget_unit_frames(jac_ctx* h)
     return JAC_OK;
 }
 
-// The frame sources of each unit: the units whose outputs the unit's tile
-// reads (its haloed box in its own block, and the neighbouring blocks' face
-// columns, rows or planes next to it), so the tile's frame can be taken from
-// their exponent bounds alone. A unit with more than kMaxFrameSources gets
-// no list (the engine then takes the bounds of every unit of its block and
-// its neighbours).
-constexpr int kMaxFrameSources = 256;
-
+// The units' frame sources (frame_sources.h).
 int build_frame_sources(jac_ctx* h, std::vector<int32_t>& src)
 {
     const bool f32 = h->dtype == JAC_F32;
-    src.clear();
-    // units of block nb overlapping columns [xa, xb], rows [ya, yb], planes [za, zb] (inclusive)
-    auto add = [&](int32_t nb, int xa, int xb, int ya, int yb, int za, int zb) {
-        if (nb < 0 || xa > xb || ya > yb || za > zb) return;
-        const BlockDesc& n = h->hdesc[nb];
-        for (int32_t v = n.u0; v >= 0 && v < n.u0 + n.ntiles; ++v) {
-            const TileUnit& w = h->hunits[v];
-            const int th = tile_rows(w.tw, f32);
-            if (w.x0 <= xb && w.x0 + w.tw - 1 >= xa && w.y0 <= yb && w.y0 + th - 1 >= ya && w.z0 <= zb &&
-                w.z1 - 1 >= za)
-                src.push_back(v);
-        }
-    };
-    for (size_t i = 0; i < h->hunits.size(); ++i) {
-        TileUnit& u = h->hunits[i];
-        const BlockDesc& d = h->hdesc[u.block];
-        const int bx = d.ext[0], by = d.ext[1], bz = d.ext[2], th = tile_rows(u.tw, f32);
-        const int x1 = std::min<int>(u.x0 + u.tw, bx) - 1, y1 = std::min<int>(u.y0 + th, by) - 1, z1 = u.z1 - 1;
-        const size_t start = src.size();
-        add(u.block, std::max(0, u.x0 - 1), std::min(bx - 1, x1 + 1), std::max(0, u.y0 - 1), std::min(by - 1, y1 + 1),
-            std::max(0, u.z0 - 1), std::min(bz - 1, z1 + 1));
-        if (u.x0 == 0 && d.nbr[0] >= 0) add(d.nbr[0], h->hdesc[d.nbr[0]].ext[0] - 1, h->hdesc[d.nbr[0]].ext[0] - 1, u.y0, y1, u.z0, z1);
-        if (x1 == bx - 1 && d.nbr[1] >= 0) add(d.nbr[1], 0, 0, u.y0, y1, u.z0, z1);
-        if (u.y0 == 0 && d.nbr[2] >= 0) add(d.nbr[2], u.x0, x1, h->hdesc[d.nbr[2]].ext[1] - 1, h->hdesc[d.nbr[2]].ext[1] - 1, u.z0, z1);
-        if (y1 == by - 1 && d.nbr[3] >= 0) add(d.nbr[3], u.x0, x1, 0, 0, u.z0, z1);
-        if (u.z0 == 0 && d.nbr[4] >= 0) add(d.nbr[4], u.x0, x1, u.y0, y1, h->hdesc[d.nbr[4]].ext[2] - 1, h->hdesc[d.nbr[4]].ext[2] - 1);
-        if (z1 == bz - 1 && d.nbr[5] >= 0) add(d.nbr[5], u.x0, x1, u.y0, y1, 0, 0);
-        u.fs0 = (int32_t)start;
-        u.fsn = (int32_t)(src.size() - start);
-        if (u.fsn > kMaxFrameSources) {
-            src.resize(start);
-            u.fsn = -1;
-        }
-    }
+    jac::build_frame_sources(h->hunits, h->hdesc, [f32](int tw) { return tile_rows(tw, f32); }, src);
     return JAC_OK;
 }
 
