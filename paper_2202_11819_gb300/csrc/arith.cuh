@@ -1033,6 +1033,26 @@ JAC_HD inline double mean7(uint64_t S, uint32_t scale_hi)
     return bitsd(d + ((uint64_t)(scale_hi - ((uint32_t)lz << 20)) << 32));
 }
 
+// q += L^2 over 192 bits for the Laplacian term L = S - 7c of a cell whose
+// frame sum is S and whose own frame integer is c. Both S and 7c lie below
+// 7 * 2^61 < 2^64, so |L| fits 64 bits unsigned (the signed difference, up to
+// 6 * 2^61 in magnitude, would not fit 64 bits signed) and L^2 < 2^128.
+JAC_HD inline void add_laplacian_square(uint64_t S, uint64_t c, uint64_t& q0, uint64_t& q1, uint64_t& q2)
+{
+    const uint64_t c7 = 7u * c;
+    const uint64_t u = S >= c7 ? S - c7 : c7 - S;
+    const uint64_t lo = u * u, hi = frame::umulhi64(u, u);
+    const uint64_t s0 = q0 + lo;
+    const uint64_t k0 = s0 < lo ? 1u : 0u;
+    const uint64_t t1 = q1 + hi;
+    const uint64_t k1 = t1 < hi ? 1u : 0u;
+    const uint64_t s1 = t1 + k0;
+    const uint64_t k2 = s1 < t1 ? 1u : 0u;
+    q0 = s0;
+    q1 = s1;
+    q2 += k1 + k2;
+}
+
 }  // namespace nframe
 
 // ------------------------------------------------------------------------

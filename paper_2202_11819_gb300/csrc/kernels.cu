@@ -1237,7 +1237,8 @@ __device__ __forceinline__ void n2_slow_cells(double* pool, const BlockDesc* des
 // tile stores the bound of its own outputs in *uout. The frame only scales
 // the integers, so the results do not depend on it.
 // What the residual modes return per thread: the exact sum of L^2 of its
-// cells in units of 2^(2 (eref - 1084)) (192 bits), and whether a step of
+// cells in units of 2^(2 (eref - 1084)) (192 bits: each term below 2^128, at
+// most 512 of them per thread), and whether a step of
 // the tile took the 96-bit frame (the unit's residual is then taken again by
 // the two-plane engine).
 struct R64Out {
@@ -1426,10 +1427,8 @@ __device__ void tile_engine_narrow2(double* __restrict__ pool, const BlockDesc* 
     // residual modes: this thread's sum of L^2 and whether a step fell back
     [[maybe_unused]] uint64_t rq0 = 0u, rq1 = 0u, rq2 = 0u;
     [[maybe_unused]] bool rbad = false;
-    // L = S - 7c: |L| < 6 * 2^61, exact in two's complement
-    [[maybe_unused]] auto lsq = [&](uint64_t S, uint64_t c) {
-        frame::add_square((int64_t)(S - 7u * c), rq0, rq1, rq2);
-    };
+    // L = S - 7c, its square added exactly (nframe::add_laplacian_square)
+    [[maybe_unused]] auto lsq = [&](uint64_t S, uint64_t c) { nframe::add_laplacian_square(S, c, rq0, rq1, rq2); };
     // the 64-bit sums and means of planes k (buffer n0) and k+1 (n1)
     auto narrow = [&](const uint64_t* n0, const uint64_t* n1, bool two) {
         const uint64_t uA = cA + c0A, uB = cB + c0B;

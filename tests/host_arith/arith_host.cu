@@ -198,3 +198,30 @@ extern "C" void host_r32_combine(const int64_t* abc, uint64_t* lohi)
     jac::r32::Acc a{abc[0], abc[1], abc[2]};
     jac::r32::combine(a, lohi[0], lohi[1]);
 }
+
+// The binary64 residual's integer form in the 64-bit frame of eref: over n
+// cells (c, xm, xp, ym, yp, zm, zp), L = S - 7c from the frame integers
+// (S the sum of the seven), L^2 summed in 192 bits and rounded once, scaled
+// by 2^(2 (eref - 1084)). 1 and the sum when every value lies in the frame
+// (neighbours may be +0), else 0.
+extern "C" int host_nframe_residual(const double* v, int n, int eref, double* out)
+{
+    using namespace jac;
+    const uint32_t elo = nframe::elo_hi(eref);
+    uint64_t q0 = 0u, q1 = 0u, q2 = 0u;
+    for (int i = 0; i < n; ++i) {
+        const double* w = v + 7 * i;
+        bool ok = true, g;
+        const uint64_t c = nframe::of(w[0], elo, g);
+        ok = ok && g;
+        uint64_t S = c;
+        for (int j = 1; j < 7; ++j) {
+            S += nframe::of0(w[j], elo, g);
+            ok = ok && g;
+        }
+        if (!ok) return 0;
+        nframe::add_laplacian_square(S, c, q0, q1, q2);
+    }
+    *out = frame::u192_to_double_scaled(q0, q1, q2, 2 * (eref - 1084));
+    return 1;
+}

@@ -704,3 +704,40 @@ def test_r32_combine_is_the_128_bit_sum(host_lib):
         lib.host_r32_combine(abc, lohi)
         s = (vals[0] * 2 ** 46 + vals[1] * 2 ** 24 + vals[2]) % 2 ** 128
         assert lohi[0] + 2 ** 64 * lohi[1] == s, vals
+
+
+def test_nframe_residual_is_the_exact_sum_of_squares_rounded_once(host_lib):
+    """The binary64 residual of the 64-bit frame: L = S - 7c of the frame
+    integers is the exact Laplacian term, and the 192-bit sum of squares over
+    512 cells (the most one thread sums) is rounded once."""
+    lib = host_lib
+    lib.host_nframe_residual.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.host_nframe_residual.restype = ctypes.c_int
+    rng = np.random.default_rng(17)
+    out = ctypes.c_double()
+    for eref in (1024, 1030, 600, 1500):
+        # the window: exponent fields eref - 9 .. eref - 1, values in [2^(eref-1032), 2^(eref-1023))
+        top = 2.0 ** (eref - 1023) * (1 - 2.0 ** -53)
+        low = 2.0 ** (eref - 1032)
+        n = 512
+        v = low * 2.0 ** rng.uniform(0, 8.99, (n, 7))
+        v[:64, 0] = low
+        v[:64, 1:] = top  # L near its largest, 6 * 2^61 frame units
+        v[64:128, 0] = top
+        v[64:128, 1:] = low  # L near its most negative
+        v[128:192, 1:] = v[128:192, :1]  # L = 0
+        v[200:260, 3] = 0.0  # zero neighbours are in the frame
+        v = np.ascontiguousarray(v)
+        assert lib.host_nframe_residual(v.ctypes.data, n, eref, ctypes.byref(out)) == 1
+        exact = Fraction(0)
+        for row in v:
+            fr = [Fraction(float(x)) for x in row]
+            exact += (sum(fr[1:]) - 6 * fr[0]) ** 2
+        assert out.value == float(exact), eref
+    # a value below the window, or a zero centre, is reported
+    w = np.ascontiguousarray(np.full((1, 7), 0.75))
+    w[0, 2] = 2.0 ** -20
+    assert lib.host_nframe_residual(w.ctypes.data, 1, 1024, ctypes.byref(out)) == 0
+    w[0, 2] = 0.75
+    w[0, 0] = 0.0
+    assert lib.host_nframe_residual(w.ctypes.data, 1, 1024, ctypes.byref(out)) == 0

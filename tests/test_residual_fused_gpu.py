@@ -242,3 +242,16 @@ def test_binary64_fused_residual_at_full_size_equals_the_residual_launch():
     r = rho.cpu().numpy()
     assert r[0] == r[1] and r[0] > 0
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("mode", FUSED + ["persistent"])
+def test_binary64_residual_at_the_frame_extremes(mode):
+    """A checkerboard of 1.9 and 0.004 (both inside one nine-binade window of
+    the 64-bit frame): every cell's Laplacian term is about six times the
+    window's top in magnitude, beyond 2^63 frame units, so the integer form
+    must square its magnitude unsigned."""
+    dims, block = (48, 20, 14), (24, 10, 7)
+    z, y, x = np.meshgrid(np.arange(dims[2]), np.arange(dims[1]), np.arange(dims[0]), indexing="ij")
+    u0 = np.where((x + y + z) % 2 == 0, 1.9, 0.004)
+    bc = (1.0, 0.5, 0.25, 1.5, 0.75, 1.25)
+    check(u0, dims, block, 3, 1, mode, bc, "f64", "exact")
